@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Frame-throughput benchmark of the HashPoint hot path on B300.
+
+One step = one frame of the whole hot path (table build + window search +
+primary-surface sampling + IDW aggregation + MLP decode + compositing) for
+every pixel of an 800x800 view of the 1M-point object scene (6 nested or
+overlapping ellipsoids, boxes and tori, 32-d features, r = 0.005, K = 8,
+n = 8, MLP 32-128-128-128-4), cycling through 8 cameras on a radius-4
+sphere.  Inputs are seeded synthetic data; L2 is flushed (256 MB write)
+before every step, outside the per-step CUDA-event timing.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
+the host cores instead (same workload, bounded ray samples per step).
+Multi-GPU (torchrun): independent replicas, one view stream per rank.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2404_14044_b300 import scenes  # noqa: E402
+
+METRIC = "rays/s (build+search+sample+render) at 800x800, 1M pts"
+N_VIEWS = 8
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="hashpoint", choices=["hashpoint", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--points", type=int, default=1_000_000)
+    ap.add_argument("--res", type=int, default=800)
+    return ap.parse_args()
+
+
+def workload(n_points, res):
+    pts = scenes.object_points(n_points, 0)
+    feats = scenes.random_features(n_points, 32, 1)
+    params = scenes.Params(radius_mode=scenes.RADIUS_FIXED, r=0.005, K=8, n_max=8)
+    dims = [32, 128, 128, 128, 4]
+    mlp = scenes.random_mlp(dims, 0, sigma_bias=1.5 / params.r)
+    cams = scenes.random_sphere_cameras(N_VIEWS, 4.0, 0, width=res, height=res)
+    return pts, feats, params, dims, mlp, cams
+
+
+def config_dict(n_points, res, extra=None):
+    d = {"workload": f"objects_{res}: {n_points} points on 6 closed shapes, {res}x{res} rays per frame, "
+                     f"8 views on a radius-4 sphere, r=0.005, K=8, n=8, MLP 32-128-128-128-4, FP32",
+         "rays_per_step": res * res, "points": n_points, "views": N_VIEWS,
+         "l2": "flushed before every step (256 MB write), flush outside the per-step event timing"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# -------------------------------------------------- algorithmic traffic/flops
+
+def algorithmic(kernel, N, Nv, P, R, S, K, F, dims, U):
+    """Algorithmic bytes (or FLOPs for the decode) of one launch of each kernel."""
+    mlp_flops = 2 * S * sum(dims[l] * dims[l + 1] for l in range(len(dims) - 1))
+    table = {
+        "k_project_count": ("hbm", 12 * N + 8 * N + 8 * P),
+        "k_scan": ("hbm", 8 * (P + 1)),
+        "k_scatter": ("hbm", 12 * N + 8 * N + 4 * Nv + 16 * Nv),
+        "k_bucket_sort": ("hbm", 8 * P + 32 * Nv),
+        "k_search_select": ("hbm", 4 * P + 16 * Nv + 20 * R + (16 + 8 * K) * S),
+        "k_aggregate_decode": ("alu", mlp_flops),
+        "k_composite": ("hbm", 28 * R + 20 * S),
+    }
+    return table[kernel]
+
+
+def agg_gather_bytes(S, K, F, U):
+    return 8 * K * S + 4 * F * U + 16 * S
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def fp32_peak_tflops(sm_count=148, clock_mhz=2032.0):
+    # 128 FP32 FMA lanes per SM, 2 FLOP per FMA
+    return sm_count * 128 * 2 * clock_mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------------ CPU side
+
+def oracle_frame_rate(pts, feats, params, dims, mlp, cam, stride, offset=0, nthreads=None):
+    """Oracle rays/s for a full frame from one oracle call on every
+    ``stride``-th ray (stride 1 = the whole frame): the call builds the whole
+    table (timed again on its own) and renders R/stride rays, and the frame
+    time is t_build + stride * (t_call - t_build)."""
+    import oracle
+    nthreads = nthreads or os.cpu_count() or 1
+    R = cam.width * cam.height
+    rays = None if stride == 1 else np.arange(offset % stride, R, stride, dtype=np.int32)
+    n = R if rays is None else len(rays)
+    t0 = time.perf_counter()
+    oracle.build_table(pts, cam, params)
+    t_build = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.render(pts, feats, cam, params, dims, mlp, rays=rays, nthreads=nthreads)
+    t_call = time.perf_counter() - t0
+    t_frame = t_call if stride == 1 else t_build + (R / n) * max(t_call - t_build, 1e-9)
+    return R / t_frame, t_build, t_frame, nthreads, t_call
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    pts, feats, params, dims, mlp, cams = workload(args.points, args.res)
+    R = args.res * args.res
+    stride = 16
+    for w in range(min(args.warmup, 1)):
+        oracle_frame_rate(pts, feats, params, dims, mlp, cams[w % N_VIEWS], 64)
+    frames = []
+    for k in range(args.steps):
+        v, t_build, t_frame, cores, _ = oracle_frame_rate(pts, feats, params, dims, mlp, cams[k % N_VIEWS], stride,
+                                                          offset=k)
+        frames.append(t_frame)
+    t_frame = float(np.mean(frames))
+    value = R / t_frame
+    sample = (f"per step: the oracle builds the whole table ({args.points} points) and renders every "
+              f"{stride}th ray of the {R}-ray frame (OpenMP over rays); frame time = build + {stride} x rays")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_frame, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(args.points, args.res, {"parallelism": "cpu oracle, rank 0 only"}),
+            "cpu_baseline": {"value": value, "unit": "rays/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU side
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2404_14044_b300 import hashpoint as H
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    pts_np, feats_np, params, dims, mlp_np, cams = workload(args.points, args.res)
+    R = args.res * args.res
+    N = len(pts_np)
+    pts = torch.from_numpy(pts_np).to(dev)
+    feats = torch.from_numpy(feats_np).to(dev)
+    mlp = torch.from_numpy(mlp_np).to(dev)
+    hp = H.HashPoint(params, dev)
+    hp.reserve(cams[0], params.r, N, R, params.n_max)
+    smp = H.SampleBuffers.allocate(R, params.K, params.n_max, dev)
+    rgb = torch.empty(R, 3, dtype=torch.float32, device=dev)
+    wsum = torch.empty(R, dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    views = [cams[(rank + i * world) % N_VIEWS] for i in range(N_VIEWS)]
+
+    def frame(cam, p=pts):
+        hp.build_table(p, cam, params.r)
+        hp.search_sample(None, params.K, params.n_max, out=smp)
+        hp.aggregate_render(smp, feats, dims, mlp, rgb, wsum)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for w in range(args.warmup):
+        flush.zero_()
+        frame(views[w % N_VIEWS])
+    code, detail = hp.status()
+    if code != 0:
+        raise SystemExit(f"device status after warm-up: {H.status_string(code)} ({detail})")
+
+    # ---- timed pass: K frames, per-step CUDA events (flush outside)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record()
+        frame(views[k % N_VIEWS])
+        ev[k][1].record()
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+    code, detail = hp.status()
+    if code != 0:
+        raise SystemExit(f"device status after timed pass: {H.status_string(code)} ({detail})")
+    t = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev_ms_max = float(t.item())
+    value = world * R * args.steps / (dev_ms_max / 1e3)
+
+    # per-frame sizes (last view) for the algorithmic traffic
+    S = int(smp.sample_offset[R].item())
+    tb = hp.table_info()
+    P = int(tb.n_buckets)
+    nv_t = torch.empty(1, dtype=torch.int32, device=dev)
+    Nv = int(hp.table()["start"][-1].item())
+    U = int(torch.unique(smp.nbr[:S][smp.nbr[:S] >= 0]).numel())
+
+    # ---- profiled pass: per-kernel device time on the launching stream
+    hp.profile_start(64 * args.steps)
+    Ss, Nvs = [], []
+    for k in range(args.steps):
+        flush.zero_()
+        frame(views[k % N_VIEWS])
+    prof = hp.profile_stop()
+    launches = sum(n for _, n in prof.values())
+    per_kernel = {name: {"ms_total": ms, "launches": n, "ms_avg": ms / n if n else 0.0}
+                  for name, (ms, n) in prof.items()}
+    dom = max(prof.items(), key=lambda kv: kv[1][0])[0]
+    bound, units = algorithmic(dom, N, Nv, P, R, S, params.K, 32, dims, U)
+    pk = peaks()
+    dom_ms = per_kernel[dom]["ms_avg"]
+    if bound == "alu":
+        clock = 2032.0
+        peak = fp32_peak_tflops(148, clock)
+        achieved = units / (dom_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "derived: 148 SMs x 128 FP32 FMA lanes x 2 FLOP x 2032 MHz",
+                "gather_bytes_per_launch": agg_gather_bytes(S, params.K, 32, U)}
+    else:
+        peak = pk.get("hbm_gbs", 6400.0)
+        achieved = units / (dom_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in pk else "fallback 6400 GB/s"}
+
+    # ---- end to end: per-frame point positions H2D from pinned memory, image D2H
+    e2e = None
+    if not args.no_e2e:
+        host_pts = torch.from_numpy(pts_np).pin_memory()
+        host_rgb = torch.empty(R, 3, dtype=torch.float32).pin_memory()
+        host_ws = torch.empty(R, dtype=torch.float32).pin_memory()
+        dev_pts = torch.empty_like(pts)
+        for w in range(2):
+            dev_pts.copy_(host_pts, non_blocking=True)
+            frame(views[w], dev_pts)
+            host_rgb.copy_(rgb, non_blocking=True)
+            host_ws.copy_(wsum, non_blocking=True)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in range(args.steps):
+            dev_pts.copy_(host_pts, non_blocking=True)
+            frame(views[k % N_VIEWS], dev_pts)
+            host_rgb.copy_(rgb, non_blocking=True)
+            host_ws.copy_(wsum, non_blocking=True)
+        e1.record()
+        barrier()
+        e2e_ms = e0.elapsed_time(e1)
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * R * args.steps / (float(t.item()) / 1e3), "unit": "rays/s",
+               "h2d_bytes_per_step": int(host_pts.numel() * 4), "d2h_bytes_per_step": int(R * 16),
+               "what": "per step: point positions H2D (pinned), table+search+render through the C-ABI, "
+                       "rgb+weight-sum D2H (pinned); features and MLP weights resident"}
+    code, detail = hp.status()
+    if code != 0:
+        raise SystemExit(f"device status after e2e pass: {H.status_string(code)} ({detail})")
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, t_build, t_frame, cores, t_call = oracle_frame_rate(pts_np, feats_np, params, dims, mlp_np, cams[0], 1)
+        cpu = {"value": v, "unit": "rays/s", "cores": cores, "kind": "oracle",
+               "sample": f"one whole frame (view 0: table of {N} points + all {R} rays, OpenMP over rays), "
+                         f"{t_frame:.2f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": dev_ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config_dict(args.points, args.res,
+                                      {"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                                       "samples_last_frame": S, "visible_points_last_frame": Nv,
+                                       "buckets": P, "unique_points_gathered": U}),
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clk, "per_kernel_ms": {k: round(v["ms_avg"], 5) for k, v in per_kernel.items()},
+                "wall_s_timed_region": t_wall}
+        print(json.dumps(line), flush=True)
+    hp.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,230 @@
+/*
+ * hashpoint.h -- C-ABI of the B300 (sm_103a) HashPoint hot path.
+ *
+ * The per-frame path of "HashPoint: Accelerated Point Searching and Sampling
+ * for Neural Rendering" (CVPR 2024):
+ *   hp_build_table      Sec. 3.2 "Accelerated structure construction": project
+ *                       the visible points, keep every point per pixel, reorder
+ *                       the list so each pixel's points are contiguous, and
+ *                       keep a pixel-keyed table of (start, count).
+ *   hp_search_sample    Sec. 3.2 "Searching" (window walk, radius test with the
+ *                       fixed radius or the cone radius of Eq. radius /
+ *                       Eq. r_approx2) and Sec. 3.3 "Adaptive primary surface
+ *                       sampling" (pseudo-UDF d_j, alpha_j, Eq. weight).
+ *   hp_aggregate_render Sec. 3.4 integration: inverse-distance aggregation of
+ *                       neighbour features, a radiance MLP, and the volume
+ *                       rendering of Eq. 2.
+ *
+ * Conventions (all entry points):
+ *   - Pointers named d_* are device pointers; they are owned by the caller and
+ *     must stay valid until the work enqueued on `stream` has finished.
+ *     Other pointers are host pointers, read during the call only.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Every call only enqueues work; nothing is synchronised except
+ *     by hp_get_status.
+ *   - Errors a host can see (bad sizes, NULL pointers, unbuilt table, missing
+ *     workspace) are returned at once and nothing is enqueued.  Errors found on
+ *     the device (sample capacity overflow, a bounded wait that gave up, a ray
+ *     pixel out of range) are recorded in the context's device status word and
+ *     reported by hp_get_status; the kernels still terminate.
+ *   - A context is used by one host thread at a time (thread-compatible, not
+ *     thread-safe).  Nothing is printed; no exception crosses the ABI.
+ *   - Float inputs are IEEE binary32.  Every discrete decision (pixel keys,
+ *     radius tests, orderings, neighbour sets, weights vs eps_w, clusters,
+ *     sample counts) follows a written float32 arithmetic contract so that it
+ *     is reproducible bit for bit by an independent CPU implementation.
+ */
+#ifndef HASHPOINT_H
+#define HASHPOINT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HP_OK = 0,
+    HP_ERR_INVALID_ARG = 1,   /* a size, pointer or parameter is out of range */
+    HP_ERR_CUDA = 2,          /* a CUDA runtime call failed (launch, memset, alloc) */
+    HP_ERR_OVERFLOW = 3,      /* device: more samples than hp_samples.capacity */
+    HP_ERR_TIMEOUT = 4,       /* device: a bounded inter-block wait gave up */
+    HP_ERR_NOT_BUILT = 5,     /* search before build, or build parameters changed */
+    HP_ERR_NO_MEMORY = 6,     /* workspace too small / allocation failed */
+    HP_ERR_BAD_RAY = 7        /* device: a ray pixel id outside [0, W*H) */
+} hp_status;
+
+typedef struct hp_ctx hp_ctx;
+
+/* Pinhole camera.  World -> camera: X_cam = R X_world + t (R row-major),
+ * camera axes x right, y down, z forward; pixel (u, v) has its centre at
+ * (u + 0.5, v + 0.5).  Rays start at the camera centre through pixel centres;
+ * points are searched for t (distance along the unit ray) in [t_near, t_far];
+ * points with camera depth <= z_near are dropped. */
+typedef struct {
+    int32_t width, height;
+    float fx, fy, cx, cy;
+    float R[9];
+    float t[3];
+    float t_near, t_far, z_near;
+} hp_camera;
+
+enum {
+    HP_RADIUS_FIXED = 0,        /* r(t) = r (Point-NeRF style fixed radius)            */
+    HP_RADIUS_CONE = 1,         /* r(t) = Eq. radius (exact similar-triangle form)      */
+    HP_RADIUS_CONE_APPROX = 2   /* r(t) = Eq. r_approx2 (small-angle form)              */
+};
+
+/* Method parameters (Sec. 3.2-3.3). */
+typedef struct {
+    int32_t radius_mode;  /* HP_RADIUS_* */
+    float rho;            /* cone modes: r_ddot / r_dot (kernel size s = 2*ceil(rho)+1);
+                             <= 0: chosen so that r(t_near) on the central ray equals r */
+    float gamma;          /* alpha_j = gamma * exp(-d_j^2 / beta2); 0 < gamma <= 1 */
+    float beta2;          /* beta^2 > 0 */
+    float eps_w;          /* a candidate is kept when w_j > eps_w (>= 0) */
+    float gap_k;          /* primary cluster: consecutive t-gap <= gap_k * r(t) */
+    float eps_d;          /* IDW distance floor (> 0) */
+    int32_t cand_cap;     /* candidates kept per ray, 1..128 (the smallest (t, id)) */
+    int32_t bg_mode;      /* 0 black background, 1 white */
+    int32_t window_h;     /* 0: derive the window half-width; > 0: force it */
+} hp_config;
+
+/* Per-sample / per-ray outputs of hp_search_sample (caller-owned device
+ * buffers).  R = number of rays; cap = capacity (rows of the per-sample
+ * arrays, R * n_samples always suffices).  Samples are packed ray by ray in
+ * ray order; the samples of ray i are rows sample_offset[i] ..
+ * sample_offset[i+1]-1, in increasing depth. */
+typedef struct {
+    int32_t *n_s;            /* [R]   samples kept (0..n_samples) */
+    int32_t *primary;        /* [R]   table key (padded pixel index) of the primary
+                                      surface's first point, -1 when none */
+    int32_t *cand_count;     /* [R]   points that passed the radius test, before cand_cap */
+    int64_t *sample_offset;  /* [R+1] exclusive prefix sum of n_s; [R] = total S */
+    float *t;                /* [cap] sample depth along the unit ray */
+    int32_t *ray;            /* [cap] ray index of the sample */
+    int32_t *src;            /* [cap] id of the point whose projection is the sample */
+    float *delta;            /* [cap] interval to the next sample; 2 r(t) for the last (Eq. 2) */
+    int32_t *nbr;            /* [cap*K] neighbour point ids, nearest first; -1 pads */
+    float *nbr_dist;         /* [cap*K] distances of those neighbours to the sample */
+    int64_t capacity;        /* rows available in the per-sample arrays */
+} hp_samples;
+
+#define HP_MLP_MAX_LAYERS 8
+#define HP_MLP_MAX_WIDTH 128
+
+/* Radiance MLP: n_layers linear layers with ReLU between them, input width
+ * dims[0] = F, output dims[n_layers] = 4 (density logit, r, g, b logits).
+ * params (device) packs W0 (dims[1] x dims[0], row-major), b0, W1, b1, ...
+ * density = softplus(o0), colour = sigmoid(o1..3).  Hidden widths are 16, 32,
+ * 64 or 128; the packed size is at most 40960 floats. */
+typedef struct {
+    int32_t n_layers;
+    int32_t dims[HP_MLP_MAX_LAYERS + 1];
+    const float *d_params;
+} hp_mlp;
+
+/* Read-only view of the table built by the last hp_build_table. */
+typedef struct {
+    int32_t h;               /* window half-width; table covers the image padded by h */
+    int32_t padded_width;    /* W + 2h */
+    int32_t padded_height;   /* H + 2h */
+    int64_t n_buckets;       /* padded_width * padded_height */
+    float r_ddot;            /* cone modes: r_ddot on the f = 1 image plane */
+    const uint32_t *d_start; /* [n_buckets+1] first list position of each bucket */
+    const float *d_points;   /* [N][4]: the reordered list, rows 0 .. d_start[n_buckets]-1:
+                                camera-space x, y, z and the point id (int32 bits),
+                                bucket by bucket, each bucket ordered by (z, x, y, id) */
+} hp_table;
+
+/* Create a context for `cfg` on the current CUDA device.  Allocates only the
+ * 64-byte device status word.  Returns HP_ERR_INVALID_ARG for bad parameters. */
+hp_status hp_create(hp_ctx **ctx, const hp_config *cfg);
+
+/* Release the context and any workspace it allocated itself. */
+hp_status hp_destroy(hp_ctx *ctx);
+
+/* Bytes of device workspace one frame needs: the table for n_points points
+ * seen by `cam` with radius r, plus scratch for n_rays rays of up to
+ * n_samples samples.  The result is a multiple of 256. */
+hp_status hp_workspace_size(const hp_config *cfg, const hp_camera *cam, float r, int64_t n_points,
+                            int64_t n_rays, int32_t n_samples, size_t *bytes);
+
+/* Host-only: the search-window half-width h (kernel size s = 2h+1) and, in
+ * the cone modes, r_ddot on the f = 1 image plane, for `cam`, `cfg` and
+ * radius r.  The window is the smallest that provably contains every point
+ * the radius test can accept (see the comment of derive_window in the
+ * library source), or the paper's s when that is larger (cone modes, Sec. 3.2). */
+hp_status hp_window(const hp_config *cfg, const hp_camera *cam, float r, int32_t *h, float *r_ddot);
+
+/* Give the context a caller-owned device workspace (256-byte aligned).  Without
+ * one the context allocates (and grows) its own with cudaMalloc. */
+hp_status hp_set_workspace(hp_ctx *ctx, void *d_ptr, size_t bytes);
+
+/* Sec. 3.2 table build for d_points (n_points x 3, world xyz) seen by `cam`.
+ * Fixed mode: r is the search radius.  Cone modes: r is used only when
+ * cfg.rho <= 0 (r_min at t_near).  n_points may be 0.  Kernels: projection +
+ * warp-aggregated bucket counts, decoupled-lookback scan, scatter, per-bucket
+ * depth sort. */
+hp_status hp_build_table(hp_ctx *ctx, const float *d_points, int64_t n_points, const hp_camera *cam,
+                         float r, void *stream);
+
+/* Describe the current table (valid after hp_build_table was enqueued). */
+hp_status hp_table_info(const hp_ctx *ctx, hp_table *out);
+
+/* Copy the current table into caller buffers (device-to-device, enqueued on
+ * `stream`): d_start receives n_buckets+1 uint32 starts, d_points receives
+ * n_points x 4 floats (the reordered list of hp_table.d_points; rows past
+ * d_start[n_buckets], the number of kept points, are unspecified). */
+hp_status hp_table_copy(const hp_ctx *ctx, uint32_t *d_start, float *d_points, void *stream);
+
+/* Sec. 3.2 window search + Sec. 3.3 primary-surface sampling for n_rays rays.
+ * d_ray_pixels: pixel ids v*W + u (device, n_rays), or NULL for all W*H
+ * pixels in row-major order (then n_rays must be W*H).  K: neighbours per
+ * candidate, 1..32; n_samples: 1..16.  Writes `out` (see hp_samples). */
+hp_status hp_search_sample(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n_rays, int32_t K,
+                           int32_t n_samples, const hp_samples *out, void *stream);
+
+/* Sec. 3.4 + Eq. 2 for the samples of the last hp_search_sample: features
+ * d_feats (n_points x F, F in {4,8,16,32,64,128}) blended by inverse distance
+ * (weights 1/max(dist, eps_d)), decoded by `mlp`, composited front to back.
+ * Writes d_rgb (n_rays x 3) and d_wsum (n_rays, the sum of compositing
+ * weights, <= 1).  `samples` must be the buffers given to hp_search_sample. */
+hp_status hp_aggregate_render(hp_ctx *ctx, const hp_samples *samples, int64_t n_rays, const float *d_feats,
+                              int32_t F, const hp_mlp *mlp, float *d_rgb, float *d_wsum, void *stream);
+
+/* Synchronise `stream`, then return the device status word recorded since the
+ * last call (HP_OK if none) and its detail (e.g. the tile or ray index), and
+ * clear it.  The return value is HP_ERR_CUDA if the synchronisation failed. */
+hp_status hp_get_status(hp_ctx *ctx, void *stream, int32_t *dev_status, int64_t *detail);
+
+/* Test hook for the bounded waits: the scan tile `skip_tile` (>= 0) does not
+ * publish its prefix, and a waiting block gives up after `spin_limit`
+ * iterations (0 = default).  skip_tile < 0 turns the hook off.  The waiter
+ * records HP_ERR_TIMEOUT and finishes; nothing hangs. */
+hp_status hp_debug_fault(hp_ctx *ctx, int32_t skip_tile, int32_t spin_limit);
+
+/* Per-kernel device timing (CUDA events recorded on the launching stream
+ * around every kernel the context launches).  hp_profile_start(ctx, n)
+ * begins recording up to n launches (events are created here, on the host);
+ * hp_profile_stop synchronises those events, writes the summed milliseconds
+ * and launch counts per kernel into ms[HP_PROF_KERNELS] and
+ * launches[HP_PROF_KERNELS] (either may be NULL), and stops recording.
+ * Kernel ids: see hp_profile_kernel_name. */
+#define HP_PROF_KERNELS 7
+hp_status hp_profile_start(hp_ctx *ctx, int32_t max_launches);
+hp_status hp_profile_stop(hp_ctx *ctx, double *ms, int32_t *launches);
+const char *hp_profile_kernel_name(int32_t id);
+
+/* Static string for a status code. */
+const char *hp_status_string(hp_status s);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int32_t hp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HASHPOINT_H */

@@ -1,0 +1,531 @@
+// C-ABI of the HashPoint hot path: argument checks, the search-window bound,
+// workspace carving and kernel launches.  See include/hashpoint.h.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "hp_kernels.cuh"
+
+using namespace hp;
+
+struct hp_ctx {
+    hp_config cfg;
+    int device = 0;
+    int num_sms = 1;
+    ErrWord *d_err = nullptr;
+    // caller workspace (if set)
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    // self-owned regions (used when no caller workspace is set)
+    char *own[3] = {nullptr, nullptr, nullptr};
+    size_t own_bytes[3] = {0, 0, 0};
+    uint32_t spin_limit = kSpinLimitDefault;
+    int32_t skip_tile = -1;
+    // table state
+    bool built = false;
+    Cam cam{};
+    int h = 0, Wp = 0, Hp = 0;
+    int64_t P = 0, N = 0;
+    float r = 0.f, rdd = 0.f;
+    size_t table_bytes = 0;
+    uint32_t *cnt = nullptr, *start = nullptr, *scan_ticket = nullptr;
+    uint2 *keyrank = nullptr;
+    float4 *spts = nullptr;
+    uint64_t *scan_flags = nullptr;
+    // search state
+    bool searched = false;
+    int64_t R = 0;
+    int K = 0, n_max = 0;
+    size_t search_bytes = 0;
+    Prof prof;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t al(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+bool is_finite32(float x) { return std::isfinite(x); }
+
+hp_status check_config(const hp_config *c)
+{
+    if (!c) return HP_ERR_INVALID_ARG;
+    if (c->radius_mode < HP_RADIUS_FIXED || c->radius_mode > HP_RADIUS_CONE_APPROX) return HP_ERR_INVALID_ARG;
+    if (!(c->gamma > 0.f && c->gamma <= 1.f)) return HP_ERR_INVALID_ARG;
+    if (!(c->beta2 > 0.f) || !is_finite32(c->beta2)) return HP_ERR_INVALID_ARG;
+    if (!(c->eps_w >= 0.f) || !is_finite32(c->eps_w)) return HP_ERR_INVALID_ARG;
+    if (!(c->gap_k > 0.f) || !is_finite32(c->gap_k)) return HP_ERR_INVALID_ARG;
+    if (!(c->eps_d > 0.f) || !is_finite32(c->eps_d)) return HP_ERR_INVALID_ARG;
+    if (c->cand_cap < 1 || c->cand_cap > kCandCap) return HP_ERR_INVALID_ARG;
+    if (c->bg_mode != 0 && c->bg_mode != 1) return HP_ERR_INVALID_ARG;
+    if (c->window_h < 0 || c->window_h > kHMax) return HP_ERR_INVALID_ARG;
+    if (!is_finite32(c->rho)) return HP_ERR_INVALID_ARG;
+    return HP_OK;
+}
+
+hp_status check_camera(const hp_camera *c)
+{
+    if (!c) return HP_ERR_INVALID_ARG;
+    if (c->width < 1 || c->height < 1 || (int64_t)c->width * c->height > 0x7fffffffLL) return HP_ERR_INVALID_ARG;
+    const float *f = &c->fx;
+    for (int i = 0; i < 4 + 9 + 3 + 3; ++i)
+        if (!is_finite32(f[i])) return HP_ERR_INVALID_ARG;
+    if (!(c->fx > 0.f) || !(c->fy > 0.f)) return HP_ERR_INVALID_ARG;
+    if (!(c->t_near > 0.f) || !(c->t_far >= c->t_near) || !(c->z_near > 0.f)) return HP_ERR_INVALID_ARG;
+    return HP_OK;
+}
+
+// Window half-width.  An accepted point lies at t >= t_near within r(t) of
+// the ray: P = t d + e with e orthogonal to d.  Its image-plane offset from
+// the ray's pixel centre is (e_x d_z - d_x e_z)/(Z d_z), bounded by
+// |e| sqrt(1 + nx^2) / Z, and Z >= t d_z - |e| sin(theta).  Bounding these
+// over all pixel centres gives the largest offset L in pixels; the point then
+// lies at most floor(L + 1/2) pixels away.  Cone modes keep the paper's
+// s = 2 ceil(r_ddot / r_dot) + 1 when it is larger (Sec. 3.2).
+hp_status derive_window(const hp_camera &c, const hp_config &cfg, float r, int *h_out, float *rdd_out)
+{
+    const double fx = c.fx, fy = c.fy, cx = c.cx, cy = c.cy;
+    const double ax = std::fmax(std::fabs(0.5 - cx), std::fabs(((double)c.width - 0.5) - cx)) / fx;
+    const double ay = std::fmax(std::fabs(0.5 - cy), std::fabs(((double)c.height - 0.5) - cy)) / fy;
+    const double q = ax * ax + ay * ay;
+    const double cosm = 1.0 / std::sqrt(1.0 + q);
+    const double sinm = std::sqrt(q / (1.0 + q));
+    double lim_x, lim_y, rdd = 0.0, rho = 0.0;
+    if (cfg.radius_mode == HP_RADIUS_FIXED) {
+        const double rr = r;
+        if (!(rr > 0)) return HP_ERR_INVALID_ARG;
+        double zlo = (double)c.t_near * cosm - rr * sinm;
+        if (zlo < (double)c.z_near) zlo = (double)c.z_near;
+        lim_x = fx * rr * std::sqrt(1.0 + ax * ax) / zlo;
+        lim_y = fy * rr * std::sqrt(1.0 + ay * ay) / zlo;
+    } else {
+        const double rdot = std::sqrt(1.0 / ((3.14159265358979323846 * fx) * fy));
+        if (cfg.rho > 0) {
+            rho = cfg.rho;
+            rdd = rho * rdot;
+        } else {
+            // r_min at t_near on the central ray equals the given radius
+            const double rr = r, tn = c.t_near;
+            if (!(rr > 0) || !(tn > rr)) return HP_ERR_INVALID_ARG;
+            rdd = (cfg.radius_mode == HP_RADIUS_CONE) ? rr / std::sqrt(tn * tn - rr * rr) : rr / tn;
+            rho = rdd / rdot;
+        }
+        const double den = cosm - rdd * sinm;
+        if (!(den > 0)) return HP_ERR_INVALID_ARG;
+        lim_x = fx * rdd * std::sqrt(1.0 + ax * ax) / den;
+        lim_y = fy * rdd * std::sqrt(1.0 + ay * ay) / den;
+    }
+    const double lim = std::fmax(lim_x, lim_y) * (1.0 + 1e-3) + 1e-3;
+    if (!(lim < (double)kHMax)) return HP_ERR_INVALID_ARG;
+    int h = (int)std::floor(lim + 0.5);
+    if (cfg.radius_mode != HP_RADIUS_FIXED) {
+        const int hp_paper = (int)std::ceil(rho);
+        if (hp_paper > h) h = hp_paper;
+    }
+    if (cfg.window_h > 0) h = cfg.window_h;
+    if (h > kHMax) return HP_ERR_INVALID_ARG;
+    *h_out = h;
+    *rdd_out = (float)rdd;
+    return HP_OK;
+}
+
+size_t table_region_bytes(int64_t N, int64_t P)
+{
+    size_t o = 0;
+    o += al(256);                                            // tickets
+    o += al(4 * (size_t)(P + 1));                            // cnt
+    o += al(4 * (size_t)(P + 1));                            // start
+    o += al(8 * (size_t)N);                                  // keyrank
+    o += al(16 * (size_t)N);                                 // spts
+    o += al(8 * (size_t)div_up(P + 1, kScanTile));           // scan flags
+    return o;
+}
+
+size_t search_region_bytes(int64_t R) { return al(256) + al(8 * (size_t)div_up(R > 0 ? R : 1, kRaysPerCta)); }
+
+size_t render_region_bytes(int64_t cap) { return al(16 * (size_t)(cap > 0 ? cap : 1)); }
+
+// Region i of the workspace: 0 table, 1 search, 2 render.
+hp_status region(hp_ctx *ctx, int i, size_t bytes, char **out)
+{
+    if (ctx->ws) {
+        size_t off = 0;
+        if (i >= 1) off += ctx->table_bytes;
+        if (i >= 2) off += ctx->search_bytes;
+        if (off + bytes > ctx->ws_bytes) return HP_ERR_NO_MEMORY;
+        *out = ctx->ws + off;
+        return HP_OK;
+    }
+    if (ctx->own_bytes[i] < bytes) {
+        if (ctx->own[i]) cudaFree(ctx->own[i]);
+        ctx->own[i] = nullptr;
+        ctx->own_bytes[i] = 0;
+        void *p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return HP_ERR_NO_MEMORY;
+        }
+        ctx->own[i] = static_cast<char *>(p);
+        ctx->own_bytes[i] = bytes;
+    }
+    *out = ctx->own[i];
+    return HP_OK;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+const char *hp_status_string(hp_status s)
+{
+    switch (s) {
+    case HP_OK: return "ok";
+    case HP_ERR_INVALID_ARG: return "invalid argument";
+    case HP_ERR_CUDA: return "CUDA error";
+    case HP_ERR_OVERFLOW: return "sample capacity overflow";
+    case HP_ERR_TIMEOUT: return "bounded wait timed out";
+    case HP_ERR_NOT_BUILT: return "table or samples not built";
+    case HP_ERR_NO_MEMORY: return "workspace too small or allocation failed";
+    case HP_ERR_BAD_RAY: return "ray pixel out of range";
+    }
+    return "unknown status";
+}
+
+int32_t hp_version(void) { return 10000; }
+
+hp_status hp_create(hp_ctx **out, const hp_config *cfg)
+{
+    if (!out) return HP_ERR_INVALID_ARG;
+    *out = nullptr;
+    hp_status s = check_config(cfg);
+    if (s != HP_OK) return s;
+    hp_ctx *ctx = new (std::nothrow) hp_ctx();
+    if (!ctx) return HP_ERR_NO_MEMORY;
+    ctx->cfg = *cfg;
+    if (cudaGetDevice(&ctx->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return HP_ERR_CUDA;
+    }
+    void *p = nullptr;
+    if (cudaMalloc(&p, 64) != cudaSuccess || cudaMemset(p, 0, 64) != cudaSuccess) {
+        cudaGetLastError();
+        if (p) cudaFree(p);
+        delete ctx;
+        return HP_ERR_CUDA;
+    }
+    ctx->d_err = static_cast<ErrWord *>(p);
+    *out = ctx;
+    return HP_OK;
+}
+
+static void prof_release(Prof &p)
+{
+    if (p.ev) {
+        for (int i = 0; i < 2 * p.cap; ++i) cudaEventDestroy(p.ev[i]);
+        delete[] p.ev;
+    }
+    delete[] p.kid;
+    p = Prof();
+}
+
+hp_status hp_profile_start(hp_ctx *ctx, int32_t max_launches)
+{
+    if (!ctx || max_launches < 1 || max_launches > (1 << 20)) return HP_ERR_INVALID_ARG;
+    prof_release(ctx->prof);
+    Prof &p = ctx->prof;
+    p.ev = new (std::nothrow) cudaEvent_t[2 * (size_t)max_launches];
+    p.kid = new (std::nothrow) int[max_launches];
+    if (!p.ev || !p.kid) {
+        delete[] p.ev;
+        delete[] p.kid;
+        p = Prof();
+        return HP_ERR_NO_MEMORY;
+    }
+    for (int i = 0; i < 2 * max_launches; ++i) {
+        if (cudaEventCreate(&p.ev[i]) != cudaSuccess) {
+            cudaGetLastError();
+            p.cap = i / 2;
+            prof_release(p);
+            return HP_ERR_CUDA;
+        }
+    }
+    p.cap = max_launches;
+    p.n = 0;
+    p.on = true;
+    return HP_OK;
+}
+
+hp_status hp_profile_stop(hp_ctx *ctx, double *ms, int32_t *launches)
+{
+    if (!ctx) return HP_ERR_INVALID_ARG;
+    Prof &p = ctx->prof;
+    double acc[KID_COUNT] = {0};
+    int32_t cnt[KID_COUNT] = {0};
+    hp_status s = HP_OK;
+    for (int i = 0; i < p.n; ++i) {
+        float t = 0.f;
+        if (cudaEventSynchronize(p.ev[2 * i + 1]) != cudaSuccess ||
+            cudaEventElapsedTime(&t, p.ev[2 * i], p.ev[2 * i + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            s = HP_ERR_CUDA;
+            break;
+        }
+        acc[p.kid[i]] += t;
+        cnt[p.kid[i]] += 1;
+    }
+    for (int k = 0; k < KID_COUNT; ++k) {
+        if (ms) ms[k] = acc[k];
+        if (launches) launches[k] = cnt[k];
+    }
+    prof_release(p);
+    return s;
+}
+
+const char *hp_profile_kernel_name(int32_t id)
+{
+    static const char *names[KID_COUNT] = {"k_project_count", "k_scan", "k_scatter", "k_bucket_sort",
+                                           "k_search_select", "k_aggregate_decode", "k_composite"};
+    return (id >= 0 && id < KID_COUNT) ? names[id] : "unknown";
+}
+
+hp_status hp_destroy(hp_ctx *ctx)
+{
+    if (!ctx) return HP_ERR_INVALID_ARG;
+    prof_release(ctx->prof);
+    for (int i = 0; i < 3; ++i)
+        if (ctx->own[i]) cudaFree(ctx->own[i]);
+    if (ctx->d_err) cudaFree(ctx->d_err);
+    delete ctx;
+    return HP_OK;
+}
+
+hp_status hp_workspace_size(const hp_config *cfg, const hp_camera *cam, float r, int64_t n_points, int64_t n_rays,
+                            int32_t n_samples, size_t *bytes)
+{
+    hp_status s;
+    if (!bytes || n_points < 0 || n_rays < 0 || n_samples < 1 || n_samples > kMaxSamples) return HP_ERR_INVALID_ARG;
+    if ((s = check_config(cfg)) != HP_OK || (s = check_camera(cam)) != HP_OK) return s;
+    int h;
+    float rdd;
+    if ((s = derive_window(*cam, *cfg, r, &h, &rdd)) != HP_OK) return s;
+    const int64_t P = (int64_t)(cam->width + 2 * h) * (cam->height + 2 * h);
+    *bytes = table_region_bytes(n_points, P) + search_region_bytes(n_rays) + render_region_bytes(n_rays * n_samples);
+    return HP_OK;
+}
+
+hp_status hp_window(const hp_config *cfg, const hp_camera *cam, float r, int32_t *h_out, float *rdd_out)
+{
+    hp_status s;
+    if (!h_out || !rdd_out) return HP_ERR_INVALID_ARG;
+    if ((s = check_config(cfg)) != HP_OK || (s = check_camera(cam)) != HP_OK) return s;
+    int h;
+    float rdd;
+    if ((s = derive_window(*cam, *cfg, r, &h, &rdd)) != HP_OK) return s;
+    *h_out = h;
+    *rdd_out = rdd;
+    return HP_OK;
+}
+
+hp_status hp_set_workspace(hp_ctx *ctx, void *d_ptr, size_t bytes)
+{
+    if (!ctx || (d_ptr && ((uintptr_t)d_ptr % kAlign) != 0)) return HP_ERR_INVALID_ARG;
+    ctx->ws = static_cast<char *>(d_ptr);
+    ctx->ws_bytes = d_ptr ? bytes : 0;
+    ctx->built = false;
+    ctx->searched = false;
+    return HP_OK;
+}
+
+hp_status hp_debug_fault(hp_ctx *ctx, int32_t skip_tile, int32_t spin_limit)
+{
+    if (!ctx || spin_limit < 0) return HP_ERR_INVALID_ARG;
+    ctx->skip_tile = skip_tile;
+    ctx->spin_limit = spin_limit > 0 ? (uint32_t)spin_limit : kSpinLimitDefault;
+    return HP_OK;
+}
+
+hp_status hp_build_table(hp_ctx *ctx, const float *d_points, int64_t n_points, const hp_camera *cam, float r,
+                         void *stream)
+{
+    hp_status s;
+    if (!ctx || n_points < 0 || n_points > 0x7fffffffLL || (n_points > 0 && !d_points)) return HP_ERR_INVALID_ARG;
+    if ((s = check_camera(cam)) != HP_OK) return s;
+    if (!is_finite32(r)) return HP_ERR_INVALID_ARG;
+    int h;
+    float rdd;
+    if ((s = derive_window(*cam, ctx->cfg, r, &h, &rdd)) != HP_OK) return s;
+    const int Wp = cam->width + 2 * h, Hp = cam->height + 2 * h;
+    const int64_t P = (int64_t)Wp * Hp;
+    if (P + 1 > 0xffffffffLL) return HP_ERR_INVALID_ARG;
+    ctx->built = false;
+    ctx->searched = false;
+    ctx->table_bytes = table_region_bytes(n_points, P);
+    char *base = nullptr;
+    if ((s = region(ctx, 0, ctx->table_bytes, &base)) != HP_OK) return s;
+    size_t o = 0;
+    ctx->scan_ticket = reinterpret_cast<uint32_t *>(base + o); o += al(256);
+    ctx->cnt = reinterpret_cast<uint32_t *>(base + o);         o += al(4 * (size_t)(P + 1));
+    ctx->start = reinterpret_cast<uint32_t *>(base + o);       o += al(4 * (size_t)(P + 1));
+    ctx->keyrank = reinterpret_cast<uint2 *>(base + o);        o += al(8 * (size_t)n_points);
+    ctx->spts = reinterpret_cast<float4 *>(base + o);          o += al(16 * (size_t)n_points);
+    ctx->scan_flags = reinterpret_cast<uint64_t *>(base + o);
+
+    Cam c{};
+    std::memcpy(c.R, cam->R, sizeof(c.R));
+    std::memcpy(c.t, cam->t, sizeof(c.t));
+    c.fx = cam->fx; c.fy = cam->fy; c.cx = cam->cx; c.cy = cam->cy;
+    c.t_near = cam->t_near; c.t_far = cam->t_far; c.z_near = cam->z_near;
+    c.width = cam->width; c.height = cam->height;
+    ctx->cam = c;
+    ctx->h = h; ctx->Wp = Wp; ctx->Hp = Hp; ctx->P = P; ctx->N = n_points;
+    ctx->r = r; ctx->rdd = rdd;
+
+    BuildArgs a{};
+    a.pts = d_points; a.N = n_points; a.cam = c; a.h = h; a.P = P;
+    a.cnt = ctx->cnt; a.start = ctx->start; a.keyrank = ctx->keyrank; a.spts = ctx->spts;
+    a.scan_flags = ctx->scan_flags; a.scan_ticket = ctx->scan_ticket; a.err = ctx->d_err;
+    a.spin_limit = ctx->spin_limit; a.skip_tile = ctx->skip_tile;
+    if (launch_build(a, static_cast<cudaStream_t>(stream), &ctx->prof) != cudaSuccess) {
+        cudaGetLastError();
+        return HP_ERR_CUDA;
+    }
+    ctx->built = true;
+    return HP_OK;
+}
+
+hp_status hp_table_info(const hp_ctx *ctx, hp_table *out)
+{
+    if (!ctx || !out) return HP_ERR_INVALID_ARG;
+    if (!ctx->built) return HP_ERR_NOT_BUILT;
+    out->h = ctx->h;
+    out->padded_width = ctx->Wp;
+    out->padded_height = ctx->Hp;
+    out->n_buckets = ctx->P;
+    out->r_ddot = ctx->rdd;
+    out->d_start = ctx->start;
+    out->d_points = reinterpret_cast<const float *>(ctx->spts);
+    return HP_OK;
+}
+
+hp_status hp_table_copy(const hp_ctx *ctx, uint32_t *d_start, float *d_points, void *stream)
+{
+    if (!ctx || !d_start || (ctx->N > 0 && !d_points)) return HP_ERR_INVALID_ARG;
+    if (!ctx->built) return HP_ERR_NOT_BUILT;
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(d_start, ctx->start, 4 * (size_t)(ctx->P + 1), cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        (ctx->N > 0 &&
+         cudaMemcpyAsync(d_points, ctx->spts, 16 * (size_t)ctx->N, cudaMemcpyDeviceToDevice, st) != cudaSuccess)) {
+        cudaGetLastError();
+        return HP_ERR_CUDA;
+    }
+    return HP_OK;
+}
+
+hp_status hp_search_sample(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n_rays, int32_t K, int32_t n_samples,
+                           const hp_samples *out, void *stream)
+{
+    if (!ctx || !out) return HP_ERR_INVALID_ARG;
+    if (!ctx->built) return HP_ERR_NOT_BUILT;
+    if (n_rays < 0 || n_rays > 0x7fffffffLL || K < 1 || K > kMaxK || n_samples < 1 || n_samples > kMaxSamples)
+        return HP_ERR_INVALID_ARG;
+    if (!d_ray_pixels && n_rays != 0 && n_rays != (int64_t)ctx->cam.width * ctx->cam.height)
+        return HP_ERR_INVALID_ARG;
+    if (!out->sample_offset || out->capacity < 0) return HP_ERR_INVALID_ARG;
+    if (n_rays > 0 && (!out->n_s || !out->primary || !out->cand_count)) return HP_ERR_INVALID_ARG;
+    if (out->capacity > 0 && (!out->t || !out->ray || !out->src || !out->delta || !out->nbr || !out->nbr_dist))
+        return HP_ERR_INVALID_ARG;
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    ctx->searched = false;
+    ctx->search_bytes = search_region_bytes(n_rays);
+    char *base = nullptr;
+    hp_status s;
+    if ((s = region(ctx, 1, ctx->search_bytes, &base)) != HP_OK) return s;
+    if (n_rays == 0) {
+        if (cudaMemsetAsync(out->sample_offset, 0, sizeof(int64_t), st) != cudaSuccess) {
+            cudaGetLastError();
+            return HP_ERR_CUDA;
+        }
+    } else {
+        SearchArgs a{};
+        a.cam = ctx->cam; a.mode = ctx->cfg.radius_mode; a.r = ctx->r; a.rdd = ctx->rdd; a.h = ctx->h;
+        a.Wp = ctx->Wp; a.gamma = ctx->cfg.gamma; a.beta2 = ctx->cfg.beta2; a.eps_w = ctx->cfg.eps_w;
+        a.gap_k = ctx->cfg.gap_k; a.cand_cap = ctx->cfg.cand_cap; a.K = K; a.n_max = n_samples;
+        a.start = ctx->start; a.spts = ctx->spts; a.rays = d_ray_pixels; a.R = n_rays;
+        a.n_s = out->n_s; a.primary = out->primary; a.cand_count = out->cand_count;
+        a.sample_offset = out->sample_offset; a.t = out->t; a.ray = out->ray; a.src = out->src;
+        a.delta = out->delta; a.nbr = out->nbr; a.nbr_dist = out->nbr_dist; a.capacity = out->capacity;
+        a.ticket = reinterpret_cast<uint32_t *>(base);
+        a.flags = reinterpret_cast<uint64_t *>(base + al(256));
+        a.err = ctx->d_err;
+        a.spin_limit = ctx->spin_limit;
+        if (launch_search(a, st, &ctx->prof) != cudaSuccess) {
+            cudaGetLastError();
+            return HP_ERR_CUDA;
+        }
+    }
+    ctx->R = n_rays;
+    ctx->K = K;
+    ctx->n_max = n_samples;
+    ctx->searched = true;
+    return HP_OK;
+}
+
+hp_status hp_aggregate_render(hp_ctx *ctx, const hp_samples *smp, int64_t n_rays, const float *d_feats, int32_t F,
+                              const hp_mlp *mlp, float *d_rgb, float *d_wsum, void *stream)
+{
+    if (!ctx || !smp || !mlp) return HP_ERR_INVALID_ARG;
+    if (!ctx->built || !ctx->searched || n_rays != ctx->R) return HP_ERR_NOT_BUILT;
+    if (!(F == 4 || F == 8 || F == 16 || F == 32 || F == 64 || F == 128)) return HP_ERR_INVALID_ARG;
+    if (mlp->n_layers < 1 || mlp->n_layers > HP_MLP_MAX_LAYERS || !mlp->d_params) return HP_ERR_INVALID_ARG;
+    if (mlp->dims[0] != F || mlp->dims[mlp->n_layers] != 4) return HP_ERR_INVALID_ARG;
+    int64_t n_par = 0;
+    for (int l = 0; l < mlp->n_layers; ++l) {
+        const int fo = mlp->dims[l + 1];
+        if (l + 1 < mlp->n_layers && !(fo == 16 || fo == 32 || fo == 64 || fo == 128)) return HP_ERR_INVALID_ARG;
+        n_par += (int64_t)mlp->dims[l] * fo + fo;
+    }
+    if (n_par > 40960) return HP_ERR_INVALID_ARG;
+    if (n_rays > 0 && ((ctx->N > 0 && !d_feats) || !d_rgb || !d_wsum || !aligned16(d_feats)))
+        return HP_ERR_INVALID_ARG;
+    if (n_rays == 0) return HP_OK;
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *base = nullptr;
+    hp_status s;
+    if ((s = region(ctx, 2, render_region_bytes(smp->capacity), &base)) != HP_OK) return s;
+    RenderArgs a{};
+    a.n_s = smp->n_s; a.sample_offset = smp->sample_offset; a.delta = smp->delta; a.nbr = smp->nbr;
+    a.nbr_dist = smp->nbr_dist; a.capacity = smp->capacity; a.R = n_rays; a.K = ctx->K;
+    a.feats = d_feats; a.F = F; a.mlp = mlp->d_params; a.n_layers = mlp->n_layers;
+    for (int l = 0; l <= mlp->n_layers; ++l) a.dims[l] = mlp->dims[l];
+    a.eps_d = ctx->cfg.eps_d; a.bg_mode = ctx->cfg.bg_mode;
+    a.sample_out = reinterpret_cast<float4 *>(base);
+    a.rgb = d_rgb; a.wsum = d_wsum; a.num_sms = ctx->num_sms;
+    if (render_smem_bytes(a) > 227 * 1024) return HP_ERR_INVALID_ARG;
+    if (launch_render(a, st, &ctx->prof) != cudaSuccess) {
+        cudaGetLastError();
+        return HP_ERR_CUDA;
+    }
+    return HP_OK;
+}
+
+hp_status hp_get_status(hp_ctx *ctx, void *stream, int32_t *dev_status, int64_t *detail)
+{
+    if (!ctx) return HP_ERR_INVALID_ARG;
+    ErrWord w{};
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(st) != cudaSuccess ||
+        cudaMemcpy(&w, ctx->d_err, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemset(ctx->d_err, 0, sizeof(w)) != cudaSuccess) {
+        cudaGetLastError();
+        return HP_ERR_CUDA;
+    }
+    if (dev_status) *dev_status = w.status;
+    if (detail) *detail = w.detail;
+    return HP_OK;
+}
+
+}  // extern "C"

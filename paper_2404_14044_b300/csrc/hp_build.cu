@@ -1,0 +1,174 @@
+// Table build (Sec. 3.2, "Accelerated structure construction"): every visible
+// point is projected to its pixel; all points of a pixel are kept (no
+// z-buffer); the point list is reordered so that each pixel's points are
+// contiguous, and the table holds, per pixel key, the start of its run (the
+// count is the difference of consecutive starts).
+//
+// K1 k_project_count  camera transform + key, warp-aggregated atomic count;
+//                     the atomic's return value is the point's slot in its run
+// K2 k_scan           exclusive prefix sum of the counts (decoupled look-back)
+// K3 k_scatter        each point written to start[key] + slot as float4
+//                     (camera x, y, z, id bits)
+// K4 k_bucket_sort    each run ordered by (z, x, y, id), which makes the list
+//                     independent of the atomics' order and of the input order
+#include "hp_kernels.cuh"
+
+namespace hp {
+
+__global__ void __launch_bounds__(256) k_project_count(const float *__restrict__ pts, int64_t N, Cam cam, int h,
+                                                       uint32_t *__restrict__ cnt, uint2 *__restrict__ keyrank)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool in = i < N;
+    uint32_t key = kNoKey;
+    if (in) {
+        float3 X = cam_point(cam, __ldg(pts + 3 * i), __ldg(pts + 3 * i + 1), __ldg(pts + 3 * i + 2));
+        key = pixel_key(cam, h, X);
+    }
+    const bool valid = in && key != kNoKey;
+    const unsigned active = __ballot_sync(0xffffffffu, valid);
+    uint32_t rank = 0;
+    if (valid) {
+        // lanes that hit the same bucket share one atomic
+        const unsigned grp = __match_any_sync(active, key);
+        const int leader = __ffs(grp) - 1;
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(cnt + key, (uint32_t)__popc(grp));
+        base = __shfl_sync(grp, base, leader);
+        rank = base + (uint32_t)__popc(grp & ((1u << lane) - 1u));
+    }
+    if (in) keyrank[i] = make_uint2(key, rank);
+}
+
+// Exclusive scan of n uint32 values; tile = kScanTile entries.
+__global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
+                                                      int64_t n, uint64_t *flags, uint32_t *ticket, ErrWord *err,
+                                                      uint32_t spin_limit, int32_t skip_tile)
+{
+    __shared__ int64_t s_tile;
+    __shared__ int64_t s_prefix;
+    __shared__ int s_warp[kScanThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t base = tile * kScanTile + (int64_t)tid * kScanItems;
+    uint32_t v[kScanItems];
+    if (base + kScanItems <= n) {
+        const uint4 a = *reinterpret_cast<const uint4 *>(in + base);
+        const uint4 b = *reinterpret_cast<const uint4 *>(in + base + 4);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) v[k] = (base + k < n) ? in[base + k] : 0u;
+    }
+    int tsum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) tsum += (int)v[k];
+    const int incl = warp_incl_scan(tsum);
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < kScanThreads / 32 ? s_warp[lane] : 0;
+        int wi = warp_incl_scan(w);
+        if (lane < kScanThreads / 32) s_warp[lane] = wi - w;      // exclusive warp offsets
+        if (lane == kScanThreads / 32 - 1) {
+            const int64_t agg = wi;
+            s_prefix = lookback_prefix(flags, tile, agg, err, spin_limit, tile != skip_tile);
+        }
+    }
+    __syncthreads();
+    uint32_t run = (uint32_t)(s_prefix + s_warp[warp] + (incl - tsum));
+    uint32_t o[kScanItems];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        o[k] = run;
+        run += v[k];
+    }
+    if (base + kScanItems <= n) {
+        *reinterpret_cast<uint4 *>(out + base) = make_uint4(o[0], o[1], o[2], o[3]);
+        *reinterpret_cast<uint4 *>(out + base + 4) = make_uint4(o[4], o[5], o[6], o[7]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k)
+            if (base + k < n) out[base + k] = o[k];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_scatter(const float *__restrict__ pts, int64_t N, Cam cam,
+                                                 const uint2 *__restrict__ keyrank,
+                                                 const uint32_t *__restrict__ start, float4 *__restrict__ spts)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const uint2 kr = keyrank[i];
+    if (kr.x == kNoKey) return;
+    // the same float32 sequence as K1, so the stored position is the one keyed
+    float3 X = cam_point(cam, __ldg(pts + 3 * i), __ldg(pts + 3 * i + 1), __ldg(pts + 3 * i + 2));
+    spts[start[kr.x] + kr.y] = make_float4(X.x, X.y, X.z, __int_as_float((int)i));
+}
+
+__device__ __forceinline__ bool pt_less(const float4 &a, const float4 &b)
+{
+    if (a.z != b.z) return a.z < b.z;
+    if (a.x != b.x) return a.x < b.x;
+    if (a.y != b.y) return a.y < b.y;
+    return __float_as_int(a.w) < __float_as_int(b.w);
+}
+
+// One thread per bucket: insertion sort of the bucket's run (runs are short).
+__global__ void __launch_bounds__(256) k_bucket_sort(const uint32_t *__restrict__ start, int64_t P,
+                                                     float4 *__restrict__ spts)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P) return;
+    const uint32_t a = start[k], b = start[k + 1];
+    if (b - a < 2) return;
+    for (uint32_t i = a + 1; i < b; ++i) {
+        const float4 x = spts[i];
+        uint32_t j = i;
+        while (j > a) {
+            const float4 y = spts[j - 1];
+            if (!pt_less(x, y)) break;
+            spts[j] = y;
+            --j;
+        }
+        spts[j] = x;
+    }
+}
+
+cudaError_t launch_build(const BuildArgs &a, cudaStream_t st, Prof *prof)
+{
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(a.cnt, 0, sizeof(uint32_t) * (size_t)(a.P + 1), st)) != cudaSuccess) return e;
+    const int64_t n_scan = a.P + 1;
+    const int64_t scan_tiles = div_up(n_scan, kScanTile);
+    if ((e = cudaMemsetAsync(a.scan_flags, 0, sizeof(uint64_t) * (size_t)scan_tiles, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(a.scan_ticket, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+    if (a.N > 0) {
+        prof_begin(prof, st, KID_PROJECT);
+        k_project_count<<<(unsigned)div_up(a.N, 256), 256, 0, st>>>(a.pts, a.N, a.cam, a.h, a.cnt, a.keyrank);
+        prof_end(prof, st);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    prof_begin(prof, st, KID_SCAN);
+    k_scan<<<(unsigned)scan_tiles, kScanThreads, 0, st>>>(a.cnt, a.start, n_scan, a.scan_flags, a.scan_ticket,
+                                                          a.err, a.spin_limit, a.skip_tile);
+    prof_end(prof, st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (a.N > 0) {
+        prof_begin(prof, st, KID_SCATTER);
+        k_scatter<<<(unsigned)div_up(a.N, 256), 256, 0, st>>>(a.pts, a.N, a.cam, a.keyrank, a.start, a.spts);
+        prof_end(prof, st);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        prof_begin(prof, st, KID_SORT);
+        k_bucket_sort<<<(unsigned)div_up(a.P, 256), 256, 0, st>>>(a.start, a.P, a.spts);
+        prof_end(prof, st);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace hp

@@ -1,0 +1,113 @@
+// Launch interfaces between the C-ABI layer and the kernels.
+#pragma once
+
+#include "hp_common.cuh"
+
+namespace hp {
+
+// Kernel ids of the per-kernel profiler (hp_profile_*).
+enum KernelId { KID_PROJECT = 0, KID_SCAN, KID_SCATTER, KID_SORT, KID_SEARCH, KID_DECODE, KID_COMPOSITE, KID_COUNT };
+
+// Optional CUDA-event pairs around each launch, on the launching stream.
+struct Prof {
+    bool on = false;
+    int cap = 0;
+    int n = 0;
+    cudaEvent_t *ev = nullptr;   // 2 * cap
+    int *kid = nullptr;          // cap
+};
+
+inline void prof_begin(Prof *p, cudaStream_t st, int kid)
+{
+    if (p && p->on && p->n < p->cap) {
+        p->kid[p->n] = kid;
+        cudaEventRecord(p->ev[2 * p->n], st);
+    }
+}
+
+inline void prof_end(Prof *p, cudaStream_t st)
+{
+    if (p && p->on && p->n < p->cap) {
+        cudaEventRecord(p->ev[2 * p->n + 1], st);
+        ++p->n;
+    }
+}
+
+struct BuildArgs {
+    const float *pts;
+    int64_t N;
+    Cam cam;
+    int h;
+    int64_t P;              // buckets = (W+2h)(H+2h)
+    uint32_t *cnt;          // [P+1]
+    uint32_t *start;        // [P+1]
+    uint2 *keyrank;         // [N]
+    float4 *spts;           // [N]
+    uint64_t *scan_flags;   // [ceil((P+1)/kScanTile)]
+    uint32_t *scan_ticket;
+    ErrWord *err;
+    uint32_t spin_limit;
+    int32_t skip_tile;
+};
+
+struct SearchArgs {
+    Cam cam;
+    int mode;
+    float r;
+    float rdd;
+    int h;
+    int Wp;
+    float gamma, beta2, eps_w, gap_k;
+    int cand_cap;
+    int K;
+    int n_max;
+    const uint32_t *start;
+    const float4 *spts;
+    const int32_t *rays;     // NULL: ray i is pixel i
+    int64_t R;
+    int32_t *n_s;
+    int32_t *primary;
+    int32_t *cand_count;
+    int64_t *sample_offset;
+    float *t;
+    int32_t *ray;
+    int32_t *src;
+    float *delta;
+    int32_t *nbr;
+    float *nbr_dist;
+    int64_t capacity;
+    uint64_t *flags;         // [ceil(R / kRaysPerCta)]
+    uint32_t *ticket;
+    ErrWord *err;
+    uint32_t spin_limit;
+};
+
+struct RenderArgs {
+    const int32_t *n_s;
+    const int64_t *sample_offset;
+    const float *delta;
+    const int32_t *nbr;
+    const float *nbr_dist;
+    int64_t capacity;
+    int64_t R;
+    int K;
+    const float *feats;
+    int F;
+    const float *mlp;        // packed W0,b0,W1,b1,... (global)
+    int n_layers;
+    int dims[HP_MLP_MAX_LAYERS + 1];
+    float eps_d;
+    int bg_mode;
+    float4 *sample_out;      // [capacity] (sigma, r, g, b)
+    float *rgb;              // [R*3]
+    float *wsum;             // [R]
+    int num_sms;
+};
+
+cudaError_t launch_build(const BuildArgs &a, cudaStream_t st, Prof *prof);
+size_t search_smem_bytes(int K, int n_max);
+cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof);
+size_t render_smem_bytes(const RenderArgs &a);
+cudaError_t launch_render(const RenderArgs &a, cudaStream_t st, Prof *prof);
+
+}  // namespace hp

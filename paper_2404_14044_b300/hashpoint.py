@@ -1,0 +1,321 @@
+"""Python binding of the C-ABI library ``libhashpoint.so`` (argument
+marshalling only: every step of the hot path runs in the library's CUDA
+kernels).  PyTorch provides device memory and streams.
+
+The library must have been built (``python -m paper_2404_14044_b300.build``);
+importing the binding without it raises ``RuntimeError`` -- there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+from typing import Dict, Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhashpoint.so")
+
+HP_OK, HP_ERR_INVALID_ARG, HP_ERR_CUDA, HP_ERR_OVERFLOW, HP_ERR_TIMEOUT = 0, 1, 2, 3, 4
+HP_ERR_NOT_BUILT, HP_ERR_NO_MEMORY, HP_ERR_BAD_RAY = 5, 6, 7
+MLP_MAX_LAYERS = 8
+
+# every symbol include/hashpoint.h declares
+SYMBOLS = ("hp_create", "hp_destroy", "hp_workspace_size", "hp_window", "hp_set_workspace", "hp_build_table",
+           "hp_table_info", "hp_table_copy", "hp_search_sample", "hp_aggregate_render", "hp_get_status",
+           "hp_debug_fault", "hp_profile_start", "hp_profile_stop", "hp_profile_kernel_name",
+           "hp_status_string", "hp_version")
+PROF_KERNELS = 7
+
+
+class HPError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {status_string(code)} ({code})")
+        self.code = code
+
+
+class Camera(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("R", C.c_float * 9), ("t", C.c_float * 3),
+                ("t_near", C.c_float), ("t_far", C.c_float), ("z_near", C.c_float)]
+
+
+class Config(C.Structure):
+    _fields_ = [("radius_mode", C.c_int32), ("rho", C.c_float), ("gamma", C.c_float), ("beta2", C.c_float),
+                ("eps_w", C.c_float), ("gap_k", C.c_float), ("eps_d", C.c_float), ("cand_cap", C.c_int32),
+                ("bg_mode", C.c_int32), ("window_h", C.c_int32)]
+
+
+class Samples(C.Structure):
+    _fields_ = [("n_s", C.c_void_p), ("primary", C.c_void_p), ("cand_count", C.c_void_p),
+                ("sample_offset", C.c_void_p), ("t", C.c_void_p), ("ray", C.c_void_p), ("src", C.c_void_p),
+                ("delta", C.c_void_p), ("nbr", C.c_void_p), ("nbr_dist", C.c_void_p), ("capacity", C.c_int64)]
+
+
+class Mlp(C.Structure):
+    _fields_ = [("n_layers", C.c_int32), ("dims", C.c_int32 * (MLP_MAX_LAYERS + 1)), ("d_params", C.c_void_p)]
+
+
+class Table(C.Structure):
+    _fields_ = [("h", C.c_int32), ("padded_width", C.c_int32), ("padded_height", C.c_int32),
+                ("n_buckets", C.c_int64), ("r_ddot", C.c_float), ("d_start", C.c_void_p), ("d_points", C.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libhashpoint.so (raises RuntimeError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2404_14044_b300.build`")
+        L = C.CDLL(LIB_PATH)
+        vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
+        L.hp_create.argtypes = [C.POINTER(vp), C.POINTER(Config)]
+        L.hp_destroy.argtypes = [vp]
+        L.hp_workspace_size.argtypes = [C.POINTER(Config), C.POINTER(Camera), C.c_float, i64, i64, i32,
+                                        C.POINTER(C.c_size_t)]
+        L.hp_window.argtypes = [C.POINTER(Config), C.POINTER(Camera), C.c_float, C.POINTER(i32), C.POINTER(C.c_float)]
+        L.hp_set_workspace.argtypes = [vp, vp, C.c_size_t]
+        L.hp_build_table.argtypes = [vp, vp, i64, C.POINTER(Camera), C.c_float, vp]
+        L.hp_table_info.argtypes = [vp, C.POINTER(Table)]
+        L.hp_table_copy.argtypes = [vp, vp, vp, vp]
+        L.hp_search_sample.argtypes = [vp, vp, i64, i32, i32, C.POINTER(Samples), vp]
+        L.hp_aggregate_render.argtypes = [vp, C.POINTER(Samples), i64, vp, i32, C.POINTER(Mlp), vp, vp, vp]
+        L.hp_get_status.argtypes = [vp, vp, C.POINTER(i32), C.POINTER(i64)]
+        L.hp_debug_fault.argtypes = [vp, i32, i32]
+        L.hp_profile_start.argtypes = [vp, i32]
+        L.hp_profile_stop.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(i32)]
+        L.hp_profile_kernel_name.argtypes = [i32]
+        L.hp_profile_kernel_name.restype = C.c_char_p
+        L.hp_status_string.argtypes = [i32]
+        L.hp_status_string.restype = C.c_char_p
+        L.hp_version.restype = i32
+        for name in SYMBOLS:
+            if name not in ("hp_status_string", "hp_version", "hp_profile_kernel_name"):
+                getattr(L, name).restype = i32
+        _lib = L
+    return _lib
+
+
+def status_string(code: int) -> str:
+    return lib().hp_status_string(int(code)).decode()
+
+
+def window(params, camera):
+    """(h, r_ddot) of the search window (host-only call)."""
+    h, rdd = C.c_int32(), C.c_float()
+    _check(lib().hp_window(C.byref(config_struct(params)), C.byref(camera_struct(camera)), float(params.r),
+                           C.byref(h), C.byref(rdd)), "hp_window")
+    return h.value, rdd.value
+
+
+def workspace_size(params, camera, n_points: int, n_rays: int, n_samples: int) -> int:
+    n = C.c_size_t()
+    _check(lib().hp_workspace_size(C.byref(config_struct(params)), C.byref(camera_struct(camera)), float(params.r),
+                                   int(n_points), int(n_rays), int(n_samples), C.byref(n)), "hp_workspace_size")
+    return n.value
+
+
+def _check(rc: int, where: str):
+    if rc != HP_OK:
+        raise HPError(rc, where)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream: Optional[torch.cuda.Stream]):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def camera_struct(cam) -> Camera:
+    c = Camera()
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.R[:] = [float(v) for v in cam.R.reshape(-1)]
+    c.t[:] = [float(v) for v in cam.t.reshape(-1)]
+    c.t_near, c.t_far, c.z_near = float(cam.t_near), float(cam.t_far), float(cam.z_near)
+    return c
+
+
+def config_struct(p) -> Config:
+    c = Config()
+    c.radius_mode, c.rho = int(p.radius_mode), float(p.rho)
+    c.gamma, c.beta2, c.eps_w, c.gap_k, c.eps_d = float(p.gamma), float(p.beta2), float(p.eps_w), float(p.gap_k), float(p.eps_d)
+    c.cand_cap, c.bg_mode, c.window_h = int(p.cand_cap), int(p.bg_mode), int(p.window_h)
+    return c
+
+
+@dataclasses.dataclass
+class SampleBuffers:
+    """Device tensors of one hp_search_sample call (see hp_samples)."""
+
+    n_s: torch.Tensor
+    primary: torch.Tensor
+    cand_count: torch.Tensor
+    sample_offset: torch.Tensor
+    t: torch.Tensor
+    ray: torch.Tensor
+    src: torch.Tensor
+    delta: torch.Tensor
+    nbr: torch.Tensor
+    nbr_dist: torch.Tensor
+    K: int
+
+    @property
+    def capacity(self) -> int:
+        return self.t.shape[0]
+
+    def struct(self) -> Samples:
+        s = Samples()
+        for f in ("n_s", "primary", "cand_count", "sample_offset", "t", "ray", "src", "delta", "nbr", "nbr_dist"):
+            setattr(s, f, getattr(self, f).data_ptr())
+        s.capacity = self.capacity
+        return s
+
+    @staticmethod
+    def allocate(R: int, K: int, n_samples: int, device, capacity: Optional[int] = None) -> "SampleBuffers":
+        cap = R * n_samples if capacity is None else capacity
+        cap1 = max(cap, 1)
+        i32 = dict(dtype=torch.int32, device=device)
+        f32 = dict(dtype=torch.float32, device=device)
+        return SampleBuffers(
+            n_s=torch.empty(max(R, 1), **i32), primary=torch.empty(max(R, 1), **i32),
+            cand_count=torch.empty(max(R, 1), **i32),
+            sample_offset=torch.empty(R + 1, dtype=torch.int64, device=device),
+            t=torch.empty(cap1, **f32)[:cap], ray=torch.empty(cap1, **i32)[:cap], src=torch.empty(cap1, **i32)[:cap],
+            delta=torch.empty(cap1, **f32)[:cap], nbr=torch.empty(cap1 * K, **i32)[: cap * K].view(cap, K),
+            nbr_dist=torch.empty(cap1 * K, **f32)[: cap * K].view(cap, K), K=K)
+
+    def packed(self, R: int) -> Dict[str, torch.Tensor]:
+        """Host copies trimmed to the S samples written (syncs)."""
+        S = int(self.sample_offset[R].item())
+        S = min(S, self.capacity)
+        return dict(S=S, n_s=self.n_s[:R].cpu(), primary=self.primary[:R].cpu(), cand_count=self.cand_count[:R].cpu(),
+                    sample_offset=self.sample_offset.cpu(), t=self.t[:S].cpu(), ray=self.ray[:S].cpu(),
+                    src=self.src[:S].cpu(), delta=self.delta[:S].cpu(), nbr=self.nbr[:S].cpu(),
+                    nbr_dist=self.nbr_dist[:S].cpu())
+
+
+class HashPoint:
+    """One hot-path context (hp_ctx) on the current CUDA device."""
+
+    def __init__(self, params, device: Optional[torch.device] = None):
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.params = params
+        self._cfg = config_struct(params)
+        self._ctx = C.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib().hp_create(C.byref(self._ctx), C.byref(self._cfg)), "hp_create")
+        self._ws = None
+        self._cam = None
+        self.n_points = 0
+
+    def close(self):
+        if self._ctx:
+            lib().hp_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- workspace (torch-allocated)
+    def reserve(self, camera, r: float, n_points: int, n_rays: int, n_samples: int):
+        n = C.c_size_t()
+        _check(lib().hp_workspace_size(C.byref(self._cfg), C.byref(camera_struct(camera)), float(r), int(n_points),
+                                       int(n_rays), int(n_samples), C.byref(n)), "hp_workspace_size")
+        if self._ws is None or self._ws.numel() < n.value:
+            self._ws = torch.empty(n.value, dtype=torch.uint8, device=self.device)
+            _check(lib().hp_set_workspace(self._ctx, _ptr(self._ws), n.value), "hp_set_workspace")
+        return n.value
+
+    # -- the three stages
+    def build_table(self, points: torch.Tensor, camera, r: float, stream=None):
+        assert points.is_cuda and points.dtype == torch.float32 and points.is_contiguous() and points.shape[-1] == 3
+        self._cam = camera
+        self.n_points = points.shape[0]
+        _check(lib().hp_build_table(self._ctx, _ptr(points), points.shape[0], C.byref(camera_struct(camera)),
+                                    float(r), _stream(stream)), "hp_build_table")
+
+    def table_info(self) -> Table:
+        t = Table()
+        _check(lib().hp_table_info(self._ctx, C.byref(t)), "hp_table_info")
+        return t
+
+    def table(self, stream=None) -> Dict[str, torch.Tensor]:
+        info = self.table_info()
+        start = torch.empty(info.n_buckets + 1, dtype=torch.int32, device=self.device)
+        pts = torch.empty(max(self.n_points, 1), 4, dtype=torch.float32, device=self.device)
+        _check(lib().hp_table_copy(self._ctx, _ptr(start), _ptr(pts), _stream(stream)), "hp_table_copy")
+        return dict(h=info.h, padded_width=info.padded_width, padded_height=info.padded_height,
+                    r_ddot=info.r_ddot, start=start, points=pts[: self.n_points])
+
+    def search_sample(self, rays: Optional[torch.Tensor], K: int, n_samples: int,
+                      out: Optional[SampleBuffers] = None, stream=None) -> SampleBuffers:
+        if rays is not None:
+            assert rays.is_cuda and rays.dtype == torch.int32 and rays.is_contiguous()
+            R = rays.shape[0]
+        else:
+            R = self._cam.width * self._cam.height
+        if out is None:
+            out = SampleBuffers.allocate(R, K, n_samples, self.device)
+        s = out.struct()
+        _check(lib().hp_search_sample(self._ctx, _ptr(rays), R, int(K), int(n_samples), C.byref(s), _stream(stream)),
+               "hp_search_sample")
+        self._R = R
+        return out
+
+    def aggregate_render(self, samples: SampleBuffers, feats: torch.Tensor, mlp_dims: Sequence[int],
+                         mlp_params: torch.Tensor, rgb: Optional[torch.Tensor] = None,
+                         wsum: Optional[torch.Tensor] = None, stream=None):
+        assert feats.is_cuda and feats.dtype == torch.float32 and feats.is_contiguous()
+        assert mlp_params.is_cuda and mlp_params.dtype == torch.float32 and mlp_params.is_contiguous()
+        R = self._R
+        if rgb is None:
+            rgb = torch.empty(max(R, 1), 3, dtype=torch.float32, device=self.device)[:R]
+        if wsum is None:
+            wsum = torch.empty(max(R, 1), dtype=torch.float32, device=self.device)[:R]
+        m = Mlp()
+        m.n_layers = len(mlp_dims) - 1
+        for i, d in enumerate(mlp_dims):
+            m.dims[i] = int(d)
+        m.d_params = mlp_params.data_ptr()
+        s = samples.struct()
+        _check(lib().hp_aggregate_render(self._ctx, C.byref(s), R, _ptr(feats), feats.shape[1], C.byref(m),
+                                         _ptr(rgb), _ptr(wsum), _stream(stream)), "hp_aggregate_render")
+        return rgb, wsum
+
+    def render(self, points, feats, camera, mlp_dims, mlp_params, rays=None, stream=None, samples=None):
+        """build_table + search_sample + aggregate_render for one frame."""
+        p = self.params
+        self.build_table(points, camera, p.r, stream)
+        smp = self.search_sample(rays, p.K, p.n_max, out=samples, stream=stream)
+        rgb, wsum = self.aggregate_render(smp, feats, mlp_dims, mlp_params, stream=stream)
+        return rgb, wsum, smp
+
+    def status(self, stream=None):
+        code, detail = C.c_int32(), C.c_int64()
+        _check(lib().hp_get_status(self._ctx, _stream(stream), C.byref(code), C.byref(detail)), "hp_get_status")
+        return code.value, detail.value
+
+    def profile_start(self, max_launches: int = 4096):
+        _check(lib().hp_profile_start(self._ctx, int(max_launches)), "hp_profile_start")
+
+    def profile_stop(self):
+        """{kernel name: (total ms, launches)} since profile_start (syncs)."""
+        ms = (C.c_double * PROF_KERNELS)()
+        n = (C.c_int32 * PROF_KERNELS)()
+        _check(lib().hp_profile_stop(self._ctx, ms, n), "hp_profile_stop")
+        return {lib().hp_profile_kernel_name(i).decode(): (ms[i], n[i]) for i in range(PROF_KERNELS)}
+
+    def debug_fault(self, skip_tile: int, spin_limit: int = 0):
+        _check(lib().hp_debug_fault(self._ctx, int(skip_tile), int(spin_limit)), "hp_debug_fault")
