@@ -132,7 +132,8 @@ def algorithmic(kernel, N, Nv, P, R, S, K, F, dims, U):
         "k_scan": ("hbm", 8 * (P + 1)),
         "k_scatter": ("hbm", 12 * N + 8 * N + 4 * Nv + 16 * Nv),
         "k_bucket_sort": ("hbm", 8 * P + 32 * Nv),
-        "k_search_select": ("hbm", 4 * P + 16 * Nv + 20 * R + (16 + 8 * K) * S),
+        "k_search_select": ("hbm", 4 * P + 16 * Nv + 12 * R + (12 + 8 * K) * S),
+        "k_pack_samples": ("hbm", 4 * R + 8 * (R + 1) + (12 + 8 * K) * S + (16 + 8 * K) * S),
         "k_aggregate_decode": ("alu", mlp_flops),
         "k_composite": ("hbm", 28 * R + 20 * S),
     }

@@ -147,9 +147,9 @@ hp_status hp_destroy(hp_ctx *ctx);
 
 /* Bytes of device workspace one frame needs: the table for n_points points
  * seen by `cam` with radius r, plus scratch for n_rays rays of up to
- * n_samples samples.  The result is a multiple of 256. */
+ * n_samples samples with K neighbours each.  The result is a multiple of 256. */
 hp_status hp_workspace_size(const hp_config *cfg, const hp_camera *cam, float r, int64_t n_points,
-                            int64_t n_rays, int32_t n_samples, size_t *bytes);
+                            int64_t n_rays, int32_t K, int32_t n_samples, size_t *bytes);
 
 /* Host-only: the search-window half-width h (kernel size s = 2h+1) and, in
  * the cone modes, r_ddot on the f = 1 image plane, for `cam`, `cfg` and
@@ -212,7 +212,7 @@ hp_status hp_debug_fault(hp_ctx *ctx, int32_t skip_tile, int32_t spin_limit);
  * and launch counts per kernel into ms[HP_PROF_KERNELS] and
  * launches[HP_PROF_KERNELS] (either may be NULL), and stops recording.
  * Kernel ids: see hp_profile_kernel_name. */
-#define HP_PROF_KERNELS 7
+#define HP_PROF_KERNELS 8
 hp_status hp_profile_start(hp_ctx *ctx, int32_t max_launches);
 hp_status hp_profile_stop(hp_ctx *ctx, double *ms, int32_t *launches);
 const char *hp_profile_kernel_name(int32_t id);

@@ -141,7 +141,12 @@ size_t table_region_bytes(int64_t N, int64_t P)
     return o;
 }
 
-size_t search_region_bytes(int64_t R) { return al(256) + al(8 * (size_t)div_up(R > 0 ? R : 1, kRaysPerCta)); }
+// ticket + look-back words, then the per-ray sample slots
+size_t search_region_bytes(int64_t R, int n_max, int K)
+{
+    const size_t slots = (size_t)(R > 0 ? R : 1) * n_max;
+    return al(256) + al(8 * (size_t)div_up(R > 0 ? R : 1, 256)) + 3 * al(4 * slots) + 2 * al(4 * slots * K);
+}
 
 size_t render_region_bytes(int64_t cap) { return al(16 * (size_t)(cap > 0 ? cap : 1)); }
 
@@ -288,7 +293,8 @@ hp_status hp_profile_stop(hp_ctx *ctx, double *ms, int32_t *launches)
 const char *hp_profile_kernel_name(int32_t id)
 {
     static const char *names[KID_COUNT] = {"k_project_count", "k_scan", "k_scatter", "k_bucket_sort",
-                                           "k_search_select", "k_aggregate_decode", "k_composite"};
+                                           "k_search_select", "k_pack_samples", "k_aggregate_decode",
+                                           "k_composite"};
     return (id >= 0 && id < KID_COUNT) ? names[id] : "unknown";
 }
 
@@ -304,16 +310,18 @@ hp_status hp_destroy(hp_ctx *ctx)
 }
 
 hp_status hp_workspace_size(const hp_config *cfg, const hp_camera *cam, float r, int64_t n_points, int64_t n_rays,
-                            int32_t n_samples, size_t *bytes)
+                            int32_t K, int32_t n_samples, size_t *bytes)
 {
     hp_status s;
-    if (!bytes || n_points < 0 || n_rays < 0 || n_samples < 1 || n_samples > kMaxSamples) return HP_ERR_INVALID_ARG;
+    if (!bytes || n_points < 0 || n_rays < 0 || n_samples < 1 || n_samples > kMaxSamples || K < 1 || K > kMaxK)
+        return HP_ERR_INVALID_ARG;
     if ((s = check_config(cfg)) != HP_OK || (s = check_camera(cam)) != HP_OK) return s;
     int h;
     float rdd;
     if ((s = derive_window(*cam, *cfg, r, &h, &rdd)) != HP_OK) return s;
     const int64_t P = (int64_t)(cam->width + 2 * h) * (cam->height + 2 * h);
-    *bytes = table_region_bytes(n_points, P) + search_region_bytes(n_rays) + render_region_bytes(n_rays * n_samples);
+    *bytes = table_region_bytes(n_points, P) + search_region_bytes(n_rays, n_samples, K) +
+             render_region_bytes(n_rays * n_samples);
     return HP_OK;
 }
 
@@ -440,7 +448,7 @@ hp_status hp_search_sample(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n_r
         return HP_ERR_INVALID_ARG;
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
     ctx->searched = false;
-    ctx->search_bytes = search_region_bytes(n_rays);
+    ctx->search_bytes = search_region_bytes(n_rays, n_samples, K);
     char *base = nullptr;
     hp_status s;
     if ((s = region(ctx, 1, ctx->search_bytes, &base)) != HP_OK) return s;
@@ -458,8 +466,15 @@ hp_status hp_search_sample(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n_r
         a.n_s = out->n_s; a.primary = out->primary; a.cand_count = out->cand_count;
         a.sample_offset = out->sample_offset; a.t = out->t; a.ray = out->ray; a.src = out->src;
         a.delta = out->delta; a.nbr = out->nbr; a.nbr_dist = out->nbr_dist; a.capacity = out->capacity;
-        a.ticket = reinterpret_cast<uint32_t *>(base);
-        a.flags = reinterpret_cast<uint64_t *>(base + al(256));
+        const size_t slots = (size_t)n_rays * n_samples;
+        size_t o = 0;
+        a.ticket = reinterpret_cast<uint32_t *>(base + o);   o += al(256);
+        a.flags = reinterpret_cast<uint64_t *>(base + o);    o += al(8 * (size_t)div_up(n_rays, 256));
+        a.slot_t = reinterpret_cast<float *>(base + o);      o += al(4 * slots);
+        a.slot_src = reinterpret_cast<int32_t *>(base + o);  o += al(4 * slots);
+        a.slot_delta = reinterpret_cast<float *>(base + o);  o += al(4 * slots);
+        a.slot_nbr = reinterpret_cast<int32_t *>(base + o);  o += al(4 * slots * K);
+        a.slot_dist = reinterpret_cast<float *>(base + o);
         a.err = ctx->d_err;
         a.spin_limit = ctx->spin_limit;
         if (launch_search(a, st, &ctx->prof) != cudaSuccess) {

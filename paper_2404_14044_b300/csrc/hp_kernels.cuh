@@ -6,7 +6,9 @@
 namespace hp {
 
 // Kernel ids of the per-kernel profiler (hp_profile_*).
-enum KernelId { KID_PROJECT = 0, KID_SCAN, KID_SCATTER, KID_SORT, KID_SEARCH, KID_DECODE, KID_COMPOSITE, KID_COUNT };
+enum KernelId {
+    KID_PROJECT = 0, KID_SCAN, KID_SCATTER, KID_SORT, KID_SEARCH, KID_PACK, KID_DECODE, KID_COMPOSITE, KID_COUNT
+};
 
 // Optional CUDA-event pairs around each launch, on the launching stream.
 struct Prof {
@@ -76,7 +78,12 @@ struct SearchArgs {
     int32_t *nbr;
     float *nbr_dist;
     int64_t capacity;
-    uint64_t *flags;         // [ceil(R / kRaysPerCta)]
+    float *slot_t;           // [R * n_max] per-ray sample slots (scratch)
+    int32_t *slot_src;
+    float *slot_delta;
+    int32_t *slot_nbr;       // [R * n_max * K]
+    float *slot_dist;
+    uint64_t *flags;         // [ceil(R / 256)] look-back words of the packing scan
     uint32_t *ticket;
     ErrWord *err;
     uint32_t spin_limit;
@@ -105,7 +112,7 @@ struct RenderArgs {
 };
 
 cudaError_t launch_build(const BuildArgs &a, cudaStream_t st, Prof *prof);
-size_t search_smem_bytes(int K, int n_max);
+size_t search_smem_bytes();
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof);
 size_t render_smem_bytes(const RenderArgs &a);
 cudaError_t launch_render(const RenderArgs &a, cudaStream_t st, Prof *prof);

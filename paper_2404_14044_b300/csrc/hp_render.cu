@@ -73,6 +73,7 @@ __device__ __forceinline__ void dense_relu(const float *__restrict__ prm, const 
 #pragma unroll
         for (int s = 0; s < 4; ++s) acc[s][m] = bb;
     }
+#pragma unroll 4
     for (int i = 0; i < ld.fi; ++i) {
         const float4 x = *reinterpret_cast<const float4 *>(in + i * kTileS + ((4 * ty) ^ swz(i)));
         float w[OPT];

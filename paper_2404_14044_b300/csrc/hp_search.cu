@@ -1,21 +1,23 @@
 // Window search (Sec. 3.2 "Searching") and adaptive primary surface sampling
 // (Sec. 3.3), fused in one kernel.
 //
-// A block owns a tile of kRaysPerCta consecutive rays (tile number from an
-// atomic ticket) and its warps take rays one at a time.  For a ray through
+// A block owns kSearchRaysPerBlock consecutive rays and its warps take them
+// one at a time.  For a ray through
 // pixel (u, v) the s x s window of buckets is s rows of the padded table;
 // the buckets of one row are adjacent keys, so each row's points are one
 // contiguous run of the reordered list [start[k], start[k+s]).  A warp reads
-// a run 32 points at a time (one coalesced 512-byte load), tests the radius
-// predicate in every lane and appends the accepted points with a ballot
-// prefix into its shared-memory candidate buffer.  The buffer is sorted by
-// (t, id) with a warp bitonic sort; then, candidate by candidate in depth
-// order, the warp finds the K nearest candidates within r(t_j) of the
-// sample (warp min-reductions), forms d_j, alpha_j and w_j, and applies the
-// primary-cluster rule, stopping as soon as the cluster ends.  Samples are
-// staged in shared memory; the tile's sample count is turned into its global
-// offset with a decoupled look-back, and the tile writes its samples packed,
-// ray by ray, so the output order is independent of scheduling.
+// the concatenated runs 32 points at a time (coalesced 16-byte loads), tests
+// the radius predicate in every lane and appends the accepted points with a
+// ballot prefix into its shared-memory candidate buffer.  The buffer is
+// sorted by (t, id) with a warp bitonic sort; then each lane takes one
+// candidate j, finds the K nearest candidates within r(t_j) of the sample
+// (register top-K over shared-memory broadcasts) and forms d_j and alpha_j;
+// the weights w_j and the primary-cluster rule are applied in depth order,
+// stopping when the cluster ends or when gamma * T_j <= eps_w (no later
+// weight can pass).  Each ray writes its samples into its own n_samples
+// slots of a scratch area; K6 packs them ray by ray (scan + copy), so the
+// output order is independent of scheduling and blocks never wait on one
+// another while they search.
 #include "hp_kernels.cuh"
 
 namespace hp {
@@ -25,27 +27,16 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 
 struct SearchSmem {
-    size_t cp, ck, st, ssrc, sdel, snbr, sdist, sns, soff, map, ci, total;
+    size_t cp, ck, ci, total;
 };
 
-__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
-
-__host__ __device__ inline SearchSmem search_layout(int K, int n_max)
+__host__ __device__ inline SearchSmem search_layout()
 {
     SearchSmem L;
     size_t o = 0;
-    const size_t slots = (size_t)kRaysPerCta * n_max;
-    L.cp = o;    o += sizeof(float4) * kCandCap * kSearchWarps;
-    L.ck = o;    o += sizeof(uint64_t) * kCandCap * kSearchWarps;
-    L.st = o;    o += align16(4 * slots);
-    L.ssrc = o;  o += align16(4 * slots);
-    L.sdel = o;  o += align16(4 * slots);
-    L.snbr = o;  o += align16(4 * slots * K);
-    L.sdist = o; o += align16(4 * slots * K);
-    L.sns = o;   o += align16(4 * kRaysPerCta);
-    L.soff = o;  o += align16(4 * (kRaysPerCta + 1));
-    L.map = o;   o += align16(2 * slots);
-    L.ci = o;    o += align16((size_t)kCandCap * kSearchWarps);
+    L.cp = o; o += sizeof(float4) * kCandCap * kSearchWarps;
+    L.ck = o; o += sizeof(uint64_t) * kCandCap * kSearchWarps;
+    L.ci = o; o += (size_t)kCandCap * kSearchWarps;
     L.total = o;
     return L;
 }
@@ -64,36 +55,95 @@ __device__ __forceinline__ bool accept_point(const SearchArgs &a, const Ray &ray
     return rho2 <= dmul(rad, rad);
 }
 
-__device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+// Keep the cand_cap smallest (t, id) of the accepted points: lanes whose
+// point passed append it at a ballot prefix; once the buffer is full each
+// further point replaces the current largest key if it is smaller.
+__device__ __forceinline__ void append_candidates(bool acc, uint64_t key, float4 p, int lane, unsigned lt_mask,
+                                                  int cap, uint64_t *ck, float4 *cp, int &kept, int &total)
+{
+    const unsigned m = __ballot_sync(kFull, acc);
+    if (m == 0) return;
+    const int n = __popc(m);
+    if (kept + n <= cap) {
+        if (acc) {
+            const int pos = kept + __popc(m & lt_mask);
+            ck[pos] = key;
+            cp[pos] = p;
+        }
+        kept += n;
+    } else {
+        __syncwarp();
+        unsigned mm = m;
+        while (mm) {
+            const int sl = __ffs(mm) - 1;
+            mm &= mm - 1;
+            const uint64_t kk = __shfl_sync(kFull, key, sl);
+            float4 pp;
+            pp.x = __shfl_sync(kFull, p.x, sl);
+            pp.y = __shfl_sync(kFull, p.y, sl);
+            pp.z = __shfl_sync(kFull, p.z, sl);
+            pp.w = __shfl_sync(kFull, p.w, sl);
+            if (kept < cap) {
+                if (lane == 0) {
+                    ck[kept] = kk;
+                    cp[kept] = pp;
+                }
+                ++kept;
+            } else {
+                uint64_t best = 0;
+                int bi = -1;
+                for (int e = lane; e < cap; e += 32) {
+                    const uint64_t v = ck[e];
+                    if (bi < 0 || v > best) { best = v; bi = e; }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const uint64_t ob = __shfl_xor_sync(kFull, best, o);
+                    const int oi = __shfl_xor_sync(kFull, bi, o);
+                    if (oi >= 0 && (bi < 0 || ob > best)) { best = ob; bi = oi; }
+                }
+                if (kk < best && lane == 0) {
+                    ck[bi] = kk;
+                    cp[bi] = pp;
+                }
+            }
+            __syncwarp();
+        }
+    }
+    total += n;
+}
+
+// Insert x into the ascending register array keys (the largest falls off).
+template <int KB>
+__device__ __forceinline__ void knn_insert(uint64_t (&keys)[KB], uint64_t x)
+{
+#pragma unroll
+    for (int m = 0; m < KB; ++m) {
+        const uint64_t k = keys[m];
+        const bool lt = x < k;
+        keys[m] = lt ? x : k;
+        x = lt ? k : x;
+    }
+}
 
 }  // namespace
 
+template <int KB>
 __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select(const SearchArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int64_t s_tile, s_prefix;
-    __shared__ int s_next, s_total;
-    const SearchSmem L = search_layout(a.K, a.n_max);
+    __shared__ int s_next;
+    const SearchSmem L = search_layout();
+    const int rpc = kSearchRaysPerBlock;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
-    if (tid == 0) {
-        s_tile = atomicAdd(a.ticket, 1u);
-        s_next = 0;
-    }
+    if (tid == 0) s_next = 0;
     __syncthreads();
-    const int64_t tile = s_tile;
+    const int64_t tile = blockIdx.x;
 
     float4 *cp = reinterpret_cast<float4 *>(smem + L.cp) + warp * kCandCap;
     uint64_t *ck = reinterpret_cast<uint64_t *>(smem + L.ck) + warp * kCandCap;
     uint8_t *ci = reinterpret_cast<uint8_t *>(smem + L.ci) + warp * kCandCap;
-    float *stg_t = reinterpret_cast<float *>(smem + L.st);
-    int *stg_src = reinterpret_cast<int *>(smem + L.ssrc);
-    float *stg_del = reinterpret_cast<float *>(smem + L.sdel);
-    int *stg_nbr = reinterpret_cast<int *>(smem + L.snbr);
-    float *stg_dist = reinterpret_cast<float *>(smem + L.sdist);
-    int *s_ns = reinterpret_cast<int *>(smem + L.sns);
-    int *s_off = reinterpret_cast<int *>(smem + L.soff);
-    uint16_t *s_map = reinterpret_cast<uint16_t *>(smem + L.map);
 
     const int K = a.K, n_max = a.n_max, span = 2 * a.h + 1;
     const int64_t npix = (int64_t)a.cam.width * a.cam.height;
@@ -102,12 +152,9 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select(const Searc
         int rl = 0;
         if (lane == 0) rl = atomicAdd(&s_next, 1);
         rl = __shfl_sync(kFull, rl, 0);
-        if (rl >= kRaysPerCta) break;
-        const int64_t ri = tile * kRaysPerCta + rl;
-        if (ri >= a.R) {
-            if (lane == 0) s_ns[rl] = 0;
-            continue;
-        }
+        if (rl >= rpc) break;
+        const int64_t ri = tile * rpc + rl;
+        if (ri >= a.R) break;
         const int64_t pix = a.rays ? (int64_t)__ldg(a.rays + ri) : ri;
         if (pix < 0 || pix >= npix) {
             if (lane == 0) {
@@ -115,79 +162,46 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select(const Searc
                 a.n_s[ri] = 0;
                 a.primary[ri] = -1;
                 a.cand_count[ri] = 0;
-                s_ns[rl] = 0;
             }
             continue;
         }
         const int pu = (int)(pix % a.cam.width), pv = (int)(pix / a.cam.width);
         const Ray ray = make_ray(a.cam, a.mode, a.rdd, pu, pv);
 
-        // ---- window walk: s rows, each a contiguous run of the list
+        // ---- window walk.  The s rows' runs are concatenated into one index
+        // space (lane q holds row q's [lo, lo+len) and its exclusive offset),
+        // so every load instruction serves 32 points whatever the row lengths.
         int kept = 0, total = 0;
-        for (int dy = 0; dy < span; ++dy) {
-            const int64_t kb = (int64_t)(pv + dy) * a.Wp + pu;
-            const uint32_t lo = __ldg(a.start + kb), hi = __ldg(a.start + kb + span);
-            for (uint32_t b0 = lo; b0 < hi; b0 += 32) {
-                const uint32_t i = b0 + lane;
+        for (int r0 = 0; r0 < span; r0 += 32) {
+            const int nrows = min(32, span - r0);
+            uint32_t lo = 0;
+            int len = 0;
+            if (lane < nrows) {
+                const int64_t kb = (int64_t)(pv + r0 + lane) * a.Wp + pu;
+                lo = __ldg(a.start + kb);
+                len = (int)(__ldg(a.start + kb + span) - lo);
+            }
+            const int incl = warp_incl_scan(len);
+            const int tot = __shfl_sync(kFull, incl, 31);
+            const int excl = incl - len;
+            for (int v0 = 0; v0 < tot; v0 += 32) {
+                const int v = v0 + lane;
+                int row = 0;
+                for (int q = 1; q < nrows; ++q) {
+                    const int eq = __shfl_sync(kFull, excl, q);
+                    row = (v >= eq) ? q : row;
+                }
+                const uint32_t rlo = __shfl_sync(kFull, lo, row);
+                const int rex = __shfl_sync(kFull, excl, row);
                 bool acc = false;
                 float t = 0.0f;
                 float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (i < hi) {
-                    p = __ldg(a.spts + i);
+                if (v < tot) {
+                    p = __ldg(a.spts + rlo + (uint32_t)(v - rex));
                     acc = accept_point(a, ray, p, t);
                 }
-                const unsigned m = __ballot_sync(kFull, acc);
-                if (m == 0) continue;
-                const int n = __popc(m);
                 const uint64_t key = ((uint64_t)__float_as_uint(t) << 32) | (uint32_t)__float_as_int(p.w);
-                if (kept + n <= a.cand_cap) {
-                    if (acc) {
-                        const int pos = kept + __popc(m & lt_mask);
-                        ck[pos] = key;
-                        cp[pos] = p;
-                    }
-                    kept += n;
-                } else {
-                    // buffer full: keep the cand_cap smallest (t, id), one insertion at a time
-                    __syncwarp();
-                    unsigned mm = m;
-                    while (mm) {
-                        const int sl = __ffs(mm) - 1;
-                        mm &= mm - 1;
-                        const uint64_t kk = __shfl_sync(kFull, key, sl);
-                        float4 pp;
-                        pp.x = __shfl_sync(kFull, p.x, sl);
-                        pp.y = __shfl_sync(kFull, p.y, sl);
-                        pp.z = __shfl_sync(kFull, p.z, sl);
-                        pp.w = __shfl_sync(kFull, p.w, sl);
-                        if (kept < a.cand_cap) {
-                            if (lane == 0) {
-                                ck[kept] = kk;
-                                cp[kept] = pp;
-                            }
-                            ++kept;
-                        } else {
-                            uint64_t best = 0;
-                            int bi = -1;
-                            for (int e = lane; e < a.cand_cap; e += 32) {
-                                const uint64_t v = ck[e];
-                                if (bi < 0 || v > best) { best = v; bi = e; }
-                            }
-#pragma unroll
-                            for (int o = 16; o > 0; o >>= 1) {
-                                const uint64_t ob = __shfl_xor_sync(kFull, best, o);
-                                const int oi = __shfl_xor_sync(kFull, bi, o);
-                                if (oi >= 0 && (bi < 0 || ob > best)) { best = ob; bi = oi; }
-                            }
-                            if (kk < best && lane == 0) {
-                                ck[bi] = kk;
-                                cp[bi] = pp;
-                            }
-                        }
-                        __syncwarp();
-                    }
-                }
-                total += n;
+                append_candidates(acc, key, p, lane, lt_mask, a.cand_cap, ck, cp, kept, total);
             }
         }
         __syncwarp();
@@ -224,157 +238,185 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select(const Searc
             __syncwarp();
         }
 
-        float4 P[4];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const int i = lane + 32 * m;
-            P[m] = (i < C) ? cp[ci[i]] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-
-        // ---- adaptive primary surface sampling
+        // ---- adaptive primary surface sampling.  Lanes own candidates: lane
+        // j walks all candidates (shared-memory broadcast) keeping the K nearest
+        // within r(t_j) in registers, and forms d_j and alpha_j.  The product
+        // w_j = alpha_j T_j is then taken in depth order across the warp.
         float T = 1.0f, t_prev = 0.0f;
         int jstar = -1, ns = 0, prim = -1;
-        const int slot0 = rl * n_max;
-        for (int j = 0; j < C; ++j) {
-            const uint64_t kj = ck[j];
-            const float tj = __uint_as_float((uint32_t)(kj >> 32));
-            if (jstar >= 0) {
-                const float gap = dsub(tj, t_prev);
-                if (!(gap <= dmul(a.gap_k, radius_at(a.mode, a.r, ray, t_prev)))) break;
-            }
-            const float rad = radius_at(a.mode, a.r, ray, tj);
-            const float rad2 = dmul(rad, rad);
-            uint64_t q[4];
+        const int64_t slot0 = ri * n_max;
+        bool done = false;
+        for (int c0 = 0; c0 < C && !done; c0 += 32) {
+            const int j = c0 + lane;
+            float tj = 0.0f, alpha = 0.0f;
+            int idj = -1;
+            uint64_t keys[KB];
 #pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                q[m] = ~0ull;
-                if (lane + 32 * m < C) {
-                    const float ax = dfma(tj, ray.dx, -P[m].x);
-                    const float ay = dfma(tj, ray.dy, -P[m].y);
-                    const float az = dfma(tj, ray.dz, -P[m].z);
+            for (int m = 0; m < KB; ++m) keys[m] = ~0ull;
+            if (j < C) {
+                const uint64_t kj = ck[j];
+                tj = __uint_as_float((uint32_t)(kj >> 32));
+                idj = (int)(uint32_t)kj;
+                const float rad = radius_at(a.mode, a.r, ray, tj);
+                const float rad2 = dmul(rad, rad);
+                for (int i = 0; i < C; ++i) {
+                    const float4 Pi = cp[ci[i]];
+                    const float ax = dfma(tj, ray.dx, -Pi.x);
+                    const float ay = dfma(tj, ray.dy, -Pi.y);
+                    const float az = dfma(tj, ray.dz, -Pi.z);
                     const float d2 = dadd(dadd(dmul(ax, ax), dmul(ay, ay)), dmul(az, az));
-                    if (d2 <= rad2) q[m] = ((uint64_t)__float_as_uint(d2) << 32) | (uint32_t)__float_as_int(P[m].w);
+                    if (d2 <= rad2)
+                        knn_insert<KB>(keys, ((uint64_t)__float_as_uint(d2) << 32) | (uint32_t)__float_as_int(Pi.w));
                 }
-            }
-            float s = 0.0f;
-            int kp = 0, my_id = -1;
-            float my_d = 0.0f;
-            for (int k = 0; k < K; ++k) {
-                uint64_t mn = umin64(umin64(q[0], q[1]), umin64(q[2], q[3]));
+                float s = 0.0f;
+                int kp = 0;
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) mn = umin64(mn, __shfl_xor_sync(kFull, mn, o));
-                if (mn == ~0ull) break;
+                for (int m = 0; m < KB; ++m) {
+                    if (m < K && keys[m] != ~0ull) {
+                        s = dadd(s, dsqrt(__uint_as_float((uint32_t)(keys[m] >> 32))));
+                        ++kp;
+                    }
+                }
+                const float dj = ddiv(s, (float)kp);
+                alpha = dmul(a.gamma, exp32(-ddiv(dmul(dj, dj), a.beta2)));
+            }
+            const int nj = min(32, C - c0);
+            const int ns0 = ns;
+            unsigned sel = 0;
+            for (int jj = 0; jj < nj; ++jj) {
+                const float aj = __shfl_sync(kFull, alpha, jj);
+                const float tjj = __shfl_sync(kFull, tj, jj);
+                if (jstar >= 0) {
+                    const float gap = dsub(tjj, t_prev);
+                    if (!(gap <= dmul(a.gap_k, radius_at(a.mode, a.r, ray, t_prev)))) {
+                        done = true;
+                        break;
+                    }
+                }
+                const float w = dmul(aj, T);
+                T = dmul(T, dsub(1.0f, aj));
+                if (w > a.eps_w) {
+                    if (jstar < 0) {
+                        jstar = c0 + jj;
+                        const float4 pj = cp[ci[jstar]];
+                        prim = (int)pixel_key(a.cam, a.h, make_float3(pj.x, pj.y, pj.z));
+                    }
+                    sel |= 1u << jj;
+                    if (++ns == n_max) {
+                        done = true;
+                        break;
+                    }
+                }
+                t_prev = tjj;
+                // w_k <= gamma T_k <= gamma T for every later k: nothing more can pass
+                if (!(dmul(a.gamma, T) > a.eps_w)) {
+                    done = true;
+                    break;
+                }
+            }
+            if ((sel >> lane) & 1u) {
+                const int64_t slot = slot0 + ns0 + __popc(sel & lt_mask);
+                a.slot_t[slot] = tj;
+                a.slot_src[slot] = idj;
 #pragma unroll
-                for (int m = 0; m < 4; ++m)
-                    if (q[m] == mn) q[m] = ~0ull;
-                const float dist = dsqrt(__uint_as_float((uint32_t)(mn >> 32)));
-                s = dadd(s, dist);
-                if (lane == k) {
-                    my_id = (int)(uint32_t)mn;
-                    my_d = dist;
+                for (int m = 0; m < KB; ++m) {
+                    if (m < K) {
+                        const bool ok = keys[m] != ~0ull;
+                        a.slot_nbr[slot * K + m] = ok ? (int)(uint32_t)keys[m] : -1;
+                        a.slot_dist[slot * K + m] = ok ? dsqrt(__uint_as_float((uint32_t)(keys[m] >> 32))) : 0.0f;
+                    }
                 }
-                ++kp;
             }
-            const float dj = ddiv(s, (float)kp);
-            const float alpha = dmul(a.gamma, exp32(-ddiv(dmul(dj, dj), a.beta2)));
-            const float w = dmul(alpha, T);
-            T = dmul(T, dsub(1.0f, alpha));
-            if (w > a.eps_w) {
-                if (jstar < 0) {
-                    jstar = j;
-                    const float4 pj = cp[ci[j]];
-                    prim = (int)pixel_key(a.cam, a.h, make_float3(pj.x, pj.y, pj.z));
-                }
-                const int slot = slot0 + ns;
-                if (lane < K) {
-                    stg_nbr[slot * K + lane] = my_id;
-                    stg_dist[slot * K + lane] = my_d;
-                }
-                if (lane == 0) {
-                    stg_t[slot] = tj;
-                    stg_src[slot] = (int)(uint32_t)kj;
-                }
-                if (++ns == n_max) break;
-            }
-            t_prev = tj;
         }
         __syncwarp();
         if (lane < ns) {
-            const int slot = slot0 + lane;
-            const float tm = stg_t[slot];
-            stg_del[slot] = (lane + 1 < ns) ? stg_t[slot + 1] - tm : 2.0f * radius_at(a.mode, a.r, ray, tm);
+            const int64_t slot = slot0 + lane;
+            const float tm = a.slot_t[slot];
+            a.slot_delta[slot] = (lane + 1 < ns) ? a.slot_t[slot + 1] - tm : 2.0f * radius_at(a.mode, a.r, ray, tm);
         }
         if (lane == 0) {
             a.n_s[ri] = ns;
             a.primary[ri] = prim;
             a.cand_count[ri] = total;
-            s_ns[rl] = ns;
         }
         __syncwarp();
     }
-    __syncthreads();
+}
 
-    // ---- tile prefix: exclusive scan of the per-ray counts, then look-back
+// Packing (K6): exclusive scan of n_s with a decoupled look-back over
+// uniform tiles of 256 rays (one warp per 32 rays), then each warp copies
+// its rays' sample slots -- contiguous runs of n_s rows -- to the packed
+// outputs with coalesced loads and stores.
+__global__ void __launch_bounds__(256) k_pack_samples(const SearchArgs a)
+{
+    __shared__ int64_t s_tile, s_prefix;
+    __shared__ int s_warp[8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(a.ticket, 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t ri = tile * 256 + tid;
+    const int ns = ri < a.R ? a.n_s[ri] : 0;
+    const int incl = warp_incl_scan(ns);
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
     if (warp == 0) {
-        const int v0 = s_ns[lane], v1 = s_ns[lane + 32];
-        const int i0 = warp_incl_scan(v0);
-        const int t0 = __shfl_sync(kFull, i0, 31);
-        const int i1 = warp_incl_scan(v1) + t0;
-        s_off[lane] = i0 - v0;
-        s_off[lane + 32] = i1 - v1;
-        if (lane == 31) {
-            s_off[kRaysPerCta] = i1;
-            s_total = i1;
-            s_prefix = lookback_prefix(a.flags, tile, i1, a.err, a.spin_limit, true);
+        const int w = lane < 8 ? s_warp[lane] : 0;
+        const int wi = warp_incl_scan(w);
+        if (lane < 8) s_warp[lane] = wi - w;
+        if (lane == 7) s_prefix = lookback_prefix(a.flags, tile, wi, a.err, a.spin_limit, true);
+    }
+    __syncthreads();
+    const int64_t off = s_prefix + s_warp[warp] + (incl - ns);
+    if (ri < a.R) a.sample_offset[ri] = off;
+    if (ri == a.R - 1) {
+        a.sample_offset[a.R] = off + ns;
+        if (off + ns > a.capacity) set_error(a.err, HP_ERR_OVERFLOW, off + ns);
+    }
+    const int K = a.K, n_max = a.n_max;
+    const int64_t wray0 = tile * 256 + warp * 32;
+    for (int q = 0; q < 32; ++q) {
+        const int64_t r = wray0 + q;
+        if (r >= a.R) break;
+        const int n = __shfl_sync(kFull, ns, q);
+        if (n == 0) continue;
+        const int64_t o = __shfl_sync(kFull, off, q);
+        const int64_t src = r * n_max;
+        int64_t lim = a.capacity - o;               // rows that fit
+        const int nn = lim < n ? (int)(lim > 0 ? lim : 0) : n;
+        if (lane < nn) {
+            a.t[o + lane] = a.slot_t[src + lane];
+            a.src[o + lane] = a.slot_src[src + lane];
+            a.delta[o + lane] = a.slot_delta[src + lane];
+            a.ray[o + lane] = (int)r;
         }
-    }
-    __syncthreads();
-    const int total = s_total;
-    const int64_t prefix = s_prefix;
-    for (int rl = tid; rl < kRaysPerCta; rl += blockDim.x) {
-        const int64_t ri = tile * kRaysPerCta + rl;
-        if (ri < a.R) a.sample_offset[ri] = prefix + s_off[rl];
-        if (ri == a.R - 1) a.sample_offset[a.R] = prefix + s_off[rl] + s_ns[rl];
-    }
-    for (int e = tid; e < kRaysPerCta * n_max; e += blockDim.x) {
-        const int rl = e / n_max, m = e - rl * n_max;
-        if (m < s_ns[rl]) s_map[s_off[rl] + m] = (uint16_t)e;
-    }
-    __syncthreads();
-    if (tid == 0 && prefix + total > a.capacity) set_error(a.err, HP_ERR_OVERFLOW, prefix + total);
-    for (int e = tid; e < total; e += blockDim.x) {
-        const int64_t g = prefix + e;
-        if (g >= a.capacity) break;
-        const int slot = s_map[e];
-        a.t[g] = stg_t[slot];
-        a.ray[g] = (int)(tile * kRaysPerCta + slot / n_max);
-        a.src[g] = stg_src[slot];
-        a.delta[g] = stg_del[slot];
-    }
-    for (int e = tid; e < total * K; e += blockDim.x) {
-        const int s = e / K, k = e - s * K;
-        const int64_t g = prefix + s;
-        if (g >= a.capacity) break;
-        const int slot = s_map[s];
-        a.nbr[g * K + k] = stg_nbr[slot * K + k];
-        a.nbr_dist[g * K + k] = stg_dist[slot * K + k];
+        for (int e = lane; e < nn * K; e += 32) {
+            a.nbr[o * K + e] = a.slot_nbr[src * K + e];
+            a.nbr_dist[o * K + e] = a.slot_dist[src * K + e];
+        }
     }
 }
 
-size_t search_smem_bytes(int K, int n_max) { return search_layout(K, n_max).total; }
+size_t search_smem_bytes() { return search_layout().total; }
 
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof)
 {
     cudaError_t e;
-    const int64_t tiles = div_up(a.R, kRaysPerCta);
+    const int64_t blocks = div_up(a.R, kSearchRaysPerBlock);
+    const int64_t tiles = div_up(a.R, 256);
     if ((e = cudaMemsetAsync(a.flags, 0, sizeof(uint64_t) * (size_t)tiles, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(a.ticket, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
-    const size_t smem = search_smem_bytes(a.K, a.n_max);
-    if ((e = cudaFuncSetAttribute(k_search_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-        cudaSuccess)
+    const size_t smem = search_smem_bytes();
+    auto kern = a.K <= 4 ? k_search_select<4> : a.K <= 8 ? k_search_select<8>
+              : a.K <= 16 ? k_search_select<16> : k_search_select<32>;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
     prof_begin(prof, st, KID_SEARCH);
-    k_search_select<<<(unsigned)tiles, kSearchWarps * 32, smem, st>>>(a);
+    kern<<<(unsigned)blocks, kSearchWarps * 32, smem, st>>>(a);
+    prof_end(prof, st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    prof_begin(prof, st, KID_PACK);
+    k_pack_samples<<<(unsigned)tiles, 256, 0, st>>>(a);
     prof_end(prof, st);
     return cudaGetLastError();
 }

@@ -27,7 +27,7 @@ SYMBOLS = ("hp_create", "hp_destroy", "hp_workspace_size", "hp_window", "hp_set_
            "hp_table_info", "hp_table_copy", "hp_search_sample", "hp_aggregate_render", "hp_get_status",
            "hp_debug_fault", "hp_profile_start", "hp_profile_stop", "hp_profile_kernel_name",
            "hp_status_string", "hp_version")
-PROF_KERNELS = 7
+PROF_KERNELS = 8
 
 
 class HPError(RuntimeError):
@@ -76,7 +76,7 @@ def lib():
         vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
         L.hp_create.argtypes = [C.POINTER(vp), C.POINTER(Config)]
         L.hp_destroy.argtypes = [vp]
-        L.hp_workspace_size.argtypes = [C.POINTER(Config), C.POINTER(Camera), C.c_float, i64, i64, i32,
+        L.hp_workspace_size.argtypes = [C.POINTER(Config), C.POINTER(Camera), C.c_float, i64, i64, i32, i32,
                                         C.POINTER(C.c_size_t)]
         L.hp_window.argtypes = [C.POINTER(Config), C.POINTER(Camera), C.c_float, C.POINTER(i32), C.POINTER(C.c_float)]
         L.hp_set_workspace.argtypes = [vp, vp, C.c_size_t]
@@ -113,10 +113,11 @@ def window(params, camera):
     return h.value, rdd.value
 
 
-def workspace_size(params, camera, n_points: int, n_rays: int, n_samples: int) -> int:
+def workspace_size(params, camera, n_points: int, n_rays: int, n_samples: int, K: int = None) -> int:
     n = C.c_size_t()
+    K = params.K if K is None else K
     _check(lib().hp_workspace_size(C.byref(config_struct(params)), C.byref(camera_struct(camera)), float(params.r),
-                                   int(n_points), int(n_rays), int(n_samples), C.byref(n)), "hp_workspace_size")
+                                   int(n_points), int(n_rays), int(K), int(n_samples), C.byref(n)), "hp_workspace_size")
     return n.value
 
 
@@ -229,10 +230,11 @@ class HashPoint:
             pass
 
     # -- workspace (torch-allocated)
-    def reserve(self, camera, r: float, n_points: int, n_rays: int, n_samples: int):
+    def reserve(self, camera, r: float, n_points: int, n_rays: int, n_samples: int, K: int = None):
         n = C.c_size_t()
+        K = self.params.K if K is None else K
         _check(lib().hp_workspace_size(C.byref(self._cfg), C.byref(camera_struct(camera)), float(r), int(n_points),
-                                       int(n_rays), int(n_samples), C.byref(n)), "hp_workspace_size")
+                                       int(n_rays), int(K), int(n_samples), C.byref(n)), "hp_workspace_size")
         if self._ws is None or self._ws.numel() < n.value:
             self._ws = torch.empty(n.value, dtype=torch.uint8, device=self.device)
             _check(lib().hp_set_workspace(self._ctx, _ptr(self._ws), n.value), "hp_set_workspace")
