@@ -52,7 +52,8 @@ typedef enum {
     HP_ERR_TIMEOUT = 4,       /* device: a bounded inter-block wait gave up */
     HP_ERR_NOT_BUILT = 5,     /* search before build, or build parameters changed */
     HP_ERR_NO_MEMORY = 6,     /* workspace too small / allocation failed */
-    HP_ERR_BAD_RAY = 7        /* device: a ray pixel id outside [0, W*H) */
+    HP_ERR_BAD_RAY = 7,       /* device: a ray pixel id outside [0, W*H) */
+    HP_ERR_TOO_LARGE = 8      /* a size above the fixed limit of an allocation-free entry point */
 } hp_status;
 
 typedef struct hp_ctx hp_ctx;
@@ -216,6 +217,31 @@ hp_status hp_debug_fault(hp_ctx *ctx, int32_t skip_tile, int32_t spin_limit);
 hp_status hp_profile_start(hp_ctx *ctx, int32_t max_launches);
 hp_status hp_profile_stop(hp_ctx *ctx, double *ms, int32_t *launches);
 const char *hp_profile_kernel_name(int32_t id);
+
+/* Allocation-free exclusive prefix sum -- not part of the paper's method (the
+ * paper has no counterpart); it is the bucket-count scan of hp_build_table
+ * offered on its own for callers that must not allocate device memory: code
+ * hosted by an application that owns the whole device memory budget and
+ * forbids libraries to call cudaMalloc, or a real-time loop where a
+ * cudaMalloc, which can synchronise the device, would stall the frame.
+ *
+ * d_out[i] = d_in[0] + ... + d_in[i-1] for i < n (uint32, wrapping), d_in and
+ * d_out device pointers, 16-byte aligned, n <= HP_SCAN_NOALLOC_MAX_N (larger
+ * n returns HP_ERR_TOO_LARGE; n == 0 does nothing).  If d_status (device,
+ * optional) is given, the call's device status (HP_OK or HP_ERR_TIMEOUT from
+ * the bounded inter-block wait) is copied there on `stream`.
+ *
+ * Memory: the scratch (look-back words, ticket, status) lives in one
+ * file-scope static device array of 262,176 bytes that every device which
+ * loads the library holds until the process exits.  The call allocates and
+ * frees nothing; it only clears the part of the array it uses.  The first
+ * call on a device looks the array's device address up (cudaGetSymbolAddress,
+ * with that device current) and caches it; make that first call before any
+ * stream capture.  All calls share the one array: calls whose GPU work
+ * overlaps (different streams, or several host threads without ordering)
+ * race and give wrong sums -- order them on one stream. */
+#define HP_SCAN_NOALLOC_MAX_N 67108864
+hp_status hp_scan_noalloc(const uint32_t *d_in, uint32_t *d_out, int64_t n, int32_t *d_status, void *stream);
 
 /* Static string for a status code. */
 const char *hp_status_string(hp_status s);

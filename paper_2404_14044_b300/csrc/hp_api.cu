@@ -194,6 +194,7 @@ const char *hp_status_string(hp_status s)
     case HP_ERR_NOT_BUILT: return "table or samples not built";
     case HP_ERR_NO_MEMORY: return "workspace too small or allocation failed";
     case HP_ERR_BAD_RAY: return "ray pixel out of range";
+    case HP_ERR_TOO_LARGE: return "size exceeds the allocation-free limit";
     }
     return "unknown status";
 }

@@ -111,6 +111,9 @@ struct RenderArgs {
     int num_sms;
 };
 
+__global__ void k_scan(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int64_t n, uint64_t *flags,
+                       uint32_t *ticket, ErrWord *err, uint32_t spin_limit, int32_t skip_tile);
+
 cudaError_t launch_build(const BuildArgs &a, cudaStream_t st, Prof *prof);
 size_t search_smem_bytes();
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof);

@@ -19,14 +19,15 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhashpoint.so")
 
 HP_OK, HP_ERR_INVALID_ARG, HP_ERR_CUDA, HP_ERR_OVERFLOW, HP_ERR_TIMEOUT = 0, 1, 2, 3, 4
-HP_ERR_NOT_BUILT, HP_ERR_NO_MEMORY, HP_ERR_BAD_RAY = 5, 6, 7
+HP_ERR_NOT_BUILT, HP_ERR_NO_MEMORY, HP_ERR_BAD_RAY, HP_ERR_TOO_LARGE = 5, 6, 7, 8
+SCAN_NOALLOC_MAX_N = 67108864
 MLP_MAX_LAYERS = 8
 
 # every symbol include/hashpoint.h declares
 SYMBOLS = ("hp_create", "hp_destroy", "hp_workspace_size", "hp_window", "hp_set_workspace", "hp_build_table",
            "hp_table_info", "hp_table_copy", "hp_search_sample", "hp_aggregate_render", "hp_get_status",
            "hp_debug_fault", "hp_profile_start", "hp_profile_stop", "hp_profile_kernel_name",
-           "hp_status_string", "hp_version")
+           "hp_scan_noalloc", "hp_status_string", "hp_version")
 PROF_KERNELS = 8
 
 
@@ -91,6 +92,7 @@ def lib():
         L.hp_profile_stop.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(i32)]
         L.hp_profile_kernel_name.argtypes = [i32]
         L.hp_profile_kernel_name.restype = C.c_char_p
+        L.hp_scan_noalloc.argtypes = [vp, vp, i64, vp, vp]
         L.hp_status_string.argtypes = [i32]
         L.hp_status_string.restype = C.c_char_p
         L.hp_version.restype = i32
@@ -119,6 +121,16 @@ def workspace_size(params, camera, n_points: int, n_rays: int, n_samples: int, K
     _check(lib().hp_workspace_size(C.byref(config_struct(params)), C.byref(camera_struct(camera)), float(params.r),
                                    int(n_points), int(n_rays), int(K), int(n_samples), C.byref(n)), "hp_workspace_size")
     return n.value
+
+
+def scan_noalloc(d_in: torch.Tensor, d_out: torch.Tensor, d_status: Optional[torch.Tensor] = None, stream=None):
+    """Exclusive prefix sum of uint32 values (int32 tensors) through the
+    allocation-free entry point hp_scan_noalloc: for callers that may not
+    allocate device memory; its scratch is a fixed static device array."""
+    assert d_in.is_cuda and d_out.is_cuda and d_in.dtype == torch.int32 and d_out.dtype == torch.int32
+    assert d_in.is_contiguous() and d_out.is_contiguous() and d_out.numel() >= d_in.numel()
+    _check(lib().hp_scan_noalloc(_ptr(d_in), _ptr(d_out), d_in.numel(), _ptr(d_status), _stream(stream)),
+           "hp_scan_noalloc")
 
 
 def _check(rc: int, where: str):
