@@ -115,6 +115,16 @@ typedef struct {
 #define HP_MLP_MAX_LAYERS 8
 #define HP_MLP_MAX_WIDTH 128
 
+/* Decode arithmetic (hp_mlp.decode). */
+enum {
+    HP_DECODE_FP32 = 0,       /* FP32-accurate; tensor cores (tcgen05) with the error-corrected
+                                 FP16 split when every hidden layer has fan-in a multiple of 16
+                                 (<= 128) and width 16..128 step 16, else FP32 FMA cores */
+    HP_DECODE_FP32_SIMT = 1,  /* FP32 FMA cores only */
+    HP_DECODE_BF16 = 2        /* BF16 operands on the tensor cores, FP32 accumulation (hidden
+                                 layers); output layer, activations and compositing stay FP32 */
+};
+
 /* Radiance MLP: n_layers linear layers with ReLU between them, input width
  * dims[0] = F, output dims[n_layers] = 4 (density logit, r, g, b logits).
  * params (device) packs W0 (dims[1] x dims[0], row-major), b0, W1, b1, ...
@@ -124,6 +134,7 @@ typedef struct {
     int32_t n_layers;
     int32_t dims[HP_MLP_MAX_LAYERS + 1];
     const float *d_params;
+    int32_t decode;          /* HP_DECODE_* */
 } hp_mlp;
 
 /* Read-only view of the table built by the last hp_build_table. */
@@ -217,6 +228,14 @@ hp_status hp_debug_fault(hp_ctx *ctx, int32_t skip_tile, int32_t spin_limit);
 hp_status hp_profile_start(hp_ctx *ctx, int32_t max_launches);
 hp_status hp_profile_stop(hp_ctx *ctx, double *ms, int32_t *launches);
 const char *hp_profile_kernel_name(int32_t id);
+
+/* Self-test of the tensor-core path: D = A B^T for A (128 x K) and B (N x K),
+ * row-major 16-bit inputs (FP16, or BF16 when bf16 != 0), D (128 x N) FP32,
+ * all device pointers; K in 16..128 and N in 16..256, multiples of 16.  One
+ * block stages both operands, issues K/16 tcgen05.mma and reads the TMEM
+ * accumulator back.  A device-side timeout is reported by hp_get_status. */
+hp_status hp_selftest_mma(hp_ctx *ctx, const uint16_t *d_a, const uint16_t *d_b, float *d_d, int32_t K, int32_t N,
+                          int32_t bf16, void *stream);
 
 /* Allocation-free exclusive prefix sum -- not part of the paper's method (the
  * paper has no counterpart); it is the bucket-count scan of hp_build_table

@@ -518,10 +518,26 @@ hp_status hp_aggregate_render(hp_ctx *ctx, const hp_samples *smp, int64_t n_rays
     a.feats = d_feats; a.F = F; a.mlp = mlp->d_params; a.n_layers = mlp->n_layers;
     for (int l = 0; l <= mlp->n_layers; ++l) a.dims[l] = mlp->dims[l];
     a.eps_d = ctx->cfg.eps_d; a.bg_mode = ctx->cfg.bg_mode;
+    a.decode = mlp->decode; a.err = ctx->d_err;
+    if (a.decode < HP_DECODE_FP32 || a.decode > HP_DECODE_BF16) return HP_ERR_INVALID_ARG;
+    if (a.decode == HP_DECODE_BF16 && !decode_tc_supported(a, true, nullptr)) return HP_ERR_INVALID_ARG;
     a.sample_out = reinterpret_cast<float4 *>(base);
     a.rgb = d_rgb; a.wsum = d_wsum; a.num_sms = ctx->num_sms;
     if (render_smem_bytes(a) > 227 * 1024) return HP_ERR_INVALID_ARG;
     if (launch_render(a, st, &ctx->prof) != cudaSuccess) {
+        cudaGetLastError();
+        return HP_ERR_CUDA;
+    }
+    return HP_OK;
+}
+
+hp_status hp_selftest_mma(hp_ctx *ctx, const uint16_t *d_a, const uint16_t *d_b, float *d_d, int32_t K, int32_t N,
+                          int32_t bf16, void *stream)
+{
+    if (!ctx || !d_a || !d_b || !d_d) return HP_ERR_INVALID_ARG;
+    if (K < 16 || K > 128 || K % 16 != 0 || N < 16 || N > 256 || N % 16 != 0) return HP_ERR_INVALID_ARG;
+    if (launch_mma_selftest(d_a, d_b, d_d, K, N, bf16, ctx->d_err, static_cast<cudaStream_t>(stream)) !=
+        cudaSuccess) {
         cudaGetLastError();
         return HP_ERR_CUDA;
     }

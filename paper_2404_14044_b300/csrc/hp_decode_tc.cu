@@ -1,0 +1,407 @@
+// Radiance-MLP decode on the 5th-generation tensor cores (tcgen05 + TMEM).
+//
+// k_decode_tc (persistent, one 256-thread block per SM, 128 samples per
+// tile): the block stages the hidden layers' weights once in shared memory as
+// K-major FP16 (or BF16) operands; per tile it gathers and inverse-distance
+// blends the samples' neighbour features straight into the first A operand,
+// then for every hidden layer one thread issues tcgen05.mma (M = 128 samples,
+// N = layer width, K = 16 per instruction) into TMEM; the whole block reads
+// the FP32 accumulators back (tcgen05.ld), adds bias, applies ReLU and writes
+// the next layer's A operand; the 4-wide output layer and the density /
+// colour activations run on the FP32 cores from registers.
+//
+// Precision.  The default FP32-accurate mode splits every operand x into
+// hi = fp16(x) and lo = fp16((x - hi) * 2^11) and accumulates
+// A_hi B_hi into D1 and A_hi B_lo + A_lo B_hi into D2, so that
+// D1 + 2^-11 D2 carries about 22 significant bits (Ootomo & Yokota 2022; the
+// dropped lo*lo term is ~2^-22 relative).  The BF16 mode keeps one BF16 term
+// per operand and one accumulator (the BF16 decode variant).
+#include "hp_kernels.cuh"
+#include "hp_tc.cuh"
+
+namespace hp {
+
+namespace {
+
+constexpr int kTcTile = 128;
+constexpr int kTcThreads = 256;
+constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t kMbarLimit = 1u << 24;
+
+struct TcLayout {
+    int nh;                              // hidden (tensor-core) layers
+    int fi[HP_MLP_MAX_LAYERS], fo[HP_MLP_MAX_LAYERS];
+    int w_hi[HP_MLP_MAX_LAYERS], w_lo[HP_MLP_MAX_LAYERS];   // byte offsets
+    int bias[HP_MLP_MAX_LAYERS + 1];     // float offsets into the FP32 block
+    int wl;                              // float offset of the output layer's W [4][fi]
+    int f32_block;                       // byte offset of the FP32 block
+    int a_hi, a_lo;                      // byte offsets of the activation operand
+    int comb;                            // byte offset of the [128][4] combine buffer
+    int mbar, tslot;
+    int total;
+};
+
+inline int up16(int x) { return (x + 15) & ~15; }
+
+TcLayout tc_layout(const RenderArgs &a, bool bf16)
+{
+    TcLayout L{};
+    L.nh = a.n_layers - 1;
+    int o = 0, maxw = 0;
+    for (int l = 0; l < L.nh; ++l) {
+        L.fi[l] = a.dims[l];
+        L.fo[l] = a.dims[l + 1];
+        maxw = maxw > L.fi[l] ? maxw : L.fi[l];
+        L.w_hi[l] = o;
+        o += L.fi[l] * L.fo[l] * 2;
+        L.w_lo[l] = o;
+        if (!bf16) o += L.fi[l] * L.fo[l] * 2;
+    }
+    L.a_hi = o;
+    o += kTcTile * maxw * 2;
+    L.a_lo = o;
+    if (!bf16) o += kTcTile * maxw * 2;
+    L.f32_block = o;
+    int f = 0;
+    for (int l = 0; l < a.n_layers; ++l) {
+        L.bias[l] = f;
+        f += a.dims[l + 1];
+    }
+    L.wl = f;
+    f += 4 * a.dims[a.n_layers - 1];
+    o += up16(f * 4);
+    L.comb = o;
+    o += kTcTile * 4 * 4;
+    L.mbar = o;
+    o += 16;
+    L.tslot = o;
+    o += 16;
+    L.total = o;
+    return L;
+}
+
+__device__ __forceinline__ float softplus_f(float x) { return x > 0.0f ? x + log1pf(expf(-x)) : log1pf(expf(x)); }
+__device__ __forceinline__ float sigmoid_f(float x) { return 1.0f / (1.0f + expf(-x)); }
+
+template <bool kBF16>
+__device__ __forceinline__ void store_operand8(unsigned char *hi_base, unsigned char *lo_base, uint32_t off,
+                                               const float (&v)[8])
+{
+    if constexpr (kBF16) {
+        __nv_bfloat16 h[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) h[i] = __float2bfloat16_rn(v[i]);
+        *reinterpret_cast<uint4 *>(hi_base + off) = *reinterpret_cast<const uint4 *>(h);
+    } else {
+        __half h[8], l[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) tc::split_f16(v[i], h[i], l[i]);
+        *reinterpret_cast<uint4 *>(hi_base + off) = *reinterpret_cast<const uint4 *>(h);
+        *reinterpret_cast<uint4 *>(lo_base + off) = *reinterpret_cast<const uint4 *>(l);
+    }
+}
+
+template <bool kBF16>
+__device__ __forceinline__ void store_operand4(unsigned char *hi_base, unsigned char *lo_base, uint32_t off,
+                                               float4 v)
+{
+    const float x[4] = {v.x, v.y, v.z, v.w};
+    if constexpr (kBF16) {
+        __nv_bfloat16 h[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) h[i] = __float2bfloat16_rn(x[i]);
+        *reinterpret_cast<uint2 *>(hi_base + off) = *reinterpret_cast<const uint2 *>(h);
+    } else {
+        __half h[4], l[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) tc::split_f16(x[i], h[i], l[i]);
+        *reinterpret_cast<uint2 *>(hi_base + off) = *reinterpret_cast<const uint2 *>(h);
+        *reinterpret_cast<uint2 *>(lo_base + off) = *reinterpret_cast<const uint2 *>(l);
+    }
+}
+
+}  // namespace
+
+template <bool kBF16>
+__global__ void __launch_bounds__(kTcThreads, 1) k_decode_tc(const RenderArgs a, const TcLayout L)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float *f32 = reinterpret_cast<float *>(smem + L.f32_block);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L.mbar);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + L.tslot);
+    unsigned char *A_hi = smem + L.a_hi;
+    unsigned char *A_lo = smem + L.a_lo;
+    float *comb = reinterpret_cast<float *>(smem + L.comb);
+
+    // ---- stage weights (global W is [out][in] FP32) and FP32 biases
+    {
+        int g = 0;
+        for (int l = 0; l < a.n_layers; ++l) {
+            const int fi = a.dims[l], fo = a.dims[l + 1];
+            const int nw = fi * fo;
+            if (l < L.nh) {
+                for (int e = tid; e < nw; e += blockDim.x) {
+                    const int o = e / fi, i = e - o * fi;
+                    const float w = __ldg(a.mlp + g + e);
+                    const uint32_t off = tc::kmajor_off(o, i, fi);
+                    if constexpr (kBF16) {
+                        *reinterpret_cast<__nv_bfloat16 *>(smem + L.w_hi[l] + off) = __float2bfloat16_rn(w);
+                    } else {
+                        __half h, lo;
+                        tc::split_f16(w, h, lo);
+                        *reinterpret_cast<__half *>(smem + L.w_hi[l] + off) = h;
+                        *reinterpret_cast<__half *>(smem + L.w_lo[l] + off) = lo;
+                    }
+                }
+            } else {
+                for (int e = tid; e < nw; e += blockDim.x) f32[L.wl + e] = __ldg(a.mlp + g + e);
+            }
+            g += nw;
+            for (int e = tid; e < fo; e += blockDim.x) f32[L.bias[l] + e] = __ldg(a.mlp + g + e);
+            g += fo;
+        }
+    }
+    if (tid == 0) {
+        tc::mbar_init(mbar, 1);
+        tc::mbar_fence_init();
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, kTmemCols);
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = *tslot;
+    const uint32_t d1 = tbase, d2 = tbase + 128;
+
+    const int64_t S_all = __ldg(a.sample_offset + a.R);
+    const int64_t S = S_all < a.capacity ? S_all : a.capacity;
+    const int F = a.F, K = a.K;
+    const int lpr = F >> 2, spw = 32 / lpr;                   // lanes per feature row, samples per warp step
+    const int sub = lane / lpr, chunk = lane - sub * lpr;
+    const float4 *feats4 = reinterpret_cast<const float4 *>(a.feats);
+    const int q = warp & 3, hf = warp >> 2;                    // TMEM lane quarter, column half
+    const int row = 32 * q + lane;                             // sample row of this thread in the tile
+    const uint32_t lane_off = (uint32_t)(32 * q) << 16;
+    uint32_t phase = 0;
+    bool ok = true;
+
+    for (int64_t base = (int64_t)blockIdx.x * kTcTile; base < S && ok; base += (int64_t)gridDim.x * kTcTile) {
+        // ---- gather + inverse-distance blend -> first A operand (K = F).
+        // Lane (s, c) of a warp owns sample s of the group and the 16-byte
+        // chunk c of its feature row and walks the K neighbours itself, so
+        // the K row loads of a lane are independent and in flight together.
+        for (int s0 = warp * spw; s0 < kTcTile; s0 += (kTcThreads / 32) * spw) {
+            const int sl = s0 + sub;
+            const int64_t g = base + sl;
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (sl < kTcTile && g < S) {
+                float wsum = 0.0f;
+                const int *nb = a.nbr + g * K;
+                const float *nd = a.nbr_dist + g * K;
+#pragma unroll 8
+                for (int k = 0; k < K; ++k) {
+                    const int id = __ldg(nb + k);
+                    if (id >= 0) {
+                        const float w = 1.0f / fmaxf(__ldg(nd + k), a.eps_d);
+                        const float4 f = __ldg(feats4 + (int64_t)id * lpr + chunk);
+                        acc.x = fmaf(w, f.x, acc.x);
+                        acc.y = fmaf(w, f.y, acc.y);
+                        acc.z = fmaf(w, f.z, acc.z);
+                        acc.w = fmaf(w, f.w, acc.w);
+                        wsum += w;
+                    }
+                }
+                const float inv = 1.0f / wsum;
+                acc.x *= inv; acc.y *= inv; acc.z *= inv; acc.w *= inv;
+            }
+            if (sl < kTcTile) store_operand4<kBF16>(A_hi, A_lo, tc::kmajor_off(sl, 4 * chunk, F), acc);
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+
+        float o4[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int l = 0; l < L.nh && ok; ++l) {
+            const int fi = L.fi[l], fo = L.fo[l];
+            if (tid == 0) {
+                tc::fence_after_sync();
+                const uint32_t idesc = tc::idesc_f16(kTcTile, fo, kBF16);
+                const uint32_t ah = tc::smem_u32(A_hi), al = tc::smem_u32(A_lo);
+                const uint32_t wh = tc::smem_u32(smem + L.w_hi[l]), wl = tc::smem_u32(smem + L.w_lo[l]);
+                const uint32_t sbo = (uint32_t)fi * 16;
+                for (int kk = 0; kk < fi / 16; ++kk) {
+                    const uint64_t dah = tc::sdesc(ah + kk * 256, 128, sbo), dbh = tc::sdesc(wh + kk * 256, 128, sbo);
+                    tc::mma_f16(d1, dah, dbh, idesc, kk > 0);
+                    if constexpr (!kBF16) {
+                        const uint64_t dal = tc::sdesc(al + kk * 256, 128, sbo);
+                        const uint64_t dbl = tc::sdesc(wl + kk * 256, 128, sbo);
+                        tc::mma_f16(d2, dah, dbl, idesc, kk > 0);
+                        tc::mma_f16(d2, dal, dbh, idesc, 1);
+                    }
+                }
+                tc::commit(mbar);
+            }
+            if (!tc::mbar_wait(mbar, phase, kMbarLimit)) {
+                ok = false;
+                set_error(a.err, HP_ERR_TIMEOUT, -2);
+            }
+            phase ^= 1u;
+            ok = __syncthreads_and(ok) != 0;
+            if (!ok) break;
+            tc::fence_after_sync();
+
+            // ---- epilogue: this thread's sample row, half of the columns
+            const int half = fo >> 1, c0 = hf * half;
+            const float *bias = f32 + L.bias[l];
+            const bool last = (l + 1 == L.nh);
+            for (int c = c0; c < c0 + half; c += 8) {
+                float v1[8], v2[8];
+                tc::ld8(d1 + lane_off + (uint32_t)c, v1);
+                if constexpr (!kBF16) tc::ld8(d2 + lane_off + (uint32_t)c, v2);
+                tc::wait_ld();
+                float h[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    float x = v1[i];
+                    if constexpr (!kBF16) x = fmaf(v2[i], 1.0f / 2048.0f, x);
+                    h[i] = fmaxf(x + bias[c + i], 0.0f);
+                }
+                if (!last) {
+                    store_operand8<kBF16>(A_hi, A_lo, tc::kmajor_off(row, c, fo), h);
+                } else {
+                    const float *W = f32 + L.wl;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        o4[0] = fmaf(h[i], W[0 * fo + c + i], o4[0]);
+                        o4[1] = fmaf(h[i], W[1 * fo + c + i], o4[1]);
+                        o4[2] = fmaf(h[i], W[2 * fo + c + i], o4[2]);
+                        o4[3] = fmaf(h[i], W[3 * fo + c + i], o4[3]);
+                    }
+                }
+            }
+            tc::fence_async_smem();
+            tc::fence_before_sync();
+            __syncthreads();
+        }
+        if (!ok) break;
+
+        // ---- output layer: combine the two column halves, activations
+        if (hf == 1) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) comb[row * 4 + i] = o4[i];
+        }
+        __syncthreads();
+        if (hf == 0) {
+            const float *bl = f32 + L.bias[a.n_layers - 1];
+            float o[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) o[i] = o4[i] + comb[row * 4 + i] + bl[i];
+            const int64_t g = base + row;
+            if (g < S) a.sample_out[g] = make_float4(softplus_f(o[0]), sigmoid_f(o[1]), sigmoid_f(o[2]), sigmoid_f(o[3]));
+        }
+        __syncthreads();
+    }
+
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tbase, kTmemCols);
+}
+
+// One 128 x N x K product D = A B^T on the tensor cores (A: 128 x K, B: N x K,
+// row-major 16-bit inputs), for the library's self-test of the tcgen05 path.
+__global__ void __launch_bounds__(128, 1) k_mma_selftest(const uint16_t *A, const uint16_t *B, float *D, int K, int N,
+                                                         int bf16, ErrWord *err)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    unsigned char *sa = smem;
+    unsigned char *sb = smem + 128 * K * 2;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sb + N * K * 2);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+    for (int e = tid; e < 128 * K; e += blockDim.x) {
+        const int r = e / K, k = e - r * K;
+        *reinterpret_cast<uint16_t *>(sa + tc::kmajor_off(r, k, K)) = A[e];
+    }
+    for (int e = tid; e < N * K; e += blockDim.x) {
+        const int r = e / K, k = e - r * K;
+        *reinterpret_cast<uint16_t *>(sb + tc::kmajor_off(r, k, K)) = B[e];
+    }
+    if (tid == 0) {
+        tc::mbar_init(mbar, 1);
+        tc::mbar_fence_init();
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, kTmemCols);
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = *tslot;
+    if (tid == 0) {
+        const uint32_t idesc = tc::idesc_f16(128, N, bf16 != 0);
+        for (int kk = 0; kk < K / 16; ++kk)
+            tc::mma_f16(tbase, tc::sdesc(tc::smem_u32(sa) + kk * 256, 128, K * 16),
+                        tc::sdesc(tc::smem_u32(sb) + kk * 256, 128, K * 16), idesc, kk > 0);
+        tc::commit(mbar);
+    }
+    const bool done = tc::mbar_wait(mbar, 0, kMbarLimit);
+    if (!done && tid == 0) set_error(err, HP_ERR_TIMEOUT, -3);
+    if (__syncthreads_and(done)) {
+        tc::fence_after_sync();
+        const int r = 32 * warp + lane;
+        for (int c = 0; c < N; c += 8) {
+            float v[8];
+            tc::ld8(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, v);
+            tc::wait_ld();
+#pragma unroll
+            for (int i = 0; i < 8; ++i) D[r * N + c + i] = v[i];
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tbase, kTmemCols);
+}
+
+// Tensor-core decode possible for this MLP?  Hidden layers on tcgen05 need
+// K (fan-in) multiple of 16 and N (width) in 16..128 step 16.
+bool decode_tc_supported(const RenderArgs &a, bool bf16, size_t *smem)
+{
+    if (a.n_layers < 2) return false;
+    for (int l = 0; l + 1 < a.n_layers; ++l) {
+        const int fi = a.dims[l], fo = a.dims[l + 1];
+        if (fi % 16 != 0 || fi > 128 || fo % 16 != 0 || fo < 16 || fo > 128) return false;
+    }
+    const TcLayout L = tc_layout(a, bf16);
+    if (smem) *smem = (size_t)L.total;
+    return L.total <= 227 * 1024;
+}
+
+cudaError_t launch_decode_tc(const RenderArgs &a, bool bf16, cudaStream_t st)
+{
+    cudaError_t e;
+    const TcLayout L = tc_layout(a, bf16);
+    auto kern = bf16 ? k_decode_tc<true> : k_decode_tc<false>;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total)) != cudaSuccess)
+        return e;
+    int64_t grid = a.num_sms;
+    const int64_t tiles = div_up(a.capacity > 0 ? a.capacity : 1, kTcTile);
+    if (grid > tiles) grid = tiles;
+    kern<<<(unsigned)grid, kTcThreads, L.total, st>>>(a, L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mma_selftest(const uint16_t *A, const uint16_t *B, float *D, int K, int N, int bf16, ErrWord *err,
+                                cudaStream_t st)
+{
+    cudaError_t e;
+    const size_t smem = (size_t)128 * K * 2 + (size_t)N * K * 2 + 32;
+    if ((e = cudaFuncSetAttribute(k_mma_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+        return e;
+    k_mma_selftest<<<1, 128, smem, st>>>(A, B, D, K, N, bf16, err);
+    return cudaGetLastError();
+}
+
+}  // namespace hp

@@ -105,6 +105,8 @@ struct RenderArgs {
     int dims[HP_MLP_MAX_LAYERS + 1];
     float eps_d;
     int bg_mode;
+    int decode;              // HP_DECODE_*
+    ErrWord *err;
     float4 *sample_out;      // [capacity] (sigma, r, g, b)
     float *rgb;              // [R*3]
     float *wsum;             // [R]
@@ -119,5 +121,9 @@ size_t search_smem_bytes();
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof);
 size_t render_smem_bytes(const RenderArgs &a);
 cudaError_t launch_render(const RenderArgs &a, cudaStream_t st, Prof *prof);
+bool decode_tc_supported(const RenderArgs &a, bool bf16, size_t *smem);
+cudaError_t launch_decode_tc(const RenderArgs &a, bool bf16, cudaStream_t st);
+cudaError_t launch_mma_selftest(const uint16_t *A, const uint16_t *B, float *D, int K, int N, int bf16, ErrWord *err,
+                                cudaStream_t st);
 
 }  // namespace hp

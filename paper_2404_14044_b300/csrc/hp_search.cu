@@ -206,10 +206,31 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select(const Searc
         }
         __syncwarp();
 
-        // ---- sort the candidates by (t, id): bitonic network in shared memory
+        // ---- sort the candidates by (t, id): up to 32 in registers (shuffle
+        // bitonic network), more in shared memory
         const int C = kept;
-        if (C > 1) {
-            int n2 = 2;
+        if (C <= 32) {
+            uint64_t key = lane < C ? ck[lane] : ~0ull;
+            int idx = lane;
+#pragma unroll
+            for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    const uint64_t ok = __shfl_xor_sync(kFull, key, j);
+                    const int oi = __shfl_xor_sync(kFull, idx, j);
+                    const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
+                    if (keep_min ? (ok < key) : (ok > key)) {
+                        key = ok;
+                        idx = oi;
+                    }
+                }
+            }
+            __syncwarp();
+            ck[lane] = key;
+            ci[lane] = (uint8_t)idx;
+            __syncwarp();
+        } else {
+            int n2 = 64;
             while (n2 < C) n2 <<= 1;
             for (int e = C + lane; e < n2; e += 32) ck[e] = ~0ull;
             for (int e = lane; e < n2; e += 32) ci[e] = (uint8_t)e;
@@ -233,9 +254,6 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select(const Searc
                     __syncwarp();
                 }
             }
-        } else if (C == 1) {
-            if (lane == 0) ci[0] = 0;
-            __syncwarp();
         }
 
         // ---- adaptive primary surface sampling.  Lanes own candidates: lane
@@ -259,14 +277,21 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select(const Searc
                 idj = (int)(uint32_t)kj;
                 const float rad = radius_at(a.mode, a.r, ray, tj);
                 const float rad2 = dmul(rad, rad);
-                for (int i = 0; i < C; ++i) {
+                // Only candidates whose depth is within lim of t_j can lie within
+                // r(t_j) of x_j: |x_j - P_i| >= |t_j - t_i| up to float32 rounding
+                // (~1e-6 (1 + t)), far inside the margin, so the set is unchanged.
+                const float lim = rad * 1.001f + 1e-5f * (1.0f + tj);
+                int i0 = j;
+                while (i0 > 0 && tj - __uint_as_float((uint32_t)(ck[i0 - 1] >> 32)) <= lim) --i0;
+                for (int i = i0; i < C; ++i) {
+                    const uint64_t ki = ck[i];
+                    if (__uint_as_float((uint32_t)(ki >> 32)) - tj > lim) break;
                     const float4 Pi = cp[ci[i]];
                     const float ax = dfma(tj, ray.dx, -Pi.x);
                     const float ay = dfma(tj, ray.dy, -Pi.y);
                     const float az = dfma(tj, ray.dz, -Pi.z);
                     const float d2 = dadd(dadd(dmul(ax, ax), dmul(ay, ay)), dmul(az, az));
-                    if (d2 <= rad2)
-                        knn_insert<KB>(keys, ((uint64_t)__float_as_uint(d2) << 32) | (uint32_t)__float_as_int(Pi.w));
+                    if (d2 <= rad2) knn_insert<KB>(keys, ((uint64_t)__float_as_uint(d2) << 32) | (uint32_t)ki);
                 }
                 float s = 0.0f;
                 int kp = 0;

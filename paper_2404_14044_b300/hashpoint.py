@@ -27,7 +27,7 @@ MLP_MAX_LAYERS = 8
 SYMBOLS = ("hp_create", "hp_destroy", "hp_workspace_size", "hp_window", "hp_set_workspace", "hp_build_table",
            "hp_table_info", "hp_table_copy", "hp_search_sample", "hp_aggregate_render", "hp_get_status",
            "hp_debug_fault", "hp_profile_start", "hp_profile_stop", "hp_profile_kernel_name",
-           "hp_scan_noalloc", "hp_status_string", "hp_version")
+           "hp_selftest_mma", "hp_scan_noalloc", "hp_status_string", "hp_version")
 PROF_KERNELS = 8
 
 
@@ -56,7 +56,11 @@ class Samples(C.Structure):
 
 
 class Mlp(C.Structure):
-    _fields_ = [("n_layers", C.c_int32), ("dims", C.c_int32 * (MLP_MAX_LAYERS + 1)), ("d_params", C.c_void_p)]
+    _fields_ = [("n_layers", C.c_int32), ("dims", C.c_int32 * (MLP_MAX_LAYERS + 1)), ("d_params", C.c_void_p),
+                ("decode", C.c_int32)]
+
+
+DECODE_FP32, DECODE_FP32_SIMT, DECODE_BF16 = 0, 1, 2
 
 
 class Table(C.Structure):
@@ -93,6 +97,7 @@ def lib():
         L.hp_profile_kernel_name.argtypes = [i32]
         L.hp_profile_kernel_name.restype = C.c_char_p
         L.hp_scan_noalloc.argtypes = [vp, vp, i64, vp, vp]
+        L.hp_selftest_mma.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp]
         L.hp_status_string.argtypes = [i32]
         L.hp_status_string.restype = C.c_char_p
         L.hp_version.restype = i32
@@ -290,7 +295,7 @@ class HashPoint:
 
     def aggregate_render(self, samples: SampleBuffers, feats: torch.Tensor, mlp_dims: Sequence[int],
                          mlp_params: torch.Tensor, rgb: Optional[torch.Tensor] = None,
-                         wsum: Optional[torch.Tensor] = None, stream=None):
+                         wsum: Optional[torch.Tensor] = None, stream=None, decode: int = DECODE_FP32):
         assert feats.is_cuda and feats.dtype == torch.float32 and feats.is_contiguous()
         assert mlp_params.is_cuda and mlp_params.dtype == torch.float32 and mlp_params.is_contiguous()
         R = self._R
@@ -303,18 +308,28 @@ class HashPoint:
         for i, d in enumerate(mlp_dims):
             m.dims[i] = int(d)
         m.d_params = mlp_params.data_ptr()
+        m.decode = int(decode)
         s = samples.struct()
         _check(lib().hp_aggregate_render(self._ctx, C.byref(s), R, _ptr(feats), feats.shape[1], C.byref(m),
                                          _ptr(rgb), _ptr(wsum), _stream(stream)), "hp_aggregate_render")
         return rgb, wsum
 
-    def render(self, points, feats, camera, mlp_dims, mlp_params, rays=None, stream=None, samples=None):
+    def render(self, points, feats, camera, mlp_dims, mlp_params, rays=None, stream=None, samples=None,
+               decode: int = DECODE_FP32):
         """build_table + search_sample + aggregate_render for one frame."""
         p = self.params
         self.build_table(points, camera, p.r, stream)
         smp = self.search_sample(rays, p.K, p.n_max, out=samples, stream=stream)
-        rgb, wsum = self.aggregate_render(smp, feats, mlp_dims, mlp_params, stream=stream)
+        rgb, wsum = self.aggregate_render(smp, feats, mlp_dims, mlp_params, stream=stream, decode=decode)
         return rgb, wsum, smp
+
+    def selftest_mma(self, A: torch.Tensor, B: torch.Tensor, bf16: bool = False, stream=None) -> torch.Tensor:
+        """D = A B^T on the tensor cores (A 128 x K, B N x K, fp16 or bf16)."""
+        assert A.shape[0] == 128 and A.shape[1] == B.shape[1] and A.is_contiguous() and B.is_contiguous()
+        D = torch.empty(128, B.shape[0], dtype=torch.float32, device=A.device)
+        _check(lib().hp_selftest_mma(self._ctx, _ptr(A), _ptr(B), _ptr(D), A.shape[1], B.shape[0], int(bf16),
+                                     _stream(stream)), "hp_selftest_mma")
+        return D
 
     def status(self, stream=None):
         code, detail = C.c_int32(), C.c_int64()
