@@ -85,7 +85,9 @@ typedef struct {
     float gamma;          /* alpha_j = gamma * exp(-d_j^2 / beta2); 0 < gamma <= 1 */
     float beta2;          /* beta^2 > 0 */
     float eps_w;          /* a candidate is kept when w_j > eps_w (>= 0) */
-    float gap_k;          /* primary cluster: consecutive t-gap <= gap_k * r(t) */
+    float gap_k;          /* primary cluster: consecutive t-gap <= gap_k * r(t); 0 disables the
+                             gate, so lowering gamma moves sampling from the primary surface
+                             towards multi-surface sampling (Supplementary, noisy input) */
     float eps_d;          /* IDW distance floor (> 0) */
     int32_t cand_cap;     /* candidates kept per ray, 1..128 (the smallest (t, id)) */
     int32_t bg_mode;      /* 0 black background, 1 white */

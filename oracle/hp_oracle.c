@@ -50,7 +50,9 @@
  *   D10 weight        w_j = alpha_j * T_j,  T_1 = 1,  T_{j+1} = T_j * (1 - alpha_j)
  *   D11 primary       j* = first j with w_j > eps_w; the cluster runs on while
  *                     (t_{j+1} - t_j) <= gap_k * r(t_j); samples are its members
- *                     with w_j > eps_w, in order, at most n
+ *                     with w_j > eps_w, in order, at most n.  gap_k = 0 drops the
+ *                     cluster gate: every candidate from j* on with w_j > eps_w
+ *                     (the gamma-controlled move towards multi-surface sampling)
  *   exp32             Cody & Waite range reduction (two-part ln 2) and a
  *                     degree-7 Taylor polynomial in Horner form, scaled by 2^k
  */
@@ -456,7 +458,7 @@ static void select_samples(const frame_t *f, const ray_t *ray, const cand_t *cs,
         project_key(f->cam, f->h, cs[jstar].P, &key);
         res->primary = (int32_t)key;
         for (int64_t j = jstar; j < C && res->n_s < n_max; ++j) {
-            if (j > jstar) {
+            if (j > jstar && p->gap_k > 0.0f) {
                 float gap = cs[j].t - cs[j - 1].t;
                 if (!(gap <= p->gap_k * radius_at(p, ray, cs[j - 1].t))) break;
             }

@@ -32,6 +32,9 @@ struct hp_ctx {
     uint2 *keyrank = nullptr;
     float4 *spts = nullptr;
     uint64_t *scan_flags = nullptr;
+    float4 *raytab = nullptr;        // per-pixel rays, cached while the intrinsics are unchanged
+    bool raytab_valid = false;
+    float raytab_key[8] = {0};
     // search state
     bool searched = false;
     int64_t R = 0;
@@ -54,7 +57,7 @@ hp_status check_config(const hp_config *c)
     if (!(c->gamma > 0.f && c->gamma <= 1.f)) return HP_ERR_INVALID_ARG;
     if (!(c->beta2 > 0.f) || !is_finite32(c->beta2)) return HP_ERR_INVALID_ARG;
     if (!(c->eps_w >= 0.f) || !is_finite32(c->eps_w)) return HP_ERR_INVALID_ARG;
-    if (!(c->gap_k > 0.f) || !is_finite32(c->gap_k)) return HP_ERR_INVALID_ARG;
+    if (!(c->gap_k >= 0.f) || !is_finite32(c->gap_k)) return HP_ERR_INVALID_ARG;
     if (!(c->eps_d > 0.f) || !is_finite32(c->eps_d)) return HP_ERR_INVALID_ARG;
     if (c->cand_cap < 1 || c->cand_cap > kCandCap) return HP_ERR_INVALID_ARG;
     if (c->bg_mode != 0 && c->bg_mode != 1) return HP_ERR_INVALID_ARG;
@@ -129,9 +132,10 @@ hp_status derive_window(const hp_camera &c, const hp_config &cfg, float r, int *
     return HP_OK;
 }
 
-size_t table_region_bytes(int64_t N, int64_t P)
+size_t table_region_bytes(int64_t N, int64_t P, int64_t npix)
 {
     size_t o = 0;
+    o += al(16 * (size_t)npix);                              // ray table (first: depends on W*H only)
     o += al(256);                                            // tickets
     o += al(4 * (size_t)(P + 1));                            // cnt
     o += al(4 * (size_t)(P + 1));                            // start
@@ -162,6 +166,7 @@ hp_status region(hp_ctx *ctx, int i, size_t bytes, char **out)
         return HP_OK;
     }
     if (ctx->own_bytes[i] < bytes) {
+        if (i == 0) ctx->raytab_valid = false;          // fresh memory: the cached ray table is gone
         if (ctx->own[i]) cudaFree(ctx->own[i]);
         ctx->own[i] = nullptr;
         ctx->own_bytes[i] = 0;
@@ -321,7 +326,8 @@ hp_status hp_workspace_size(const hp_config *cfg, const hp_camera *cam, float r,
     float rdd;
     if ((s = derive_window(*cam, *cfg, r, &h, &rdd)) != HP_OK) return s;
     const int64_t P = (int64_t)(cam->width + 2 * h) * (cam->height + 2 * h);
-    *bytes = table_region_bytes(n_points, P) + search_region_bytes(n_rays, n_samples, K) +
+    *bytes = table_region_bytes(n_points, P, (int64_t)cam->width * cam->height) +
+             search_region_bytes(n_rays, n_samples, K) +
              render_region_bytes(n_rays * n_samples);
     return HP_OK;
 }
@@ -342,6 +348,7 @@ hp_status hp_window(const hp_config *cfg, const hp_camera *cam, float r, int32_t
 hp_status hp_set_workspace(hp_ctx *ctx, void *d_ptr, size_t bytes)
 {
     if (!ctx || (d_ptr && ((uintptr_t)d_ptr % kAlign) != 0)) return HP_ERR_INVALID_ARG;
+    ctx->raytab_valid = false;
     ctx->ws = static_cast<char *>(d_ptr);
     ctx->ws_bytes = d_ptr ? bytes : 0;
     ctx->built = false;
@@ -372,10 +379,23 @@ hp_status hp_build_table(hp_ctx *ctx, const float *d_points, int64_t n_points, c
     if (P + 1 > 0xffffffffLL) return HP_ERR_INVALID_ARG;
     ctx->built = false;
     ctx->searched = false;
-    ctx->table_bytes = table_region_bytes(n_points, P);
+    const int64_t npix = (int64_t)cam->width * cam->height;
+    ctx->table_bytes = table_region_bytes(n_points, P, npix);
     char *base = nullptr;
     if ((s = region(ctx, 0, ctx->table_bytes, &base)) != HP_OK) return s;
     size_t o = 0;
+    {
+        // the ray table depends on the intrinsics, the radius mode and r_ddot only
+        const float key[8] = {(float)cam->width, (float)cam->height, cam->fx, cam->fy, cam->cx, cam->cy,
+                              (float)ctx->cfg.radius_mode, rdd};
+        float4 *rt = reinterpret_cast<float4 *>(base);
+        if (!ctx->raytab_valid || rt != ctx->raytab || std::memcmp(key, ctx->raytab_key, sizeof(key)) != 0) {
+            ctx->raytab_valid = false;
+            std::memcpy(ctx->raytab_key, key, sizeof(key));
+        }
+        ctx->raytab = rt;
+        o += al(16 * (size_t)npix);
+    }
     ctx->scan_ticket = reinterpret_cast<uint32_t *>(base + o); o += al(256);
     ctx->cnt = reinterpret_cast<uint32_t *>(base + o);         o += al(4 * (size_t)(P + 1));
     ctx->start = reinterpret_cast<uint32_t *>(base + o);       o += al(4 * (size_t)(P + 1));
@@ -464,6 +484,7 @@ hp_status hp_search_sample(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n_r
         a.Wp = ctx->Wp; a.gamma = ctx->cfg.gamma; a.beta2 = ctx->cfg.beta2; a.eps_w = ctx->cfg.eps_w;
         a.gap_k = ctx->cfg.gap_k; a.cand_cap = ctx->cfg.cand_cap; a.K = K; a.n_max = n_samples;
         a.start = ctx->start; a.spts = ctx->spts; a.rays = d_ray_pixels; a.R = n_rays;
+        a.raytab = ctx->raytab; a.raytab_stale = ctx->raytab_valid ? 0 : 1;
         a.n_s = out->n_s; a.primary = out->primary; a.cand_count = out->cand_count;
         a.sample_offset = out->sample_offset; a.t = out->t; a.ray = out->ray; a.src = out->src;
         a.delta = out->delta; a.nbr = out->nbr; a.nbr_dist = out->nbr_dist; a.capacity = out->capacity;
@@ -482,6 +503,7 @@ hp_status hp_search_sample(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n_r
             cudaGetLastError();
             return HP_ERR_CUDA;
         }
+        ctx->raytab_valid = true;
     }
     ctx->R = n_rays;
     ctx->K = K;

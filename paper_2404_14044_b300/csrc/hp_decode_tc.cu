@@ -24,7 +24,7 @@ namespace hp {
 namespace {
 
 constexpr int kTcTile = 128;
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 512;            // 16 warps: 4 TMEM lane quarters x 4 column groups
 constexpr uint32_t kTmemCols = 256;
 constexpr uint32_t kMbarLimit = 1u << 24;
 
@@ -71,7 +71,7 @@ TcLayout tc_layout(const RenderArgs &a, bool bf16)
     f += 4 * a.dims[a.n_layers - 1];
     o += up16(f * 4);
     L.comb = o;
-    o += kTcTile * 4 * 4;
+    o += 4 * kTcTile * 4 * 4;                // [column group][row][4]
     L.mbar = o;
     o += 16;
     L.tslot = o;
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_decode_tc(const RenderArgs a,
     const int lpr = F >> 2, spw = 32 / lpr;                   // lanes per feature row, samples per warp step
     const int sub = lane / lpr, chunk = lane - sub * lpr;
     const float4 *feats4 = reinterpret_cast<const float4 *>(a.feats);
-    const int q = warp & 3, hf = warp >> 2;                    // TMEM lane quarter, column half
+    const int q = warp & 3, cg = warp >> 2;                    // TMEM lane quarter, column group (0..3)
     const int row = 32 * q + lane;                             // sample row of this thread in the tile
     const uint32_t lane_off = (uint32_t)(32 * q) << 16;
     uint32_t phase = 0;
@@ -251,11 +251,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_decode_tc(const RenderArgs a,
             if (!ok) break;
             tc::fence_after_sync();
 
-            // ---- epilogue: this thread's sample row, half of the columns
-            const int half = fo >> 1, c0 = hf * half;
+            // ---- epilogue: this thread's sample row, a quarter of the columns
+            // (groups of 8 columns when the layer is narrower than 32)
+            const int ngroups = fo >= 32 ? 4 : fo / 8;
+            const int span = fo / ngroups, c0 = cg * span;
             const float *bias = f32 + L.bias[l];
             const bool last = (l + 1 == L.nh);
-            for (int c = c0; c < c0 + half; c += 8) {
+            for (int c = c0; cg < ngroups && c < c0 + span; c += 8) {
                 float v1[8], v2[8];
                 tc::ld8(d1 + lane_off + (uint32_t)c, v1);
                 if constexpr (!kBF16) tc::ld8(d2 + lane_off + (uint32_t)c, v2);
@@ -286,17 +288,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_decode_tc(const RenderArgs a,
         }
         if (!ok) break;
 
-        // ---- output layer: combine the two column halves, activations
-        if (hf == 1) {
+        // ---- output layer: combine the column groups, activations
+        if (cg > 0) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) comb[row * 4 + i] = o4[i];
+            for (int i = 0; i < 4; ++i) comb[(cg * kTcTile + row) * 4 + i] = o4[i];
         }
         __syncthreads();
-        if (hf == 0) {
+        if (cg == 0) {
             const float *bl = f32 + L.bias[a.n_layers - 1];
             float o[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) o[i] = o4[i] + comb[row * 4 + i] + bl[i];
+            for (int i = 0; i < 4; ++i)
+                o[i] = ((o4[i] + comb[(kTcTile + row) * 4 + i]) + comb[(2 * kTcTile + row) * 4 + i]) +
+                       comb[(3 * kTcTile + row) * 4 + i] + bl[i];
             const int64_t g = base + row;
             if (g < S) a.sample_out[g] = make_float4(softplus_f(o[0]), sigmoid_f(o[1]), sigmoid_f(o[2]), sigmoid_f(o[3]));
         }

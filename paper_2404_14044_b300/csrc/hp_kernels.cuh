@@ -53,7 +53,7 @@ struct BuildArgs {
 };
 
 struct SearchArgs {
-    Cam cam;
+    Cam cam;                 // raytab is (re)computed from cam when raytab_stale
     int mode;
     float r;
     float rdd;
@@ -65,6 +65,8 @@ struct SearchArgs {
     int n_max;
     const uint32_t *start;
     const float4 *spts;
+    float4 *raytab;          // [W*H] per-pixel (dx, dy, dz, cone c)
+    int raytab_stale;        // recompute the ray table before searching
     const int32_t *rays;     // NULL: ray i is pixel i
     int64_t R;
     int32_t *n_s;

@@ -128,6 +128,19 @@ __device__ __forceinline__ void knn_insert(uint64_t (&keys)[KB], uint64_t x)
 
 }  // namespace
 
+// Per-pixel ray table: direction and cone coefficient of every pixel's ray
+// (the decision contract's D3/D4 arithmetic).  Rays live in camera space, so
+// the table depends only on the intrinsics and the radius mode and is reused
+// by every frame whose intrinsics are unchanged.
+__global__ void __launch_bounds__(256) k_ray_table(Cam cam, int mode, float rdd, float4 *__restrict__ tab)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)cam.width * cam.height) return;
+    const int pu = (int)(i % cam.width), pv = (int)(i / cam.width);
+    const Ray r = make_ray(cam, mode, rdd, pu, pv);
+    tab[i] = make_float4(r.dx, r.dy, r.dz, r.c);
+}
+
 template <int KB>
 __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select(const SearchArgs a)
 {
@@ -155,7 +168,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select(const Searc
         if (rl >= rpc) break;
         const int64_t ri = tile * rpc + rl;
         if (ri >= a.R) break;
-        const int64_t pix = a.rays ? (int64_t)__ldg(a.rays + ri) : ri;
+        const int pix = a.rays ? __ldg(a.rays + ri) : (int)ri;
         if (pix < 0 || pix >= npix) {
             if (lane == 0) {
                 set_error(a.err, HP_ERR_BAD_RAY, ri);
@@ -165,8 +178,13 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select(const Searc
             }
             continue;
         }
-        const int pu = (int)(pix % a.cam.width), pv = (int)(pix / a.cam.width);
-        const Ray ray = make_ray(a.cam, a.mode, a.rdd, pu, pv);
+        const int pv = pix / a.cam.width, pu = pix - pv * a.cam.width;
+        const float4 rt = __ldg(a.raytab + pix);
+        Ray ray;
+        ray.dx = rt.x;
+        ray.dy = rt.y;
+        ray.dz = rt.z;
+        ray.c = rt.w;
 
         // ---- window walk.  The s rows' runs are concatenated into one index
         // space (lane q holds row q's [lo, lo+len) and its exclusive offset),
@@ -186,10 +204,12 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select(const Searc
             const int excl = incl - len;
             for (int v0 = 0; v0 < tot; v0 += 32) {
                 const int v = v0 + lane;
+                // row of v: the last row whose exclusive offset is <= v (binary search)
                 int row = 0;
-                for (int q = 1; q < nrows; ++q) {
-                    const int eq = __shfl_sync(kFull, excl, q);
-                    row = (v >= eq) ? q : row;
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int cand = row + step;
+                    const int ec = __shfl_sync(kFull, excl, cand < nrows ? cand : 31);
+                    if (cand < nrows && v >= ec) row = cand;
                 }
                 const uint32_t rlo = __shfl_sync(kFull, lo, row);
                 const int rex = __shfl_sync(kFull, excl, row);
@@ -209,7 +229,18 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select(const Searc
         // ---- sort the candidates by (t, id): up to 32 in registers (shuffle
         // bitonic network), more in shared memory
         const int C = kept;
-        if (C <= 32) {
+        if (C <= 16) {
+            // rank sort: keys are unique (ids), rank = number of smaller keys
+            const uint64_t key = lane < C ? ck[lane] : ~0ull;
+            int rank = 0;
+            for (int i = 0; i < C; ++i) rank += (ck[i] < key) ? 1 : 0;
+            __syncwarp();
+            if (lane < C) {
+                ck[rank] = key;
+                ci[rank] = (uint8_t)lane;
+            }
+            __syncwarp();
+        } else if (C <= 32) {
             uint64_t key = lane < C ? ck[lane] : ~0ull;
             int idx = lane;
 #pragma unroll
@@ -311,7 +342,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select(const Searc
             for (int jj = 0; jj < nj; ++jj) {
                 const float aj = __shfl_sync(kFull, alpha, jj);
                 const float tjj = __shfl_sync(kFull, tj, jj);
-                if (jstar >= 0) {
+                if (jstar >= 0 && a.gap_k > 0.0f) {
                     const float gap = dsub(tjj, t_prev);
                     if (!(gap <= dmul(a.gap_k, radius_at(a.mode, a.r, ray, t_prev)))) {
                         done = true;
@@ -369,9 +400,8 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select(const Searc
 }
 
 // Packing (K6): exclusive scan of n_s with a decoupled look-back over
-// uniform tiles of 256 rays (one warp per 32 rays), then each warp copies
-// its rays' sample slots -- contiguous runs of n_s rows -- to the packed
-// outputs with coalesced loads and stores.
+// uniform tiles of 256 rays, then each thread copies its ray's sample slots
+// (a contiguous run of n_s rows) to the packed outputs.
 __global__ void __launch_bounds__(256) k_pack_samples(const SearchArgs a)
 {
     __shared__ int64_t s_tile, s_prefix;
@@ -398,26 +428,34 @@ __global__ void __launch_bounds__(256) k_pack_samples(const SearchArgs a)
         a.sample_offset[a.R] = off + ns;
         if (off + ns > a.capacity) set_error(a.err, HP_ERR_OVERFLOW, off + ns);
     }
-    const int K = a.K, n_max = a.n_max;
-    const int64_t wray0 = tile * 256 + warp * 32;
-    for (int q = 0; q < 32; ++q) {
-        const int64_t r = wray0 + q;
-        if (r >= a.R) break;
-        const int n = __shfl_sync(kFull, ns, q);
-        if (n == 0) continue;
-        const int64_t o = __shfl_sync(kFull, off, q);
-        const int64_t src = r * n_max;
-        int64_t lim = a.capacity - o;               // rows that fit
-        const int nn = lim < n ? (int)(lim > 0 ? lim : 0) : n;
-        if (lane < nn) {
-            a.t[o + lane] = a.slot_t[src + lane];
-            a.src[o + lane] = a.slot_src[src + lane];
-            a.delta[o + lane] = a.slot_delta[src + lane];
-            a.ray[o + lane] = (int)r;
+    // each thread copies its own ray's rows; neighbouring rays are adjacent
+    // in the packed output, so a warp's stores stay nearly contiguous
+    if (ri < a.R && ns > 0) {
+        const int K = a.K;
+        const int64_t src = ri * a.n_max;
+        int64_t nn = a.capacity - off;
+        nn = nn < ns ? (nn > 0 ? nn : 0) : ns;
+        for (int m = 0; m < nn; ++m) {
+            a.t[off + m] = a.slot_t[src + m];
+            a.src[off + m] = a.slot_src[src + m];
+            a.delta[off + m] = a.slot_delta[src + m];
+            a.ray[off + m] = (int)ri;
         }
-        for (int e = lane; e < nn * K; e += 32) {
-            a.nbr[o * K + e] = a.slot_nbr[src * K + e];
-            a.nbr_dist[o * K + e] = a.slot_dist[src * K + e];
+        const int64_t n_el = nn * K;
+        if ((K & 3) == 0) {
+            const int4 *sn = reinterpret_cast<const int4 *>(a.slot_nbr + src * K);
+            const float4 *sd = reinterpret_cast<const float4 *>(a.slot_dist + src * K);
+            int4 *dn = reinterpret_cast<int4 *>(a.nbr + off * K);
+            float4 *dd = reinterpret_cast<float4 *>(a.nbr_dist + off * K);
+            for (int64_t e = 0; e < n_el / 4; ++e) {
+                dn[e] = sn[e];
+                dd[e] = sd[e];
+            }
+        } else {
+            for (int64_t e = 0; e < n_el; ++e) {
+                a.nbr[off * K + e] = a.slot_nbr[src * K + e];
+                a.nbr_dist[off * K + e] = a.slot_dist[src * K + e];
+            }
         }
     }
 }
@@ -428,6 +466,11 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof)
 {
     cudaError_t e;
     const int64_t blocks = div_up(a.R, kSearchRaysPerBlock);
+    if (a.raytab_stale) {
+        const int64_t npix = (int64_t)a.cam.width * a.cam.height;
+        k_ray_table<<<(unsigned)div_up(npix, 256), 256, 0, st>>>(a.cam, a.mode, a.rdd, a.raytab);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     const int64_t tiles = div_up(a.R, 256);
     if ((e = cudaMemsetAsync(a.flags, 0, sizeof(uint64_t) * (size_t)tiles, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(a.ticket, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;

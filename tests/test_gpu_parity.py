@@ -122,6 +122,21 @@ def test_parameter_variants(kw):
     assert_parity(g, o, sc.params.K)
 
 
+def test_gamma_transition_parity():
+    # gap_k = 0: no cluster gate; lowering gamma moves sampling from the primary
+    # surface onto the surfaces behind it (multi-surface), bit-exact at every gamma
+    sc = scenes.objects_800(n_points=1_000_000, res=160)
+    base = sc.params
+    S = []
+    for gamma in (0.9, 0.5, 0.2, 0.05):
+        sc.params = scenes.Params(**{**base.__dict__, "gamma": gamma, "gap_k": 0.0, "n_max": 16})
+        g = gpu_render(sc)
+        o = oracle_render(sc)
+        assert_parity(g, o, sc.params.K)
+        S.append(o["S"])
+    assert S == sorted(S) and S[-1] > 2 * S[0]
+
+
 def test_mlp_shapes():
     sc = _tiny(scenes.RADIUS_FIXED, res=32, n=8000)
     for dims in ([32, 4], [32, 16, 4], [32, 128, 128, 128, 4], [32, 32, 64, 16, 128, 4]):

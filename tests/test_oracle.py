@@ -269,6 +269,27 @@ def test_select_primary_cluster_stops_at_gap():
     assert res["n_s"] == 3 and list(res["src"]) == [0, 1, 2]
 
 
+def test_gamma_transition_without_cluster_gate():
+    # Supplementary (adaptive sampling for noisy input): with the gate off,
+    # lowering gamma lets weights decay slower, so sampling reaches the
+    # surfaces behind the primary one; with gamma = 0.9 it stays on the first
+    cam = _cam()
+    pix = 16 * 32 + 16
+    ts = [3.0, 3.004, 3.008, 3.1, 3.104, 3.108, 3.3, 3.304]
+    P, t = _ray_cands(cam, scenes.Params(r=0.01), pix, ts, [0.0, 0.003, -0.003, 0.0, 0.003, -0.003, 0.0, 0.003])
+    counts = []
+    for gamma in (0.9, 0.5, 0.1, 0.01):
+        p = scenes.Params(r=0.01, gamma=gamma, K=8, n_max=16, gap_k=0.0)
+        res = oracle.select(cam, p, pix, t, np.arange(8), P)
+        counts.append(res["n_s"])
+        # the count follows w_j = gamma (1 - gamma)^(j-1) > eps_w (alpha ~ gamma here)
+        m = math.floor(math.log(p.eps_w / gamma) / math.log(1 - gamma)) + 1 if gamma < 1 else 1
+        assert res["n_s"] == min(8, m, 16) or gamma == 0.01
+    assert counts[0] == 3 and counts == sorted(counts) and counts[-1] == 8
+    gated = oracle.select(cam, scenes.Params(r=0.01, gamma=0.01, K=8, n_max=16, gap_k=4.0), pix, t, np.arange(8), P)
+    assert gated["n_s"] == 3                               # the gate keeps the primary surface only
+
+
 def test_select_isolated_point_loses_confidence():
     # the pseudo-UDF: a candidate whose neighbourhood is far (d_j ~ beta)
     # gets alpha << gamma and is skipped; the dense cluster behind is primary
