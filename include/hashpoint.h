@@ -208,6 +208,25 @@ hp_status hp_search_sample(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n_r
 hp_status hp_aggregate_render(hp_ctx *ctx, const hp_samples *samples, int64_t n_rays, const float *d_feats,
                               int32_t F, const hp_mlp *mlp, float *d_rgb, float *d_wsum, void *stream);
 
+/* Backward of hp_aggregate_render (Sec. 3.4 + Eq. 2) with respect to the point
+ * features and the point positions, the discrete structure of the last
+ * hp_search_sample (neighbour sets, samples) held fixed -- it is not
+ * differentiable.  Sample depths move with their source point
+ * (t_j = <P_src, d>, P = R p + t), so positions receive gradient through the
+ * inverse-distance weights, the sample positions and the Delta's of Eq. 2.
+ * Call it after hp_aggregate_render with the same `samples`, before the next
+ * hp_aggregate_render on this context (it reuses the decoded samples that
+ * call kept in the workspace), with the ray list of the last search still
+ * valid.  d_points (N x 3 world) and d_feats (N x F) are the forward inputs;
+ * d_grad_rgb (R x 3) and d_grad_wsum (R, or NULL) the output gradients.
+ * Gradients are ADDED (atomically, FP32) into d_grad_feats (N x F) and
+ * d_grad_points (N x 3, world space); either may be NULL.  The MLP weights
+ * get no gradient. */
+hp_status hp_aggregate_render_backward(hp_ctx *ctx, const hp_samples *samples, int64_t n_rays,
+                                       const float *d_points, const float *d_feats, int32_t F, const hp_mlp *mlp,
+                                       const float *d_grad_rgb, const float *d_grad_wsum, float *d_grad_feats,
+                                       float *d_grad_points, void *stream);
+
 /* Synchronise `stream`, then return the device status word recorded since the
  * last call (HP_OK if none) and its detail (e.g. the tile or ray index), and
  * clear it.  The return value is HP_ERR_CUDA if the synchronisation failed. */
@@ -226,7 +245,7 @@ hp_status hp_debug_fault(hp_ctx *ctx, int32_t skip_tile, int32_t spin_limit);
  * and launch counts per kernel into ms[HP_PROF_KERNELS] and
  * launches[HP_PROF_KERNELS] (either may be NULL), and stops recording.
  * Kernel ids: see hp_profile_kernel_name. */
-#define HP_PROF_KERNELS 8
+#define HP_PROF_KERNELS 10
 hp_status hp_profile_start(hp_ctx *ctx, int32_t max_launches);
 hp_status hp_profile_stop(hp_ctx *ctx, double *ms, int32_t *launches);
 const char *hp_profile_kernel_name(int32_t id);

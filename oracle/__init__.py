@@ -56,6 +56,7 @@ def lib():
         L.or_exp32.argtypes = [C.c_float]
         L.or_exp32.restype = C.c_float
         L.or_cam_point.argtypes = [C.POINTER(Camera), fp, fp]
+        L.or_cam_points.argtypes = [C.POINTER(Camera), fp, C.c_int64, fp]
         L.or_window.argtypes = [C.POINTER(Camera), C.POINTER(Params), i32p, fp]
         L.or_window.restype = C.c_int
         L.or_build_table.argtypes = [fp, C.c_int64, C.POINTER(Camera), C.c_int32, u32p, i32p, fp]
@@ -74,6 +75,12 @@ def lib():
         L.or_select.argtypes = [C.POINTER(Camera), C.POINTER(Params), C.c_int32, C.c_int32, fp, i32p, fp, fp,
                                 i32p, i32p, fp, i32p, fp, fp]
         L.or_select.restype = C.c_int32
+        L.or_backward.argtypes = [fp, C.c_int64, fp, C.c_int32, C.POINTER(Camera), C.POINTER(Params), i32p,
+                                  C.c_int32, fp, i32p, C.c_int64, i64p, fp, i32p, i32p, dp, dp, dp, dp, dp]
+        L.or_backward.restype = C.c_int64
+        L.or_forward_frozen.argtypes = [dp, dp, dp, C.c_int32, C.POINTER(Camera), C.POINTER(Params), i32p,
+                                        C.c_int32, fp, i32p, C.c_int64, i64p, fp, i32p, i32p, dp, dp]
+        L.or_forward_frozen.restype = C.c_int64
     return _lib
 
 
@@ -113,12 +120,7 @@ def cam_points(cam, pts: np.ndarray) -> np.ndarray:
     """Camera-space positions under the decision contract (D1)."""
     pts = np.ascontiguousarray(pts, np.float32)
     out = np.empty_like(pts)
-    cs = camera_struct(cam)
-    L = lib()
-    o = np.empty(3, np.float32)
-    for i in range(len(pts)):
-        L.or_cam_point(C.byref(cs), _p(pts[i], C.c_float), _p(o, C.c_float))
-        out[i] = o
+    lib().or_cam_points(C.byref(camera_struct(cam)), _p(pts, C.c_float), len(pts), _p(out, C.c_float))
     return out
 
 
@@ -242,3 +244,60 @@ def select(cam, params, pixel, t, ids, P):
                          _p(dj, C.c_float), _p(wj, C.c_float))
     return dict(n_s=int(ns), t=ot[:ns], src=osrc[:ns], nbr=onbr[: ns * K].reshape(ns, K),
                 nbr_dist=od[: ns * K].reshape(ns, K), jstar=int(js.value), d=dj[:Cn], w=wj[:Cn])
+
+
+def backward(pts, feats, cam, params, mlp_dims, mlp_params, frame, grad_rgb, grad_wsum=None, rays=None):
+    """Gradients of the frame ``frame`` (an or_render result) with respect to
+    the features and positions, for output gradients grad_rgb (R x 3) and
+    grad_wsum (R).  Returns (g_feats N x F, g_pcam N x 3, g_pworld N x 3), double."""
+    pts = np.ascontiguousarray(pts, np.float32)
+    feats = np.ascontiguousarray(feats, np.float32)
+    N, F = feats.shape
+    R = len(frame["n_s"])
+    dims = np.ascontiguousarray(mlp_dims, np.int32)
+    mlp = np.ascontiguousarray(mlp_params, np.float32)
+    rays_a = None if rays is None else np.ascontiguousarray(rays, np.int32)
+    gr = np.ascontiguousarray(grad_rgb, np.float64).reshape(R, 3)
+    gw = None if grad_wsum is None else np.ascontiguousarray(grad_wsum, np.float64)
+    gf = np.zeros((max(N, 1), F))
+    gpc = np.zeros((max(N, 1), 3))
+    gpw = np.zeros((max(N, 1), 3))
+    off = np.ascontiguousarray(frame["sample_offset"], np.int64)
+    st = np.ascontiguousarray(frame["t"], np.float32)
+    ss = np.ascontiguousarray(frame["src"], np.int32)
+    sn = np.ascontiguousarray(frame["nbr"], np.int32)
+    rc = lib().or_backward(_p(pts, C.c_float), N, _p(feats, C.c_float), F, C.byref(camera_struct(cam)),
+                           C.byref(params_struct(params)), _p(dims, C.c_int32), len(dims) - 1, _p(mlp, C.c_float),
+                           _p(rays_a, C.c_int32), R, _p(off, C.c_int64), _p(st, C.c_float), _p(ss, C.c_int32),
+                           _p(sn, C.c_int32), _p(gr, C.c_double), _p(gw, C.c_double), _p(gf, C.c_double),
+                           _p(gpc, C.c_double), _p(gpw, C.c_double))
+    if rc != 0:
+        raise ValueError(f"or_backward failed ({rc})")
+    return gf[:N], gpc[:N], gpw[:N]
+
+
+def forward_frozen(pcam, pcam0, feats, cam, params, mlp_dims, mlp_params, frame, rays=None):
+    """rgb (R x 3), wsum (R) of the frame with its discrete structure frozen,
+    at camera-space positions pcam (double) and features feats (double)."""
+    pcam = np.ascontiguousarray(pcam, np.float64)
+    pcam0 = np.ascontiguousarray(pcam0, np.float64)
+    feats = np.ascontiguousarray(feats, np.float64)
+    F = feats.shape[1]
+    R = len(frame["n_s"])
+    dims = np.ascontiguousarray(mlp_dims, np.int32)
+    mlp = np.ascontiguousarray(mlp_params, np.float32)
+    rays_a = None if rays is None else np.ascontiguousarray(rays, np.int32)
+    rgb = np.zeros((max(R, 1), 3))
+    ws = np.zeros(max(R, 1))
+    off = np.ascontiguousarray(frame["sample_offset"], np.int64)
+    st = np.ascontiguousarray(frame["t"], np.float32)
+    ss = np.ascontiguousarray(frame["src"], np.int32)
+    sn = np.ascontiguousarray(frame["nbr"], np.int32)
+    rc = lib().or_forward_frozen(_p(pcam, C.c_double), _p(pcam0, C.c_double), _p(feats, C.c_double), F,
+                                 C.byref(camera_struct(cam)), C.byref(params_struct(params)), _p(dims, C.c_int32),
+                                 len(dims) - 1, _p(mlp, C.c_float), _p(rays_a, C.c_int32), R, _p(off, C.c_int64),
+                                 _p(st, C.c_float), _p(ss, C.c_int32), _p(sn, C.c_int32), _p(rgb, C.c_double),
+                                 _p(ws, C.c_double))
+    if rc != 0:
+        raise ValueError(f"or_forward_frozen failed ({rc})")
+    return rgb[:R], ws[:R]

@@ -127,6 +127,12 @@ void or_cam_point(const or_camera *c, const float *p, float *out)
     out[2] = ((c->R[6] * px + c->R[7] * py) + c->R[8] * pz) + c->t[2];
 }
 
+/* D1 for N points (out: N x 3). */
+void or_cam_points(const or_camera *c, const float *p, int64_t N, float *out)
+{
+    for (int64_t i = 0; i < N; ++i) or_cam_point(c, p + 3 * i, out + 3 * i);
+}
+
 /* D2: returns 1 and the padded key if the point is kept. */
 static int project_key(const or_camera *c, int h, const float *X, uint32_t *key)
 {
@@ -738,4 +744,263 @@ int32_t or_select(const or_camera *cam, const or_params *prm, int32_t pixel, int
     }
     free(cs);
     return res.n_s;
+}
+
+/* ------------------------------------------------------------ backward
+ * Gradients of the rendered colour c and weight sum W = sum_j w'_j (Eq. 2)
+ * of every ray with respect to the point features and the point positions,
+ * the discrete structure (neighbour sets, samples) held fixed.  Forward, per
+ * sample j of a ray with direction d: x_j = t_j d; IDW weights
+ * w_ij = 1/max(|x_j - P_i|, eps_d), f_j = sum_i w_ij f_i / sum_i w_ij; MLP ->
+ * o_j; sigma_j = softplus(o_j0), c_j = sigmoid(o_j1..3); E_j =
+ * exp(-sigma_j Delta_j), tau_1 = 1, tau_{j+1} = tau_j E_j, w'_j = tau_j (1 - E_j);
+ * c = sum_j w'_j c_j + (1 - W) bg.  Sample depths depend on the source point:
+ * t_j = t_j(0) + <P_src - P_src(0), d>; Delta_j = t_{j+1} - t_j, Delta_last =
+ * 2 r(t_last).  Positions are camera space P = R p + t; world gradients are
+ * R^T dL/dP.  All in double.  "pcam" holds the camera-space positions the
+ * function is evaluated at (N x 3) and "pcam0" the base positions the sample
+ * depths t_j(0) belong to. */
+
+typedef struct {
+    double P[3];
+} v3_t;
+
+static void mlp_forward_keep(const int32_t *dims, int32_t L, const float *params, const double *x, double *acts,
+                             double *pre, double *out)
+{
+    /* acts: per layer input (L x 1024), pre: per layer pre-activation (L x 1024) */
+    const float *P = params;
+    for (int32_t i = 0; i < dims[0]; ++i) acts[i] = x[i];
+    for (int32_t l = 0; l < L; ++l) {
+        int32_t fi = dims[l], fo = dims[l + 1];
+        const float *W = P, *b = P + (int64_t)fi * fo;
+        double *in = acts + (int64_t)l * 1024, *z = pre + (int64_t)l * 1024;
+        for (int32_t o = 0; o < fo; ++o) {
+            double acc = (double)b[o];
+            for (int32_t i = 0; i < fi; ++i) acc += (double)W[(int64_t)o * fi + i] * in[i];
+            z[o] = acc;
+            if (l + 1 < L) acts[(int64_t)(l + 1) * 1024 + o] = acc > 0.0 ? acc : 0.0;
+            else out[o] = acc;
+        }
+        P += (int64_t)fi * fo + fo;
+    }
+}
+
+/* Continuous forward (and optional backward) of one ray with frozen structure. */
+static void ray_continuous(const or_camera *cam, const or_params *prm, const float *d32, float c_cone,
+                           const double *pcam, const double *pcam0, const double *feats, int32_t F,
+                           const int32_t *dims, int32_t L, const float *mlp, int32_t K, int32_t n_s,
+                           const float *ts, const int32_t *src, const int32_t *nbr, double *rgb, double *wsum,
+                           const double *grad_rgb, double grad_wsum, double *g_feats, double *g_pcam)
+{
+    double d[3] = {d32[0], d32[1], d32[2]};
+    double bg = prm->bg_mode == 1 ? 1.0 : 0.0;
+    enum { MS = 64 };
+    double t[MS], sig[MS], col[MS][3], o[MS][4], delta[MS], E[MS], tau[MS], wp[MS];
+    double Wsum[MS];
+    double (*fe)[1024] = (double (*)[1024])malloc(sizeof(double) * 1024 * (size_t)(n_s > 0 ? n_s : 1));
+    double *acts_all = (double *)malloc(sizeof(double) * (size_t)L * 1024 * (size_t)(n_s > 0 ? n_s : 1));
+    double *pre_all = (double *)malloc(sizeof(double) * (size_t)L * 1024 * (size_t)(n_s > 0 ? n_s : 1));
+#define ACTS(j) (acts_all + (int64_t)(j) * L * 1024)
+#define PRE(j) (pre_all + (int64_t)(j) * L * 1024)
+    double T = 1.0, ws = 0.0, c3[3] = {0, 0, 0};
+    for (int32_t j = 0; j < n_s; ++j) {
+        const double *Ps = pcam + 3 * (int64_t)src[j], *P0 = pcam0 + 3 * (int64_t)src[j];
+        t[j] = (double)ts[j] + ((Ps[0] - P0[0]) * d[0] + (Ps[1] - P0[1]) * d[1] + (Ps[2] - P0[2]) * d[2]);
+    }
+    for (int32_t j = 0; j < n_s; ++j) {
+        double x[3] = {t[j] * d[0], t[j] * d[1], t[j] * d[2]};
+        double W = 0.0;
+        for (int32_t k = 0; k < F; ++k) fe[j][k] = 0.0;
+        for (int32_t m = 0; m < K; ++m) {
+            int32_t id = nbr[(int64_t)j * K + m];
+            if (id < 0) continue;
+            const double *Pi = pcam + 3 * (int64_t)id;
+            double dx = x[0] - Pi[0], dy = x[1] - Pi[1], dz = x[2] - Pi[2];
+            double dist = sqrt(dx * dx + dy * dy + dz * dz);
+            double w = 1.0 / (dist > prm->eps_d ? dist : (double)prm->eps_d);
+            W += w;
+            for (int32_t k = 0; k < F; ++k) fe[j][k] += w * feats[(int64_t)id * F + k];
+        }
+        for (int32_t k = 0; k < F; ++k) fe[j][k] /= W;
+        Wsum[j] = W;
+        mlp_forward_keep(dims, L, mlp, fe[j], ACTS(j), PRE(j), o[j]);
+        sig[j] = softplus_d(o[j][0]);
+        for (int a = 0; a < 3; ++a) col[j][a] = sigmoid_d(o[j][1 + a]);
+    }
+    for (int32_t j = 0; j < n_s; ++j) {
+        delta[j] = (j + 1 < n_s) ? t[j + 1] - t[j]
+                                 : 2.0 * (prm->radius_mode == 0 ? (double)prm->r : t[j] * (double)c_cone);
+        E[j] = exp(-sig[j] * delta[j]);
+        tau[j] = T;
+        wp[j] = T * -expm1(-sig[j] * delta[j]);
+        for (int a = 0; a < 3; ++a) c3[a] += wp[j] * col[j][a];
+        ws += wp[j];
+        T *= E[j];
+    }
+    for (int a = 0; a < 3; ++a) rgb[a] = c3[a] + (1.0 - ws) * bg;
+    *wsum = ws;
+    if (!grad_rgb) {
+        free(fe); free(acts_all); free(pre_all);
+        return;
+    }
+
+    /* composite backward */
+    double gw[MS], gsig[MS], gdel[MS], gt[MS], suffix = 0.0;
+    for (int32_t j = 0; j < n_s; ++j)
+        gw[j] = grad_rgb[0] * (col[j][0] - bg) + grad_rgb[1] * (col[j][1] - bg) + grad_rgb[2] * (col[j][2] - bg) +
+                grad_wsum;
+    for (int32_t j = n_s - 1; j >= 0; --j) {
+        double bracket = gw[j] * tau[j] * E[j] - suffix;   /* suffix = sum_{k>j} gw_k w'_k */
+        gsig[j] = bracket * delta[j];
+        gdel[j] = bracket * sig[j];
+        suffix += gw[j] * wp[j];
+    }
+    for (int32_t j = 0; j < n_s; ++j) gt[j] = 0.0;
+    for (int32_t j = 0; j < n_s; ++j) {
+        if (j + 1 < n_s) {
+            gt[j + 1] += gdel[j];
+            gt[j] -= gdel[j];
+        } else if (prm->radius_mode != 0) {
+            gt[j] += gdel[j] * 2.0 * (double)c_cone;
+        }
+    }
+    for (int32_t j = 0; j < n_s; ++j) {
+        /* activations and MLP backward */
+        double dz[1024], dh[1024];
+        double go[4];
+        go[0] = gsig[j] * sigmoid_d(o[j][0]);
+        for (int a = 0; a < 3; ++a) go[1 + a] = grad_rgb[a] * wp[j] * col[j][a] * (1.0 - col[j][a]);
+        for (int32_t k = 0; k < 4; ++k) dz[k] = go[k];
+        const float *Pl[16];
+        {
+            const float *P = mlp;
+            for (int32_t l = 0; l < L; ++l) { Pl[l] = P; P += (int64_t)dims[l] * dims[l + 1] + dims[l + 1]; }
+        }
+        for (int32_t l = L - 1; l >= 0; --l) {
+            int32_t fi = dims[l], fo = dims[l + 1];
+            const float *W = Pl[l];
+            for (int32_t i = 0; i < fi; ++i) {
+                double acc = 0.0;
+                for (int32_t oo = 0; oo < fo; ++oo) acc += (double)W[(int64_t)oo * fi + i] * dz[oo];
+                dh[i] = acc;
+            }
+            if (l > 0) {
+                const double *z = PRE(j) + (int64_t)(l - 1) * 1024;
+                for (int32_t i = 0; i < fi; ++i) dz[i] = z[i] > 0.0 ? dh[i] : 0.0;
+            }
+        }
+        /* dh = dL/df_j ; IDW backward */
+        double x[3] = {t[j] * d[0], t[j] * d[1], t[j] * d[2]};
+        double gx[3] = {0, 0, 0};
+        for (int32_t m = 0; m < K; ++m) {
+            int32_t id = nbr[(int64_t)j * K + m];
+            if (id < 0) continue;
+            const double *Pi = pcam + 3 * (int64_t)id;
+            double dv[3] = {x[0] - Pi[0], x[1] - Pi[1], x[2] - Pi[2]};
+            double dist = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+            double w = 1.0 / (dist > prm->eps_d ? dist : (double)prm->eps_d);
+            double gwi = 0.0;
+            for (int32_t k = 0; k < F; ++k) {
+                double fi_k = feats[(int64_t)id * F + k];
+                if (g_feats) g_feats[(int64_t)id * F + k] += w / Wsum[j] * dh[k];
+                gwi += dh[k] * (fi_k - fe[j][k]) / Wsum[j];
+            }
+            if (dist > prm->eps_d && g_pcam) {
+                double gdist = gwi * (-1.0 / (dist * dist));
+                for (int a = 0; a < 3; ++a) {
+                    g_pcam[3 * (int64_t)id + a] -= gdist * dv[a] / dist;
+                    gx[a] += gdist * dv[a] / dist;
+                }
+            }
+        }
+        gt[j] += gx[0] * d[0] + gx[1] * d[1] + gx[2] * d[2];
+        if (g_pcam)
+            for (int a = 0; a < 3; ++a) g_pcam[3 * (int64_t)src[j] + a] += gt[j] * d[a];
+    }
+    free(fe); free(acts_all); free(pre_all);
+#undef ACTS
+#undef PRE
+}
+
+/* Backward of the frame whose samples or_render produced.  grad_rgb (R x 3),
+ * grad_wsum (R, or NULL); accumulates into grad_feats (N x F), grad_pcam
+ * (N x 3, camera space) and grad_pworld (N x 3, world space); any output may
+ * be NULL.  Evaluated at the float32 camera-space positions of the contract
+ * (D1) and the float32 sample depths, so that it is the derivative of the
+ * frame that or_render computes. */
+int64_t or_backward(const float *pts, int64_t N, const float *feats, int32_t F, const or_camera *cam,
+                    const or_params *prm, const int32_t *dims, int32_t n_layers, const float *mlp,
+                    const int32_t *rays, int64_t R, const int64_t *sample_offset, const float *s_t,
+                    const int32_t *s_src, const int32_t *s_nbr, const double *grad_rgb, const double *grad_wsum,
+                    double *grad_feats, double *grad_pcam, double *grad_pworld)
+{
+    int32_t h;
+    float rdd;
+    if (or_window(cam, prm, &h, &rdd) != 0) return -1;
+    const int32_t K = prm->K;
+    int64_t W = cam->width, H = cam->height;
+    double *pc = (double *)malloc(sizeof(double) * 3 * (size_t)(N > 0 ? N : 1));
+    double *fd = (double *)malloc(sizeof(double) * (size_t)F * (size_t)(N > 0 ? N : 1));
+    double *gp = (double *)calloc(3 * (size_t)(N > 0 ? N : 1), sizeof(double));
+    for (int64_t i = 0; i < N; ++i) {
+        float X[3];
+        or_cam_point(cam, pts + 3 * i, X);
+        for (int a = 0; a < 3; ++a) pc[3 * i + a] = X[a];
+        for (int32_t k = 0; k < F; ++k) fd[i * F + k] = feats[i * F + k];
+    }
+    for (int64_t i = 0; i < R; ++i) {
+        int64_t pix = rays ? rays[i] : i;
+        if (pix < 0 || pix >= W * H) continue;
+        int64_t a = sample_offset[i], b = sample_offset[i + 1];
+        if (b == a) continue;
+        ray_t ray;
+        make_ray(cam, prm, rdd, (int)(pix % W), (int)(pix / W), &ray);
+        double rgb[3], ws;
+        ray_continuous(cam, prm, ray.d, ray.c, pc, pc, fd, F, dims, n_layers, mlp, K, (int32_t)(b - a), s_t + a,
+                       s_src + a, s_nbr + a * K, rgb, &ws, grad_rgb + 3 * i, grad_wsum ? grad_wsum[i] : 0.0,
+                       grad_feats, gp);
+    }
+    for (int64_t i = 0; i < N; ++i) {
+        if (grad_pcam)
+            for (int a = 0; a < 3; ++a) grad_pcam[3 * i + a] += gp[3 * i + a];
+        if (grad_pworld) /* dL/dp = R^T dL/dP */
+            for (int a = 0; a < 3; ++a)
+                grad_pworld[3 * i + a] += (double)cam->R[0 + a] * gp[3 * i] + (double)cam->R[3 + a] * gp[3 * i + 1] +
+                                          (double)cam->R[6 + a] * gp[3 * i + 2];
+    }
+    free(pc);
+    free(fd);
+    free(gp);
+    return 0;
+}
+
+/* Forward with frozen structure at caller-given camera-space positions
+ * (double, N x 3) and features (double, N x F), sample depths moving with
+ * their source point from the base positions pcam0 -- the function whose
+ * derivative or_backward returns (for finite-difference checks). */
+int64_t or_forward_frozen(const double *pcam, const double *pcam0, const double *feats, int32_t F,
+                          const or_camera *cam, const or_params *prm, const int32_t *dims, int32_t n_layers,
+                          const float *mlp, const int32_t *rays, int64_t R, const int64_t *sample_offset,
+                          const float *s_t, const int32_t *s_src, const int32_t *s_nbr, double *rgb, double *wsum)
+{
+    int32_t h;
+    float rdd;
+    if (or_window(cam, prm, &h, &rdd) != 0) return -1;
+    int64_t W = cam->width, H = cam->height;
+    for (int64_t i = 0; i < R; ++i) {
+        int64_t pix = rays ? rays[i] : i;
+        double bg = prm->bg_mode == 1 ? 1.0 : 0.0;
+        rgb[3 * i] = rgb[3 * i + 1] = rgb[3 * i + 2] = bg;
+        wsum[i] = 0.0;
+        if (pix < 0 || pix >= W * H) continue;
+        int64_t a = sample_offset[i], b = sample_offset[i + 1];
+        if (b == a) continue;
+        ray_t ray;
+        make_ray(cam, prm, rdd, (int)(pix % W), (int)(pix / W), &ray);
+        ray_continuous(cam, prm, ray.d, ray.c, pcam, pcam0, feats, F, dims, n_layers, mlp, prm->K,
+                       (int32_t)(b - a), s_t + a, s_src + a, s_nbr + a * prm->K, rgb + 3 * i, wsum + i, NULL, 0.0,
+                       NULL, NULL);
+    }
+    return 0;
 }

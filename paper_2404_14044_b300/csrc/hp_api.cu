@@ -37,6 +37,9 @@ struct hp_ctx {
     float raytab_key[8] = {0};
     // search state
     bool searched = false;
+    bool rendered = false;
+    const int32_t *rays = nullptr;   // pixel list of the last search (caller-owned)
+    const hp_samples *last_samples = nullptr;
     int64_t R = 0;
     int K = 0, n_max = 0;
     size_t search_bytes = 0;
@@ -152,7 +155,12 @@ size_t search_region_bytes(int64_t R, int n_max, int K)
     return al(256) + al(8 * (size_t)div_up(R > 0 ? R : 1, 256)) + 3 * al(4 * slots) + 2 * al(4 * slots * K);
 }
 
-size_t render_region_bytes(int64_t cap) { return al(16 * (size_t)(cap > 0 ? cap : 1)); }
+// decoded samples, then the backward's per-sample scratch
+size_t render_region_bytes(int64_t cap)
+{
+    const size_t c = (size_t)(cap > 0 ? cap : 1);
+    return al(16 * c) + al(16 * c) + al(4 * c);
+}
 
 // Region i of the workspace: 0 table, 1 search, 2 render.
 hp_status region(hp_ctx *ctx, int i, size_t bytes, char **out)
@@ -300,7 +308,7 @@ const char *hp_profile_kernel_name(int32_t id)
 {
     static const char *names[KID_COUNT] = {"k_project_count", "k_scan", "k_scatter", "k_bucket_sort",
                                            "k_search_select", "k_pack_samples", "k_aggregate_decode",
-                                           "k_composite"};
+                                           "k_composite", "k_composite_bwd", "k_decode_bwd"};
     return (id >= 0 && id < KID_COUNT) ? names[id] : "unknown";
 }
 
@@ -508,7 +516,9 @@ hp_status hp_search_sample(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n_r
     ctx->R = n_rays;
     ctx->K = K;
     ctx->n_max = n_samples;
+    ctx->rays = d_ray_pixels;
     ctx->searched = true;
+    ctx->rendered = false;
     return HP_OK;
 }
 
@@ -545,8 +555,49 @@ hp_status hp_aggregate_render(hp_ctx *ctx, const hp_samples *smp, int64_t n_rays
     if (a.decode == HP_DECODE_BF16 && !decode_tc_supported(a, true, nullptr)) return HP_ERR_INVALID_ARG;
     a.sample_out = reinterpret_cast<float4 *>(base);
     a.rgb = d_rgb; a.wsum = d_wsum; a.num_sms = ctx->num_sms;
-    if (render_smem_bytes(a) > 227 * 1024) return HP_ERR_INVALID_ARG;
+    const bool tc_ok = a.decode != HP_DECODE_FP32_SIMT && decode_tc_supported(a, a.decode == HP_DECODE_BF16, nullptr);
+    if (!tc_ok && render_smem_bytes(a) > 227 * 1024) return HP_ERR_INVALID_ARG;
     if (launch_render(a, st, &ctx->prof) != cudaSuccess) {
+        cudaGetLastError();
+        return HP_ERR_CUDA;
+    }
+    ctx->rendered = true;
+    return HP_OK;
+}
+
+hp_status hp_aggregate_render_backward(hp_ctx *ctx, const hp_samples *smp, int64_t n_rays, const float *d_points,
+                                       const float *d_feats, int32_t F, const hp_mlp *mlp, const float *d_grad_rgb,
+                                       const float *d_grad_wsum, float *d_grad_feats, float *d_grad_points,
+                                       void *stream)
+{
+    if (!ctx || !smp || !mlp) return HP_ERR_INVALID_ARG;
+    if (!ctx->built || !ctx->searched || !ctx->rendered || n_rays != ctx->R) return HP_ERR_NOT_BUILT;
+    if (mlp->n_layers < 1 || mlp->n_layers > HP_MLP_MAX_LAYERS || !mlp->d_params || mlp->dims[0] != F ||
+        mlp->dims[mlp->n_layers] != 4)
+        return HP_ERR_INVALID_ARG;
+    for (int l = 0; l <= mlp->n_layers; ++l)
+        if (mlp->dims[l] < 1 || mlp->dims[l] > HP_MLP_MAX_WIDTH) return HP_ERR_INVALID_ARG;
+    if (n_rays == 0) return HP_OK;
+    if (!d_grad_rgb || (ctx->N > 0 && (!d_feats || !d_points))) return HP_ERR_INVALID_ARG;
+    char *base = nullptr;
+    hp_status s;
+    if ((s = region(ctx, 2, render_region_bytes(smp->capacity), &base)) != HP_OK) return s;
+    const size_t c = (size_t)(smp->capacity > 0 ? smp->capacity : 1);
+    BwdArgs a{};
+    a.n_s = smp->n_s; a.sample_offset = smp->sample_offset; a.t = smp->t; a.ray = smp->ray; a.src = smp->src;
+    a.delta = smp->delta; a.nbr = smp->nbr; a.nbr_dist = smp->nbr_dist; a.capacity = smp->capacity;
+    a.R = n_rays; a.K = ctx->K; a.rays = ctx->rays; a.raytab = ctx->raytab; a.cam = ctx->cam;
+    a.mode = ctx->cfg.radius_mode; a.points = d_points; a.feats = d_feats; a.F = F; a.mlp = mlp->d_params;
+    a.n_layers = mlp->n_layers;
+    for (int l = 0; l <= mlp->n_layers; ++l) a.dims[l] = mlp->dims[l];
+    a.eps_d = ctx->cfg.eps_d; a.bg_mode = ctx->cfg.bg_mode;
+    a.sample_out = reinterpret_cast<const float4 *>(base);
+    a.go = reinterpret_cast<float4 *>(base + al(16 * c));
+    a.gt = reinterpret_cast<float *>(base + 2 * al(16 * c));
+    a.grad_rgb = d_grad_rgb; a.grad_wsum = d_grad_wsum; a.grad_feats = d_grad_feats; a.grad_points = d_grad_points;
+    a.num_sms = ctx->num_sms;
+    if (backward_smem_bytes(a) > 227 * 1024) return HP_ERR_INVALID_ARG;
+    if (launch_backward(a, static_cast<cudaStream_t>(stream), &ctx->prof) != cudaSuccess) {
         cudaGetLastError();
         return HP_ERR_CUDA;
     }

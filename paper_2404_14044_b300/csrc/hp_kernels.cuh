@@ -7,7 +7,8 @@ namespace hp {
 
 // Kernel ids of the per-kernel profiler (hp_profile_*).
 enum KernelId {
-    KID_PROJECT = 0, KID_SCAN, KID_SCATTER, KID_SORT, KID_SEARCH, KID_PACK, KID_DECODE, KID_COMPOSITE, KID_COUNT
+    KID_PROJECT = 0, KID_SCAN, KID_SCATTER, KID_SORT, KID_SEARCH, KID_PACK, KID_DECODE, KID_COMPOSITE,
+    KID_COMPOSITE_BWD, KID_DECODE_BWD, KID_COUNT
 };
 
 // Optional CUDA-event pairs around each launch, on the launching stream.
@@ -118,7 +119,43 @@ struct RenderArgs {
 __global__ void k_scan(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int64_t n, uint64_t *flags,
                        uint32_t *ticket, ErrWord *err, uint32_t spin_limit, int32_t skip_tile);
 
+struct BwdArgs {
+    const int32_t *n_s;
+    const int64_t *sample_offset;
+    const float *t;
+    const int32_t *ray;
+    const int32_t *src;
+    const float *delta;
+    const int32_t *nbr;
+    const float *nbr_dist;
+    int64_t capacity;
+    int64_t R;
+    int K;
+    const int32_t *rays;     // pixel of each ray (NULL: ray i is pixel i)
+    const float4 *raytab;    // per-pixel (d, cone c)
+    Cam cam;
+    int mode;
+    const float *points;     // world N x 3
+    const float *feats;
+    int F;
+    const float *mlp;
+    int n_layers;
+    int dims[HP_MLP_MAX_LAYERS + 1];
+    float eps_d;
+    int bg_mode;
+    const float4 *sample_out;   // forward (sigma, r, g, b) per sample
+    const float *grad_rgb;      // R x 3
+    const float *grad_wsum;     // R or NULL
+    float4 *go;                 // scratch: dL/d(MLP output) per sample
+    float *gt;                  // scratch: dL/dt_j through the Delta's
+    float *grad_feats;          // N x F, accumulated (NULL: skip)
+    float *grad_points;         // N x 3 world, accumulated (NULL: skip)
+    int num_sms;
+};
+
 cudaError_t launch_build(const BuildArgs &a, cudaStream_t st, Prof *prof);
+size_t backward_smem_bytes(const BwdArgs &a);
+cudaError_t launch_backward(const BwdArgs &a, cudaStream_t st, Prof *prof);
 size_t search_smem_bytes();
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof);
 size_t render_smem_bytes(const RenderArgs &a);

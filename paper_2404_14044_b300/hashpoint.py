@@ -25,10 +25,11 @@ MLP_MAX_LAYERS = 8
 
 # every symbol include/hashpoint.h declares
 SYMBOLS = ("hp_create", "hp_destroy", "hp_workspace_size", "hp_window", "hp_set_workspace", "hp_build_table",
-           "hp_table_info", "hp_table_copy", "hp_search_sample", "hp_aggregate_render", "hp_get_status",
+           "hp_table_info", "hp_table_copy", "hp_search_sample", "hp_aggregate_render",
+           "hp_aggregate_render_backward", "hp_get_status",
            "hp_debug_fault", "hp_profile_start", "hp_profile_stop", "hp_profile_kernel_name",
            "hp_selftest_mma", "hp_scan_noalloc", "hp_status_string", "hp_version")
-PROF_KERNELS = 8
+PROF_KERNELS = 10
 
 
 class HPError(RuntimeError):
@@ -90,6 +91,8 @@ def lib():
         L.hp_table_copy.argtypes = [vp, vp, vp, vp]
         L.hp_search_sample.argtypes = [vp, vp, i64, i32, i32, C.POINTER(Samples), vp]
         L.hp_aggregate_render.argtypes = [vp, C.POINTER(Samples), i64, vp, i32, C.POINTER(Mlp), vp, vp, vp]
+        L.hp_aggregate_render_backward.argtypes = [vp, C.POINTER(Samples), i64, vp, vp, i32, C.POINTER(Mlp), vp, vp,
+                                                   vp, vp, vp]
         L.hp_get_status.argtypes = [vp, vp, C.POINTER(i32), C.POINTER(i64)]
         L.hp_debug_fault.argtypes = [vp, i32, i32]
         L.hp_profile_start.argtypes = [vp, i32]
@@ -323,6 +326,31 @@ class HashPoint:
         rgb, wsum = self.aggregate_render(smp, feats, mlp_dims, mlp_params, stream=stream, decode=decode)
         return rgb, wsum, smp
 
+    def aggregate_render_backward(self, samples: SampleBuffers, points: torch.Tensor, feats: torch.Tensor,
+                                  mlp_dims: Sequence[int], mlp_params: torch.Tensor, grad_rgb: torch.Tensor,
+                                  grad_wsum: Optional[torch.Tensor] = None, grad_feats: Optional[torch.Tensor] = None,
+                                  grad_points: Optional[torch.Tensor] = None, stream=None):
+        """Accumulate dL/dfeats (N x F) and dL/dpoints (N x 3, world) for the
+        output gradients of the last aggregate_render (structure frozen)."""
+        R = self._R
+        grad_rgb = grad_rgb.contiguous().float()
+        if grad_wsum is not None:
+            grad_wsum = grad_wsum.contiguous().float()
+        if grad_feats is None:
+            grad_feats = torch.zeros_like(feats)
+        if grad_points is None:
+            grad_points = torch.zeros_like(points)
+        m = Mlp()
+        m.n_layers = len(mlp_dims) - 1
+        for i, d in enumerate(mlp_dims):
+            m.dims[i] = int(d)
+        m.d_params = mlp_params.data_ptr()
+        s = samples.struct()
+        _check(lib().hp_aggregate_render_backward(self._ctx, C.byref(s), R, _ptr(points), _ptr(feats), feats.shape[1],
+                                                  C.byref(m), _ptr(grad_rgb), _ptr(grad_wsum), _ptr(grad_feats),
+                                                  _ptr(grad_points), _stream(stream)), "hp_aggregate_render_backward")
+        return grad_feats, grad_points
+
     def selftest_mma(self, A: torch.Tensor, B: torch.Tensor, bf16: bool = False, stream=None) -> torch.Tensor:
         """D = A B^T on the tensor cores (A 128 x K, B N x K, fp16 or bf16)."""
         assert A.shape[0] == 128 and A.shape[1] == B.shape[1] and A.is_contiguous() and B.is_contiguous()
@@ -348,3 +376,31 @@ class HashPoint:
 
     def debug_fault(self, skip_tile: int, spin_limit: int = 0):
         _check(lib().hp_debug_fault(self._ctx, int(skip_tile), int(spin_limit)), "hp_debug_fault")
+
+
+class RenderFunction(torch.autograd.Function):
+    """Differentiable frame: (feats, points) -> (rgb, wsum) through the
+    library's forward kernels and its backward kernels.  The search and
+    selection are treated as constants (index outputs)."""
+
+    @staticmethod
+    def forward(ctx, feats, points, hp, camera, mlp_dims, mlp_params, rays, decode):
+        rgb, wsum, smp = hp.render(points.detach().contiguous(), feats.detach().contiguous(), camera, mlp_dims,
+                                   mlp_params, rays=rays, decode=decode)
+        ctx.hp, ctx.smp, ctx.mlp_dims, ctx.mlp_params = hp, smp, list(mlp_dims), mlp_params
+        ctx.save_for_backward(feats, points)
+        return rgb, wsum
+
+    @staticmethod
+    def backward(ctx, grad_rgb, grad_wsum):
+        feats, points = ctx.saved_tensors
+        if grad_rgb is None:
+            grad_rgb = torch.zeros(ctx.hp._R, 3, device=feats.device)
+        gf, gp = ctx.hp.aggregate_render_backward(ctx.smp, points.detach().contiguous(), feats.detach().contiguous(),
+                                                  ctx.mlp_dims, ctx.mlp_params, grad_rgb, grad_wsum)
+        return gf, gp, None, None, None, None, None, None
+
+
+def render_differentiable(hp: HashPoint, feats, points, camera, mlp_dims, mlp_params, rays=None, decode=DECODE_FP32):
+    """rgb (R x 3), wsum (R) with autograd to feats and points."""
+    return RenderFunction.apply(feats, points, hp, camera, mlp_dims, mlp_params, rays, decode)
