@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--impl", default="hashpoint", choices=["hashpoint", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-proposal", action="store_true")
     ap.add_argument("--points", type=int, default=1_000_000)
     ap.add_argument("--res", type=int, default=800)
     return ap.parse_args()
@@ -205,6 +206,105 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------- learned proposal + BF16
+
+def psnr(a, b):
+    import torch
+    mse = torch.mean((a.double() - b.double()) ** 2).item()
+    return float("inf") if mse == 0 else 10.0 * math.log10(1.0 / mse)
+
+
+def proposal_section(hp, H, pts_np, feats_np, params, dims, mlp_np, cams, steps, dev, flush):
+    """Learned depth-interval proposal + BF16 decode against the plain FP32
+    path: train the proposal on the plain search's intervals of 64 views;
+    fit features for 200 steps to a target image (FP64 oracle render of view
+    0 with a second feature draw) with the library's render + backward; then
+    compare speed and PSNR against that target, and judge the proposal's
+    misses with the plain search."""
+    import torch
+    import oracle
+    R = cams[0].width * cams[0].height
+    t = lambda a: torch.from_numpy(a).to(dev)
+    pts, mlp = t(pts_np), t(mlp_np)
+    # 1) proposal training on 64 views
+    train_cams = scenes.random_sphere_cameras(64, 4.0, 100, width=cams[0].width, height=cams[0].height)
+    state = H.ProposalState(dev, seed=0)
+    t0 = time.perf_counter()
+    for it in range(8 * 64):
+        cam = train_cams[it % 64]
+        hp.build_table(pts, cam, params.r)
+        plain = hp.search_sample(None, params.K, params.n_max)
+        hp.proposal_train_step(None, plain, state, lr=3e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    l = state.loss.cpu().numpy()
+    # 2) target and fitted features (view 0)
+    cam = cams[0]
+    tgt_np = oracle.render(pts_np, scenes.random_features(len(pts_np), 32, 7), cam, params, dims, mlp_np,
+                           nthreads=os.cpu_count() or 1)["rgb"]
+    tgt = t(tgt_np.astype(np.float32))
+    feats = t(feats_np).clone()
+    opt = torch.optim.Adam([feats], lr=2e-2)
+    rng = np.random.default_rng(0)
+    for it in range(200):
+        rays = t(np.sort(rng.choice(R, 8192, replace=False)).astype(np.int32))
+        rgb, wsum, smp = hp.render(pts, feats, cam, dims, mlp, rays=rays)
+        g = (2.0 / rgb.numel()) * (rgb - tgt[rays.long()])
+        gf, _ = hp.aggregate_render_backward(smp, pts, feats, dims, mlp, g, want_points=False)
+        feats.grad = gf
+        opt.step()
+    # 3) full frames: plain FP32 vs proposal + BF16 (and each change alone)
+    def run(mode, decode, n):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for k in range(n + 2):
+            flush.zero_()
+            if k >= 2:
+                ev[k - 2][0].record()
+            hp.build_table(pts, cam, params.r)
+            if mode == "plain":
+                smp = hp.search_sample(None, params.K, params.n_max)
+            else:
+                iv = hp.proposal_infer(None, state.bf16)
+                smp = hp.search_sample_proposal(None, params.K, params.n_max, iv, fallback_count=fb)
+            rgb, wsum = hp.aggregate_render(smp, feats, dims, mlp, decode=decode)
+            if k >= 2:
+                ev[k - 2][1].record()
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / n
+        return ms, rgb.clone(), smp
+    n = max(5, min(steps, 20))
+    fb = torch.zeros(1, dtype=torch.int32, device=dev)
+    kernels = {}
+    for mode, dec in (("plain", H.DECODE_FP32), ("proposal", H.DECODE_BF16)):
+        hp.profile_start(256)
+        run(mode, dec, 1)
+        kernels[mode] = {k: round(v[0] / max(v[1], 1), 5) for k, v in hp.profile_stop().items() if v[1]}
+    ms_plain, rgb_plain, smp_plain = run("plain", H.DECODE_FP32, n)
+    ms_bf16, rgb_bf16, _ = run("plain", H.DECODE_BF16, n)
+    ms_prop, rgb_prop32, _ = run("proposal", H.DECODE_FP32, n)
+    ms_both, rgb_both, smp_prop = run("proposal", H.DECODE_BF16, n)
+    code, detail = hp.status()
+    if code != 0:
+        raise SystemExit(f"device status after proposal pass: {H.status_string(code)} ({detail})")
+    # misses judged by the plain search: rays whose samples differ
+    a, b = smp_plain.packed(R), smp_prop.packed(R)
+    oa, ob = a["sample_offset"].numpy(), b["sample_offset"].numpy()
+    sa, sb = a["src"].numpy(), b["src"].numpy()
+    hit = np.nonzero(a["n_s"].numpy() > 0)[0]
+    miss = float(np.mean([not np.array_equal(sa[oa[i]:oa[i + 1]], sb[ob[i]:ob[i + 1]]) for i in hit]))
+    p_plain, p_both = psnr(rgb_plain, tgt), psnr(rgb_both, tgt)
+    return {"value": R / (ms_both / 1e3), "unit": "rays/s", "ms_per_step": ms_both,
+            "speedup_vs_plain_fp32": ms_plain / ms_both,
+            "ms_plain_fp32": ms_plain, "ms_plain_bf16": ms_bf16, "ms_proposal_fp32": ms_prop,
+            "psnr_plain_fp32_db": p_plain, "psnr_proposal_bf16_db": p_both, "psnr_drop_db": p_plain - p_both,
+            "psnr_bf16_vs_plain_db": psnr(rgb_bf16, rgb_plain), "psnr_proposal_vs_plain_db": psnr(rgb_prop32, rgb_plain),
+            "miss_rate": miss, "fallback_rays": int(fb.item()), "per_kernel_ms": kernels, "train": {"views": 64, "steps": 8 * 64, "seconds": t_train,
+                                         "final_loss": float(l[0] / max(l[1], 1))},
+            "protocol": "target = FP64 oracle render of view 0 with a second feature draw; features fitted "
+                        "200 Adam steps (8192 rays/step) with hp_aggregate_render_backward; misses = hit rays "
+                        "whose sample sources differ from the plain search"}
+
+
 # ------------------------------------------------------------------ GPU side
 
 def run_gpu(args):
@@ -349,6 +449,10 @@ def run_gpu(args):
     if code != 0:
         raise SystemExit(f"device status after e2e pass: {H.status_string(code)} ({detail})")
 
+    prop = None
+    if rank == 0 and world == 1 and not args.no_proposal:
+        prop = proposal_section(hp, H, pts_np, feats_np, params, dims, mlp_np, views, args.steps, dev, flush)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, t_build, t_frame, cores, t_call = oracle_frame_rate(pts_np, feats_np, params, dims, mlp_np, cams[0], 1)
@@ -365,6 +469,7 @@ def run_gpu(args):
                                        "samples_last_frame": S, "visible_points_last_frame": Nv,
                                        "buckets": P, "unique_points_gathered": U}),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "proposal_bf16": prop,
                 "clocks": clk, "per_kernel_ms": {k: round(v["ms_avg"], 5) for k, v in per_kernel.items()},
                 "wall_s_timed_region": t_wall}
         print(json.dumps(line), flush=True)

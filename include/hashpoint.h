@@ -208,6 +208,50 @@ hp_status hp_search_sample(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n_r
 hp_status hp_aggregate_render(hp_ctx *ctx, const hp_samples *samples, int64_t n_rays, const float *d_feats,
                               int32_t F, const hp_mlp *mlp, float *d_rgb, float *d_wsum, void *stream);
 
+/* ---- Learned depth-interval proposal (an extension beyond the paper, like
+ * the learned samplers it cites as related work).  A 16 -> 32 -> 32 -> 2 MLP
+ * (ReLU) reads a ray's depth histogram -- the camera depths of the points in
+ * the 3 x 3 buckets around its pixel in 16 bins over [t_near, t_far], as
+ * log(1 + n) -- and outputs (a, b): t0 = t_near + (t_far - t_near) sigmoid(a),
+ * t1 = t0 + (t_far - t0) sigmoid(b).  Parameters (HP_PROP_PARAMS floats):
+ * W0 [32][16], b0 [32], W1 [32][32], b1 [32], W2 [2][32], b2 [2]. */
+#define HP_PROP_BINS 16
+#define HP_PROP_PARAMS 1666
+
+/* Interval [t0, t1] (d_interval, R x 2 floats) for every ray from the current
+ * table, with BF16 weights (d_weights_bf16, HP_PROP_PARAMS) and FP32
+ * accumulation; a ray whose 3 x 3 buckets are empty gets [t_near, t_far].
+ * Rays: as hp_search_sample. */
+hp_status hp_proposal_infer(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n_rays, const uint16_t *d_weights_bf16,
+                            float *d_interval, void *stream);
+
+/* One Adam step of the proposal on a batch of rays of the current table,
+ * against the first and last sample depths of a plain hp_search_sample of
+ * those rays (`plain`).  The loss per ray is
+ * softplus(k (t0n - s0n + m))/k + softplus(k (s1n - t1n + m))/k + l (t1n - t0n)
+ * in units of t_far - t_near (k = 200, m = 0.01, l = 0.05), averaged over rays
+ * with samples.  d_params (FP32 master), d_adam_m, d_adam_v and d_grad
+ * (zero on the first call) hold HP_PROP_PARAMS floats each; d_weights_bf16
+ * receives the updated BF16 copy; d_loss (2 floats, optional) receives the
+ * summed loss and the number of rays used.  step counts from 1. */
+hp_status hp_proposal_train_step(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n_rays, const hp_samples *plain,
+                                 float *d_params, float *d_adam_m, float *d_adam_v, float *d_grad,
+                                 uint16_t *d_weights_bf16, int32_t step, float lr, float *d_loss, void *stream);
+
+/* hp_search_sample restricted per ray to the depth interval d_interval
+ * (R x 2, e.g. from hp_proposal_infer): only points with t in [t0, t1] are
+ * candidates, and in the fixed-radius mode the window shrinks to the bound
+ * that t0 allows.  Rays that keep no sample are searched again without the
+ * restriction (plain-search fallback) unless their whole plain window holds
+ * no point, so a ray is empty only if the plain search finds nothing either;
+ * also when the plain search accepts a point in front of t0, or behind t1
+ * while the selection ran out of candidates (decision contract D12).
+ * Outputs as hp_search_sample; d_fallback_count (device, optional) receives
+ * the number of rays searched again. */
+hp_status hp_search_sample_proposal(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n_rays, int32_t K,
+                                    int32_t n_samples, const float *d_interval, const hp_samples *out,
+                                    uint32_t *d_fallback_count, void *stream);
+
 /* Backward of hp_aggregate_render (Sec. 3.4 + Eq. 2) with respect to the point
  * features and the point positions, the discrete structure of the last
  * hp_search_sample (neighbour sets, samples) held fixed -- it is not
@@ -245,7 +289,7 @@ hp_status hp_debug_fault(hp_ctx *ctx, int32_t skip_tile, int32_t spin_limit);
  * and launch counts per kernel into ms[HP_PROF_KERNELS] and
  * launches[HP_PROF_KERNELS] (either may be NULL), and stops recording.
  * Kernel ids: see hp_profile_kernel_name. */
-#define HP_PROF_KERNELS 10
+#define HP_PROF_KERNELS 12
 hp_status hp_profile_start(hp_ctx *ctx, int32_t max_launches);
 hp_status hp_profile_stop(hp_ctx *ctx, double *ms, int32_t *launches);
 const char *hp_profile_kernel_name(int32_t id);

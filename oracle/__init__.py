@@ -62,7 +62,7 @@ def lib():
         L.or_build_table.argtypes = [fp, C.c_int64, C.POINTER(Camera), C.c_int32, u32p, i32p, fp]
         L.or_build_table.restype = C.c_int64
         L.or_render.argtypes = [fp, C.c_int64, fp, C.c_int32, C.POINTER(Camera), C.POINTER(Params), i32p,
-                                C.c_int32, fp, i32p, C.c_int64, C.c_int32, C.c_int32, i32p, i32p, i32p, i64p,
+                                C.c_int32, fp, i32p, C.c_int64, fp, C.c_int32, C.c_int32, i32p, i32p, i32p, i64p,
                                 fp, i32p, i32p, i32p, fp, dp, dp, dp, dp]
         L.or_render.restype = C.c_int64
         L.or_ray_candidates.argtypes = [fp, C.c_int64, C.POINTER(Camera), C.POINTER(Params), C.c_int32,
@@ -149,8 +149,11 @@ def ray_candidates(pts, cam, params, pixel: int, brute: bool, cap: int = 4096):
 
 
 def render(pts, feats, cam, params, mlp_dims, mlp_params, rays=None, brute=False, nthreads=1,
-           per_sample=False):
-    """Run the whole frame.  Returns a dict of numpy arrays (see or_render)."""
+           per_sample=False, intervals=None):
+    """Run the whole frame.  Returns a dict of numpy arrays (see or_render).
+    ``intervals`` (R x 2 float32): per-ray depth restriction with the plain
+    search as the fallback for rays it leaves empty."""
+    iv = None if intervals is None else np.ascontiguousarray(intervals, np.float32)
     pts = np.ascontiguousarray(pts, np.float32)
     feats = np.ascontiguousarray(feats, np.float32)
     F = feats.shape[1]
@@ -171,7 +174,7 @@ def render(pts, feats, cam, params, mlp_dims, mlp_params, rays=None, brute=False
     S = lib().or_render(
         _p(pts, C.c_float), len(pts), _p(feats, C.c_float), F, C.byref(camera_struct(cam)),
         C.byref(params_struct(params)), _p(dims, C.c_int32), len(dims) - 1, _p(mlp, C.c_float),
-        _p(rays_a, C.c_int32), R, int(brute), int(nthreads),
+        _p(rays_a, C.c_int32), R, _p(iv, C.c_float), int(brute), int(nthreads),
         _p(out["n_s"], C.c_int32), _p(out["primary"], C.c_int32), _p(out["cand_count"], C.c_int32),
         _p(out["sample_offset"], C.c_int64), _p(out["t"], C.c_float), _p(out["ray"], C.c_int32),
         _p(out["src"], C.c_int32), _p(out["nbr"], C.c_int32), _p(out["nbr_dist"], C.c_float),

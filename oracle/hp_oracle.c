@@ -53,6 +53,19 @@
  *                     with w_j > eps_w, in order, at most n.  gap_k = 0 drops the
  *                     cluster gate: every candidate from j* on with w_j > eps_w
  *                     (the gamma-controlled move towards multi-surface sampling)
+ *   D12 restricted    (learned-interval search) per-ray depth range [tn, tf] =
+ *       search        [max(t_near, t0), min(t_far, t1)]; fixed radius: window
+ *                     zlo = max((tn*cos_m) - (r*sin_m), z_near),
+ *                     lim = ((win/zlo)*1.001) + 0.001, hr = floor(lim + 0.5) if lim < h
+ *                     (cos_m, sin_m, win: float of the double image-corner terms);
+ *                     candidates: accepted (D5) with t in [tn, tf] inside the hr
+ *                     window; it falls back to the plain search when it keeps no
+ *                     sample (and the full window is not empty), when D5 accepts
+ *                     a point with t < tn, or when the selection ran out of
+ *                     candidates (no gap / n / gamma*T <= eps_w stop) while D5
+ *                     accepts a point with t > tf -- unless a sample was kept,
+ *                     gap_k > 0 and (tf - t_last) > max(gap_k, 1) * r(t_last)
+ *                     for the last restricted candidate t_last
  *   exp32             Cody & Waite range reduction (two-part ln 2) and a
  *                     degree-7 Taylor polynomial in Horner form, scaled by 2^k
  */
@@ -182,12 +195,13 @@ static float radius_at(const or_params *p, const ray_t *ray, float t)
     return p->radius_mode == 0 ? p->r : t * ray->c;
 }
 
-/* D5: returns 1 and t when the camera-space point P is accepted. */
-static int accept_point(const or_camera *c, const or_params *p, const ray_t *ray, const float *P, float *t_out)
+/* D5: returns 1 and t when the camera-space point P is accepted (depth
+ * range [tn, tf], normally [t_near, t_far]). */
+static int accept_point(const or_params *p, const ray_t *ray, const float *P, float tn, float tf, float *t_out)
 {
     const float *d = ray->d;
     float t = (P[0] * d[0] + P[1] * d[1]) + P[2] * d[2];
-    if (!(t >= c->t_near && t <= c->t_far)) return 0;
+    if (!(t >= tn && t <= tf)) return 0;
     float ex = fmaf(-t, d[0], P[0]);
     float ey = fmaf(-t, d[1], P[1]);
     float ez = fmaf(-t, d[2], P[2]);
@@ -345,7 +359,20 @@ typedef struct {
  * tests every input point (the brute-force search of Sec. 3.5); otherwise the
  * s x s window of buckets around the ray's pixel is walked and empty buckets
  * are skipped (Sec. 3.2).  Returns the count; *out is malloc'ed. */
-static int64_t ray_candidates(const frame_t *f, const ray_t *ray, int pu, int pv, int brute, cand_t **out)
+static int64_t ray_candidates_w(const frame_t *f, const ray_t *ray, int pu, int pv, int brute, float tn, float tf,
+                                int hr, int *early, int *late, cand_t **out);
+
+static int64_t ray_candidates(const frame_t *f, const ray_t *ray, int pu, int pv, int brute, float tn, float tf,
+                              cand_t **out)
+{
+    return ray_candidates_w(f, ray, pu, pv, brute, tn, tf, f->h, NULL, NULL, out);
+}
+
+/* As ray_candidates, over the window of half-width hr <= h; early / late (if
+ * given) report points the plain range [t_near, t_far] accepts with t < tn /
+ * t > tf. */
+static int64_t ray_candidates_w(const frame_t *f, const ray_t *ray, int pu, int pv, int brute, float tn, float tf,
+                                int hr, int *early, int *late, cand_t **out)
 {
     int64_t cap = 64, n = 0;
     cand_t *cs = (cand_t *)malloc(sizeof(cand_t) * (size_t)cap);
@@ -355,24 +382,31 @@ static int64_t ray_candidates(const frame_t *f, const ray_t *ray, int pu, int pv
             float X[3];
             or_cam_point(f->cam, f->pts + 3 * i, X);
             if (!(X[2] > f->cam->z_near)) continue;
-            if (!accept_point(f->cam, f->prm, ray, X, &t)) continue;
+            if (!accept_point(f->prm, ray, X, tn, tf, &t)) continue;
             if (n == cap) { cap *= 2; cs = (cand_t *)realloc(cs, sizeof(cand_t) * (size_t)cap); }
             cs[n].t = t; cs[n].id = (int32_t)i;
             cs[n].P[0] = X[0]; cs[n].P[1] = X[1]; cs[n].P[2] = X[2];
             ++n;
         }
     } else {
-        int h = f->h;
+        int h = f->h, off = h - hr;
         int64_t Wp = f->cam->width + 2 * h;
-        for (int dy = 0; dy <= 2 * h; ++dy) {
-            for (int dx = 0; dx <= 2 * h; ++dx) {
-                /* pixel (pu-h+dx, pv-h+dy) has padded key (pv+dy)*Wp + (pu+dx) */
-                int64_t k = (int64_t)(pv + dy) * Wp + (pu + dx);
+        for (int dy = 0; dy <= 2 * hr; ++dy) {
+            for (int dx = 0; dx <= 2 * hr; ++dx) {
+                /* pixel (pu-hr+dx, pv-hr+dy) has padded key (pv+off+dy)*Wp + (pu+off+dx) */
+                int64_t k = (int64_t)(pv + off + dy) * Wp + (pu + off + dx);
                 uint32_t a = f->start[k], b = f->start[k + 1];
                 if (a == b) continue;     /* count check: nothing to test */
                 for (uint32_t i = a; i < b; ++i) {
                     const float *X = f->pos + 3 * (int64_t)i;
-                    if (!accept_point(f->cam, f->prm, ray, X, &t)) continue;
+                    if (early || late) {
+                        float tp;
+                        if (accept_point(f->prm, ray, X, f->cam->t_near, f->cam->t_far, &tp)) {
+                            if (tp < tn && early) *early = 1;
+                            if (tp > tf && late) *late = 1;
+                        }
+                    }
+                    if (!accept_point(f->prm, ray, X, tn, tf, &t)) continue;
                     if (n == cap) { cap *= 2; cs = (cand_t *)realloc(cs, sizeof(cand_t) * (size_t)cap); }
                     cs[n].t = t; cs[n].id = f->ids[i];
                     cs[n].P[0] = X[0]; cs[n].P[1] = X[1]; cs[n].P[2] = X[2];
@@ -416,12 +450,13 @@ typedef struct {
  * exp(-d_j^2/beta^2), w_j = alpha_j prod_{k<j}(1-alpha_k) (Eq. weight); the
  * samples are the primary cluster's candidates with w_j > eps_w. */
 static void select_samples(const frame_t *f, const ray_t *ray, const cand_t *cs, int64_t C, int32_t K,
-                           int32_t n_max, ray_result_t *res, float *d_out, float *w_out)
+                           int32_t n_max, ray_result_t *res, float *d_out, float *w_out, int *stopped)
 {
     const or_params *p = f->prm;
     nd_t *nd = (nd_t *)malloc(sizeof(nd_t) * (size_t)(C > 0 ? C : 1));
     float *w = (float *)malloc(sizeof(float) * (size_t)(C > 0 ? C : 1));
     int32_t *knn = (int32_t *)malloc(sizeof(int32_t) * (size_t)(C > 0 ? C : 1) * (size_t)K);
+    float *tafter = (float *)malloc(sizeof(float) * (size_t)(C > 0 ? C : 1));
     float *kd = (float *)malloc(sizeof(float) * (size_t)(C > 0 ? C : 1) * (size_t)K);
     float T = 1.0f;
     for (int64_t j = 0; j < C; ++j) {
@@ -452,6 +487,7 @@ static void select_samples(const frame_t *f, const ray_t *ray, const cand_t *cs,
         if (d_out) d_out[j] = dj;
         if (w_out) w_out[j] = w[j];
         T = T * (1.0f - alpha);
+        tafter[j] = T;                 /* T after candidate j */
     }
     res->n_s = 0;
     res->primary = -1;
@@ -477,10 +513,30 @@ static void select_samples(const frame_t *f, const ray_t *ray, const cand_t *cs,
             }
         }
     }
+    /* did the depth-ordered selection stop (gap after j*, n samples, or
+     * gamma * T_j <= eps_w so that no later weight can pass) before running
+     * out of candidates? */
+    if (stopped) {
+        *stopped = 0;
+        int64_t js = -1;
+        int32_t ns = 0;
+        for (int64_t j = 0; j < C && !*stopped; ++j) {
+            if (js >= 0 && p->gap_k > 0.0f) {
+                float gap = cs[j].t - cs[j - 1].t;
+                if (!(gap <= p->gap_k * radius_at(p, ray, cs[j - 1].t))) { *stopped = 1; break; }
+            }
+            if (w[j] > p->eps_w) {
+                if (js < 0) js = j;
+                if (++ns == n_max) { *stopped = 1; break; }
+            }
+            if (!(p->gamma * tafter[j] > p->eps_w)) *stopped = 1;
+        }
+    }
     free(nd);
     free(w);
     free(knn);
     free(kd);
+    free(tafter);
 }
 
 /* ------------------------------------------- aggregation, decode, composite */
@@ -573,7 +629,7 @@ typedef struct {
  * error: -1 bad arguments, -2 out of memory, -3 a ray pixel out of range. */
 int64_t or_render(const float *pts, int64_t N, const float *feats, int32_t F, const or_camera *cam,
                   const or_params *prm, const int32_t *dims, int32_t n_layers, const float *mlp,
-                  const int32_t *rays, int64_t R, int32_t brute, int32_t nthreads,
+                  const int32_t *rays, int64_t R, const float *intervals, int32_t brute, int32_t nthreads,
                   int32_t *n_s, int32_t *primary, int32_t *cand_count, int64_t *sample_offset,
                   float *s_t, int32_t *s_ray, int32_t *s_src, int32_t *s_nbr, float *s_dist,
                   double *rgb, double *wsum, double *s_feat, double *s_out4)
@@ -598,6 +654,18 @@ int64_t or_render(const float *pts, int64_t N, const float *feats, int32_t F, co
     if (!start || !ids || !pos || !head || !st || !ssrc || !snbr || !sdist) return -2;
     if (!brute && or_build_table(pts, N, cam, h, start, ids, pos) < 0) return -2;
     frame_t fr = {pts, N, cam, prm, h, rdd, start, ids, pos};
+    /* D12 image-corner terms of the restricted window (float of double) */
+    float rcos, rsin, rwin;
+    {
+        double fx = cam->fx, fy = cam->fy, cx = cam->cx, cy = cam->cy;
+        double ax = fmax(fabs(0.5 - cx), fabs(((double)cam->width - 0.5) - cx)) / fx;
+        double ay = fmax(fabs(0.5 - cy), fabs(((double)cam->height - 0.5) - cy)) / fy;
+        double q = ax * ax + ay * ay;
+        double rr = prm->r;
+        rcos = (float)(1.0 / sqrt(1.0 + q));
+        rsin = (float)sqrt(q / (1.0 + q));
+        rwin = (float)fmax(fx * rr * sqrt(1.0 + ax * ax), fy * rr * sqrt(1.0 + ay * ay));
+    }
     int bad = 0;
 #pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads > 0 ? nthreads : 1) reduction(| : bad)
     for (int64_t i = 0; i < R; ++i) {
@@ -607,12 +675,45 @@ int64_t or_render(const float *pts, int64_t N, const float *feats, int32_t F, co
         ray_t ray;
         make_ray(cam, prm, rdd, pu, pv, &ray);
         cand_t *cs;
-        int64_t C = ray_candidates(&fr, &ray, pu, pv, brute, &cs);
-        int64_t Ck = C < prm->cand_cap ? C : prm->cand_cap;   /* keep the cand_cap smallest (t, id) */
         ray_result_t res;
         res.nbr = snbr + i * n_max * K;
         res.ndist = sdist + i * n_max * K;
-        select_samples(&fr, &ray, cs, Ck, K, n_max, &res, NULL, NULL);
+        int64_t C = 0;
+        int fallback = 1;
+        if (intervals) {
+            /* restricted to the ray's interval (D12); fall back to the plain search on a miss */
+            float tn = intervals[2 * i] > cam->t_near ? intervals[2 * i] : cam->t_near;
+            float tf = intervals[2 * i + 1] < cam->t_far ? intervals[2 * i + 1] : cam->t_far;
+            int hr = h;
+            if (prm->radius_mode == 0) {
+                float zlo = tn * rcos - prm->r * rsin;
+                if (!(zlo >= cam->z_near)) zlo = cam->z_near;
+                float lim = (rwin / zlo) * 1.001f + 1e-3f;
+                if (lim < (float)h) { int q = (int)floorf(lim + 0.5f); hr = q < h ? q : h; }
+            }
+            int early = 0, late = 0, stopped = 0;
+            C = ray_candidates_w(&fr, &ray, pu, pv, brute, tn, tf, hr, &early, &late, &cs);
+            int64_t Ck = C < prm->cand_cap ? C : prm->cand_cap;
+            select_samples(&fr, &ray, cs, Ck, K, n_max, &res, NULL, NULL, &stopped);
+            int full_empty = 1;
+            for (int dy = 0; dy <= 2 * h && full_empty; ++dy) {
+                int64_t kb = (int64_t)(pv + dy) * (W + 2 * h) + pu;
+                if (start[kb + 2 * h + 1] != start[kb]) full_empty = 0;
+            }
+            int late_ok = 0;
+            if (res.n_s > 0 && prm->gap_k > 0.0f && Ck > 0) {
+                float tl = cs[Ck - 1].t;
+                float g = prm->gap_k > 1.0f ? prm->gap_k : 1.0f;
+                late_ok = (tf - tl) > g * radius_at(prm, &ray, tl);
+            }
+            fallback = (res.n_s == 0 && !full_empty) || early || (!stopped && late && !late_ok);
+            if (fallback) { free(cs); cs = NULL; }
+        }
+        if (fallback) {
+            C = ray_candidates(&fr, &ray, pu, pv, brute, cam->t_near, cam->t_far, &cs);
+            int64_t Ck = C < prm->cand_cap ? C : prm->cand_cap;   /* keep the cand_cap smallest (t, id) */
+            select_samples(&fr, &ray, cs, Ck, K, n_max, &res, NULL, NULL, NULL);
+        }
         res.cand_count = (int32_t)C;
         head[i].n_s = res.n_s;
         head[i].primary = res.primary;
@@ -680,7 +781,7 @@ int64_t or_ray_candidates(const float *pts, int64_t N, const or_camera *cam, con
     ray_t ray;
     make_ray(cam, prm, rdd, (int)(pixel % W), (int)(pixel / W), &ray);
     cand_t *cs;
-    int64_t C = ray_candidates(&fr, &ray, (int)(pixel % W), (int)(pixel / W), brute, &cs);
+    int64_t C = ray_candidates(&fr, &ray, (int)(pixel % W), (int)(pixel / W), brute, cam->t_near, cam->t_far, &cs);
     for (int64_t i = 0; i < C && i < cap; ++i) { cid[i] = cs[i].id; ct[i] = cs[i].t; }
     free(cs); free(start); free(ids); free(pos);
     return C;
@@ -736,7 +837,7 @@ int32_t or_select(const or_camera *cam, const or_params *prm, int32_t pixel, int
     ray_result_t res;
     res.nbr = out_nbr;
     res.ndist = out_dist;
-    select_samples(&fr, &ray, cs, C, prm->K, prm->n_max, &res, d_out, w_out);
+    select_samples(&fr, &ray, cs, C, prm->K, prm->n_max, &res, d_out, w_out, NULL);
     for (int32_t m = 0; m < res.n_s; ++m) { out_t[m] = res.t[m]; out_src[m] = res.src[m]; }
     *jstar_out = -1;
     if (res.n_s > 0) {

@@ -152,7 +152,8 @@ size_t table_region_bytes(int64_t N, int64_t P, int64_t npix)
 size_t search_region_bytes(int64_t R, int n_max, int K)
 {
     const size_t slots = (size_t)(R > 0 ? R : 1) * n_max;
-    return al(256) + al(8 * (size_t)div_up(R > 0 ? R : 1, 256)) + 3 * al(4 * slots) + 2 * al(4 * slots * K);
+    return al(256) + al(8 * (size_t)div_up(R > 0 ? R : 1, 256)) + 3 * al(4 * slots) + 2 * al(4 * slots * K) +
+           al(4 * (size_t)(R > 0 ? R : 1));          // fallback list of the proposal-restricted search
 }
 
 // decoded samples, then the backward's per-sample scratch
@@ -308,7 +309,8 @@ const char *hp_profile_kernel_name(int32_t id)
 {
     static const char *names[KID_COUNT] = {"k_project_count", "k_scan", "k_scatter", "k_bucket_sort",
                                            "k_search_select", "k_pack_samples", "k_aggregate_decode",
-                                           "k_composite", "k_composite_bwd", "k_decode_bwd"};
+                                           "k_composite", "k_composite_bwd", "k_decode_bwd", "k_prop_infer",
+                                           "k_search_select_fallback"};
     return (id >= 0 && id < KID_COUNT) ? names[id] : "unknown";
 }
 
@@ -462,8 +464,9 @@ hp_status hp_table_copy(const hp_ctx *ctx, uint32_t *d_start, float *d_points, v
     return HP_OK;
 }
 
-hp_status hp_search_sample(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n_rays, int32_t K, int32_t n_samples,
-                           const hp_samples *out, void *stream)
+static hp_status search_impl(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n_rays, int32_t K, int32_t n_samples,
+                             const hp_samples *out, const float *d_interval, uint32_t *d_fallback_count,
+                             void *stream)
 {
     if (!ctx || !out) return HP_ERR_INVALID_ARG;
     if (!ctx->built) return HP_ERR_NOT_BUILT;
@@ -504,7 +507,20 @@ hp_status hp_search_sample(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n_r
         a.slot_src = reinterpret_cast<int32_t *>(base + o);  o += al(4 * slots);
         a.slot_delta = reinterpret_cast<float *>(base + o);  o += al(4 * slots);
         a.slot_nbr = reinterpret_cast<int32_t *>(base + o);  o += al(4 * slots * K);
-        a.slot_dist = reinterpret_cast<float *>(base + o);
+        a.slot_dist = reinterpret_cast<float *>(base + o);   o += al(4 * slots * K);
+        a.fallback = reinterpret_cast<int32_t *>(base + o);
+        a.fallback_count = a.ticket + 1;
+        a.interval = reinterpret_cast<const float2 *>(d_interval);
+        if (d_interval) {
+            // per-ray window bound of the restricted search (same terms as derive_window)
+            const double fx = ctx->cam.fx, fy = ctx->cam.fy, cx = ctx->cam.cx, cy = ctx->cam.cy;
+            const double ax = std::fmax(std::fabs(0.5 - cx), std::fabs(((double)ctx->cam.width - 0.5) - cx)) / fx;
+            const double ay = std::fmax(std::fabs(0.5 - cy), std::fabs(((double)ctx->cam.height - 0.5) - cy)) / fy;
+            const double q = ax * ax + ay * ay;
+            a.cos_max = (float)(1.0 / std::sqrt(1.0 + q));
+            a.sin_max = (float)std::sqrt(q / (1.0 + q));
+            a.win_fx = (float)std::fmax(fx * ctx->r * std::sqrt(1.0 + ax * ax), fy * ctx->r * std::sqrt(1.0 + ay * ay));
+        }
         a.err = ctx->d_err;
         a.spin_limit = ctx->spin_limit;
         if (launch_search(a, st, &ctx->prof) != cudaSuccess) {
@@ -512,6 +528,12 @@ hp_status hp_search_sample(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n_r
             return HP_ERR_CUDA;
         }
         ctx->raytab_valid = true;
+        if (d_interval && d_fallback_count &&
+            cudaMemcpyAsync(d_fallback_count, a.fallback_count, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            return HP_ERR_CUDA;
+        }
     }
     ctx->R = n_rays;
     ctx->K = K;
@@ -519,6 +541,63 @@ hp_status hp_search_sample(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n_r
     ctx->rays = d_ray_pixels;
     ctx->searched = true;
     ctx->rendered = false;
+    return HP_OK;
+}
+
+hp_status hp_search_sample(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n_rays, int32_t K, int32_t n_samples,
+                           const hp_samples *out, void *stream)
+{
+    return search_impl(ctx, d_ray_pixels, n_rays, K, n_samples, out, nullptr, nullptr, stream);
+}
+
+hp_status hp_search_sample_proposal(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n_rays, int32_t K,
+                                    int32_t n_samples, const float *d_interval, const hp_samples *out,
+                                    uint32_t *d_fallback_count, void *stream)
+{
+    if (!d_interval) return HP_ERR_INVALID_ARG;
+    return search_impl(ctx, d_ray_pixels, n_rays, K, n_samples, out, d_interval, d_fallback_count, stream);
+}
+
+static PropArgs prop_args(const hp_ctx *ctx, const int32_t *d_rays, int64_t n_rays)
+{
+    PropArgs a{};
+    a.cam = ctx->cam; a.h = ctx->h; a.Wp = ctx->Wp; a.Hp = ctx->Hp; a.start = ctx->start; a.spts = ctx->spts;
+    a.rays = d_rays; a.R = n_rays;
+    return a;
+}
+
+hp_status hp_proposal_infer(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n_rays, const uint16_t *d_weights_bf16,
+                            float *d_interval, void *stream)
+{
+    if (!ctx || !d_weights_bf16 || n_rays < 0 || (n_rays > 0 && !d_interval)) return HP_ERR_INVALID_ARG;
+    if (!ctx->built) return HP_ERR_NOT_BUILT;
+    if (!d_ray_pixels && n_rays != 0 && n_rays != (int64_t)ctx->cam.width * ctx->cam.height) return HP_ERR_INVALID_ARG;
+    PropArgs a = prop_args(ctx, d_ray_pixels, n_rays);
+    a.weights_bf16 = d_weights_bf16;
+    a.interval = reinterpret_cast<float2 *>(d_interval);
+    if (launch_prop_infer(a, static_cast<cudaStream_t>(stream), &ctx->prof) != cudaSuccess) {
+        cudaGetLastError();
+        return HP_ERR_CUDA;
+    }
+    return HP_OK;
+}
+
+hp_status hp_proposal_train_step(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n_rays, const hp_samples *plain,
+                                 float *d_params, float *d_adam_m, float *d_adam_v, float *d_grad,
+                                 uint16_t *d_weights_bf16, int32_t step, float lr, float *d_loss, void *stream)
+{
+    if (!ctx || !plain || !d_params || !d_adam_m || !d_adam_v || !d_grad || !d_weights_bf16 || step < 1 ||
+        !(lr > 0.f) || n_rays < 0)
+        return HP_ERR_INVALID_ARG;
+    if (!ctx->built) return HP_ERR_NOT_BUILT;
+    if (!d_ray_pixels && n_rays != 0 && n_rays != (int64_t)ctx->cam.width * ctx->cam.height) return HP_ERR_INVALID_ARG;
+    PropArgs a = prop_args(ctx, d_ray_pixels, n_rays);
+    a.params = d_params; a.grad = d_grad; a.loss = d_loss; a.weights_out = d_weights_bf16;
+    a.n_s = plain->n_s; a.sample_offset = plain->sample_offset; a.t = plain->t;
+    if (launch_prop_train(a, d_adam_m, d_adam_v, step, lr, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+        cudaGetLastError();
+        return HP_ERR_CUDA;
+    }
     return HP_OK;
 }
 

@@ -8,7 +8,7 @@ namespace hp {
 // Kernel ids of the per-kernel profiler (hp_profile_*).
 enum KernelId {
     KID_PROJECT = 0, KID_SCAN, KID_SCATTER, KID_SORT, KID_SEARCH, KID_PACK, KID_DECODE, KID_COMPOSITE,
-    KID_COMPOSITE_BWD, KID_DECODE_BWD, KID_COUNT
+    KID_COMPOSITE_BWD, KID_DECODE_BWD, KID_PROP_INFER, KID_SEARCH_FALLBACK, KID_COUNT
 };
 
 // Optional CUDA-event pairs around each launch, on the launching stream.
@@ -68,6 +68,12 @@ struct SearchArgs {
     const float4 *spts;
     float4 *raytab;          // [W*H] per-pixel (dx, dy, dz, cone c)
     int raytab_stale;        // recompute the ray table before searching
+    const float2 *interval;  // per-ray [t0, t1] (proposal-restricted search), NULL: plain
+    float win_fx, cos_max, sin_max;  // per-ray window bound of the restricted search (fixed radius)
+    int32_t *fallback;       // rays whose restricted search kept nothing (original indices)
+    uint32_t *fallback_count;
+    const int32_t *ray_map;  // fallback pass: original index of listed ray i
+    const uint32_t *count_ptr;   // fallback pass: number of listed rays (device)
     const int32_t *rays;     // NULL: ray i is pixel i
     int64_t R;
     int32_t *n_s;
@@ -119,6 +125,24 @@ struct RenderArgs {
 __global__ void k_scan(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int64_t n, uint64_t *flags,
                        uint32_t *ticket, ErrWord *err, uint32_t spin_limit, int32_t skip_tile);
 
+struct PropArgs {
+    Cam cam;
+    int h, Wp, Hp;
+    const uint32_t *start;
+    const float4 *spts;
+    const int32_t *rays;
+    int64_t R;
+    const uint16_t *weights_bf16;   // inference weights
+    float2 *interval;               // inference output
+    float *params;                  // training: FP32 master weights
+    float *grad;
+    float *loss;                    // [2]: summed loss, rays used
+    uint16_t *weights_out;          // training: refreshed BF16 copy
+    const int32_t *n_s;             // training targets: the plain search's samples
+    const int64_t *sample_offset;
+    const float *t;
+};
+
 struct BwdArgs {
     const int32_t *n_s;
     const int64_t *sample_offset;
@@ -155,6 +179,8 @@ struct BwdArgs {
 
 cudaError_t launch_build(const BuildArgs &a, cudaStream_t st, Prof *prof);
 size_t backward_smem_bytes(const BwdArgs &a);
+cudaError_t launch_prop_infer(const PropArgs &a, cudaStream_t st, Prof *prof);
+cudaError_t launch_prop_train(const PropArgs &a, float *m, float *v, int step, float lr, cudaStream_t st);
 cudaError_t launch_backward(const BwdArgs &a, cudaStream_t st, Prof *prof);
 size_t search_smem_bytes();
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof);

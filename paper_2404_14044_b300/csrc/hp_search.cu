@@ -43,10 +43,11 @@ __host__ __device__ inline SearchSmem search_layout()
 
 // Radius test: t = (X dx + Y dy) + Z dz, e = P - t d (one rounding per axis),
 // rho2 = (ex^2 + ey^2) + ez^2; accept iff t in [t_near, t_far] and rho2 <= r(t)^2.
-__device__ __forceinline__ bool accept_point(const SearchArgs &a, const Ray &ray, const float4 &p, float &t)
+__device__ __forceinline__ bool accept_point(const SearchArgs &a, const Ray &ray, const float4 &p, float tn, float tf,
+                                             float &t)
 {
     t = dadd(dadd(dmul(p.x, ray.dx), dmul(p.y, ray.dy)), dmul(p.z, ray.dz));
-    if (!(t >= a.cam.t_near && t <= a.cam.t_far)) return false;
+    if (!(t >= tn && t <= tf)) return false;
     const float ex = dfma(-t, ray.dx, p.x);
     const float ey = dfma(-t, ray.dy, p.y);
     const float ez = dfma(-t, ray.dz, p.z);
@@ -158,16 +159,19 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select(const Searc
     uint64_t *ck = reinterpret_cast<uint64_t *>(smem + L.ck) + warp * kCandCap;
     uint8_t *ci = reinterpret_cast<uint8_t *>(smem + L.ci) + warp * kCandCap;
 
-    const int K = a.K, n_max = a.n_max, span = 2 * a.h + 1;
+    const int K = a.K, n_max = a.n_max;
     const int64_t npix = (int64_t)a.cam.width * a.cam.height;
+    const int64_t R_eff = a.count_ptr ? (int64_t)*a.count_ptr : a.R;
 
     for (;;) {
         int rl = 0;
         if (lane == 0) rl = atomicAdd(&s_next, 1);
         rl = __shfl_sync(kFull, rl, 0);
         if (rl >= rpc) break;
-        const int64_t ri = tile * rpc + rl;
-        if (ri >= a.R) break;
+        const int64_t rl_idx = tile * rpc + rl;
+        if (rl_idx >= R_eff) break;
+        // ri: the ray's index in the outputs (fallback pass: from the list)
+        const int64_t ri = a.ray_map ? (int64_t)__ldg(a.ray_map + rl_idx) : rl_idx;
         const int pix = a.rays ? __ldg(a.rays + ri) : (int)ri;
         if (pix < 0 || pix >= npix) {
             if (lane == 0) {
@@ -186,16 +190,48 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select(const Searc
         ray.dz = rt.z;
         ray.c = rt.w;
 
+        // depth range and window half-width of this ray: the plain search uses
+        // [t_near, t_far] and h; the proposal-restricted search the ray's
+        // interval and the (smaller) window bound that follows from its t0
+        float tn = a.cam.t_near, tf = a.cam.t_far;
+        int hr = a.h;
+        if (a.interval) {
+            const float2 iv = __ldg(a.interval + ri);
+            tn = fmaxf(tn, iv.x);
+            tf = fminf(tf, iv.y);
+            if (a.mode == HP_RADIUS_FIXED) {
+                // window bound for t >= tn (contract step D12, written out with
+                // single roundings so the CPU reference walks the same window)
+                const float zlo = fmaxf(dsub(dmul(tn, a.cos_max), dmul(a.r, a.sin_max)), a.cam.z_near);
+                const float lim = dadd(dmul(ddiv(a.win_fx, zlo), 1.001f), 1e-3f);
+                if (lim < (float)a.h) hr = min(a.h, (int)floorf(dadd(lim, 0.5f)));
+            }
+        }
+        const int span = 2 * hr + 1, off = a.h - hr;
+        // restricted search: does the full window hold any point at all?  If
+        // not, the ray is empty for the plain search too and needs no fallback
+        bool full_window_empty = false;
+        if (a.interval) {
+            const int fspan = 2 * a.h + 1;
+            int flen = 0;
+            for (int q = lane; q < fspan; q += 32) {
+                const int64_t kb = (int64_t)(pv + q) * a.Wp + pu;
+                flen += (int)(__ldg(a.start + kb + fspan) - __ldg(a.start + kb));
+            }
+            full_window_empty = __ballot_sync(kFull, flen != 0) == 0;
+        }
+
         // ---- window walk.  The s rows' runs are concatenated into one index
         // space (lane q holds row q's [lo, lo+len) and its exclusive offset),
         // so every load instruction serves 32 points whatever the row lengths.
         int kept = 0, total = 0;
+        bool early_hit = false, late_hit = false;
         for (int r0 = 0; r0 < span; r0 += 32) {
             const int nrows = min(32, span - r0);
             uint32_t lo = 0;
             int len = 0;
             if (lane < nrows) {
-                const int64_t kb = (int64_t)(pv + r0 + lane) * a.Wp + pu;
+                const int64_t kb = (int64_t)(pv + off + r0 + lane) * a.Wp + pu + off;
                 lo = __ldg(a.start + kb);
                 len = (int)(__ldg(a.start + kb + span) - lo);
             }
@@ -218,7 +254,17 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select(const Searc
                 float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (v < tot) {
                     p = __ldg(a.spts + rlo + (uint32_t)(v - rex));
-                    acc = accept_point(a, ray, p, t);
+                    if (!a.interval) {
+                        acc = accept_point(a, ray, p, tn, tf, t);
+                    } else {
+                        // restricted: points the plain search would accept outside
+                        // [t0, t1] flag a possible miss (a surface in front, or
+                        // the cluster running on behind t1)
+                        const bool plain = accept_point(a, ray, p, a.cam.t_near, a.cam.t_far, t);
+                        acc = plain && t >= tn && t <= tf;
+                        if (plain && t < tn) early_hit = true;
+                        if (plain && t > tf) late_hit = true;
+                    }
                 }
                 const uint64_t key = ((uint64_t)__float_as_uint(t) << 32) | (uint32_t)__float_as_int(p.w);
                 append_candidates(acc, key, p, lane, lt_mask, a.cand_cap, ck, cp, kept, total);
@@ -295,6 +341,8 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select(const Searc
         int jstar = -1, ns = 0, prim = -1;
         const int64_t slot0 = ri * n_max;
         bool done = false;
+        early_hit = __any_sync(kFull, early_hit);
+        late_hit = __any_sync(kFull, late_hit);
         for (int c0 = 0; c0 < C && !done; c0 += 32) {
             const int j = c0 + lane;
             float tj = 0.0f, alpha = 0.0f;
@@ -394,6 +442,20 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select(const Searc
             a.n_s[ri] = ns;
             a.primary[ri] = prim;
             a.cand_count[ri] = total;
+            // fall back to the plain search when the restricted one is empty
+            // (unless the whole window is), when the plain search accepts a
+            // point in front of t0, or when the selection ran out of
+            // candidates while the plain search has more behind t1
+            // a point behind t1 cannot change the result when a sample was kept
+            // and the last restricted candidate lies more than max(gap_k, 1) r
+            // before t1: the gap rule stops the plain selection before it
+            bool late_ok = false;
+            if (a.interval && jstar >= 0 && a.gap_k > 0.0f && C > 0) {
+                const float tl = __uint_as_float((uint32_t)(ck[C - 1] >> 32));
+                late_ok = dsub(tf, tl) > dmul(fmaxf(a.gap_k, 1.0f), radius_at(a.mode, a.r, ray, tl));
+            }
+            const bool miss = (ns == 0 && !full_window_empty) || early_hit || (!done && late_hit && !late_ok);
+            if (a.interval && a.fallback && miss) a.fallback[atomicAdd(a.fallback_count, 1u)] = (int32_t)ri;
         }
         __syncwarp();
     }
@@ -479,10 +541,25 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof)
               : a.K <= 16 ? k_search_select<16> : k_search_select<32>;
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
+    if (a.interval && a.fallback_count &&
+        (e = cudaMemsetAsync(a.fallback_count, 0, sizeof(uint32_t), st)) != cudaSuccess)
+        return e;
     prof_begin(prof, st, KID_SEARCH);
     kern<<<(unsigned)blocks, kSearchWarps * 32, smem, st>>>(a);
     prof_end(prof, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (a.interval && a.fallback) {
+        // plain search for the rays the restricted search left empty
+        SearchArgs b = a;
+        b.interval = nullptr;
+        b.ray_map = a.fallback;
+        b.count_ptr = a.fallback_count;
+        b.raytab_stale = 0;
+        prof_begin(prof, st, KID_SEARCH_FALLBACK);
+        kern<<<(unsigned)blocks, kSearchWarps * 32, smem, st>>>(b);
+        prof_end(prof, st);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     prof_begin(prof, st, KID_PACK);
     k_pack_samples<<<(unsigned)tiles, 256, 0, st>>>(a);
     prof_end(prof, st);

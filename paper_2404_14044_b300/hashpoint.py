@@ -28,8 +28,11 @@ SYMBOLS = ("hp_create", "hp_destroy", "hp_workspace_size", "hp_window", "hp_set_
            "hp_table_info", "hp_table_copy", "hp_search_sample", "hp_aggregate_render",
            "hp_aggregate_render_backward", "hp_get_status",
            "hp_debug_fault", "hp_profile_start", "hp_profile_stop", "hp_profile_kernel_name",
-           "hp_selftest_mma", "hp_scan_noalloc", "hp_status_string", "hp_version")
-PROF_KERNELS = 10
+           "hp_selftest_mma", "hp_scan_noalloc", "hp_proposal_infer", "hp_proposal_train_step",
+           "hp_search_sample_proposal", "hp_status_string", "hp_version")
+PROF_KERNELS = 12
+PROP_PARAMS = 1666
+PROP_BINS = 16
 
 
 class HPError(RuntimeError):
@@ -100,6 +103,10 @@ def lib():
         L.hp_profile_kernel_name.argtypes = [i32]
         L.hp_profile_kernel_name.restype = C.c_char_p
         L.hp_scan_noalloc.argtypes = [vp, vp, i64, vp, vp]
+        L.hp_proposal_infer.argtypes = [vp, vp, i64, vp, vp, vp]
+        L.hp_proposal_train_step.argtypes = [vp, vp, i64, C.POINTER(Samples), vp, vp, vp, vp, vp, i32, C.c_float, vp,
+                                             vp]
+        L.hp_search_sample_proposal.argtypes = [vp, vp, i64, i32, i32, vp, C.POINTER(Samples), vp, vp]
         L.hp_selftest_mma.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp]
         L.hp_status_string.argtypes = [i32]
         L.hp_status_string.restype = C.c_char_p
@@ -296,6 +303,40 @@ class HashPoint:
         self._R = R
         return out
 
+    def search_sample_proposal(self, rays: Optional[torch.Tensor], K: int, n_samples: int, interval: torch.Tensor,
+                               out: Optional[SampleBuffers] = None, fallback_count: Optional[torch.Tensor] = None,
+                               stream=None) -> SampleBuffers:
+        """search_sample restricted to per-ray intervals with the plain search as
+        fallback; fallback_count (int32[1] device, optional) gets the number of
+        rays searched again."""
+        R = rays.shape[0] if rays is not None else self._cam.width * self._cam.height
+        if out is None:
+            out = SampleBuffers.allocate(R, K, n_samples, self.device)
+        s = out.struct()
+        _check(lib().hp_search_sample_proposal(self._ctx, _ptr(rays), R, int(K), int(n_samples), _ptr(interval),
+                                               C.byref(s), _ptr(fallback_count), _stream(stream)),
+               "hp_search_sample_proposal")
+        self._R = R
+        return out
+
+    def proposal_infer(self, rays: Optional[torch.Tensor], weights_bf16: torch.Tensor,
+                       interval: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        R = rays.shape[0] if rays is not None else self._cam.width * self._cam.height
+        if interval is None:
+            interval = torch.empty(max(R, 1), 2, dtype=torch.float32, device=self.device)[:R]
+        _check(lib().hp_proposal_infer(self._ctx, _ptr(rays), R, _ptr(weights_bf16), _ptr(interval),
+                                       _stream(stream)), "hp_proposal_infer")
+        return interval
+
+    def proposal_train_step(self, rays: Optional[torch.Tensor], plain: SampleBuffers, state: "ProposalState",
+                            lr: float = 3e-3, stream=None) -> None:
+        R = rays.shape[0] if rays is not None else self._cam.width * self._cam.height
+        state.step += 1
+        s = plain.struct()
+        _check(lib().hp_proposal_train_step(self._ctx, _ptr(rays), R, C.byref(s), _ptr(state.params), _ptr(state.m),
+                                            _ptr(state.v), _ptr(state.grad), _ptr(state.bf16), state.step, float(lr),
+                                            _ptr(state.loss), _stream(stream)), "hp_proposal_train_step")
+
     def aggregate_render(self, samples: SampleBuffers, feats: torch.Tensor, mlp_dims: Sequence[int],
                          mlp_params: torch.Tensor, rgb: Optional[torch.Tensor] = None,
                          wsum: Optional[torch.Tensor] = None, stream=None, decode: int = DECODE_FP32):
@@ -329,17 +370,26 @@ class HashPoint:
     def aggregate_render_backward(self, samples: SampleBuffers, points: torch.Tensor, feats: torch.Tensor,
                                   mlp_dims: Sequence[int], mlp_params: torch.Tensor, grad_rgb: torch.Tensor,
                                   grad_wsum: Optional[torch.Tensor] = None, grad_feats: Optional[torch.Tensor] = None,
-                                  grad_points: Optional[torch.Tensor] = None, stream=None):
+                                  grad_points: Optional[torch.Tensor] = None, stream=None, want_points: bool = True):
         """Accumulate dL/dfeats (N x F) and dL/dpoints (N x 3, world) for the
-        output gradients of the last aggregate_render (structure frozen)."""
+        output gradients of the last aggregate_render (structure frozen).
+        want_points=False skips the position gradient (returns None for it)."""
         R = self._R
+        N, F = feats.shape
         grad_rgb = grad_rgb.contiguous().float()
+        assert grad_rgb.numel() == 3 * R and points.shape == (N, 3)
         if grad_wsum is not None:
             grad_wsum = grad_wsum.contiguous().float()
+            assert grad_wsum.numel() == R
         if grad_feats is None:
             grad_feats = torch.zeros_like(feats)
-        if grad_points is None:
+        assert grad_feats.is_contiguous() and grad_feats.dtype == torch.float32 and grad_feats.numel() == N * F
+        if not want_points:
+            grad_points = None
+        elif grad_points is None:
             grad_points = torch.zeros_like(points)
+        if grad_points is not None:
+            assert grad_points.is_contiguous() and grad_points.dtype == torch.float32 and grad_points.numel() == 3 * N
         m = Mlp()
         m.n_layers = len(mlp_dims) - 1
         for i, d in enumerate(mlp_dims):
@@ -376,6 +426,32 @@ class HashPoint:
 
     def debug_fault(self, skip_tile: int, spin_limit: int = 0):
         _check(lib().hp_debug_fault(self._ctx, int(skip_tile), int(spin_limit)), "hp_debug_fault")
+
+
+class ProposalState:
+    """FP32 master weights, Adam moments, gradient, BF16 copy and loss of the
+    proposal MLP (device tensors)."""
+
+    def __init__(self, device, seed: int = 0):
+        g = torch.Generator().manual_seed(seed)
+        shapes = [(32, PROP_BINS), (32,), (32, 32), (32,), (2, 32), (2,)]
+        parts = []
+        for sh in shapes:
+            if len(sh) == 2:
+                lim = (6.0 / sh[1]) ** 0.5
+                parts.append((torch.rand(sh, generator=g) * 2 - 1).mul(lim).reshape(-1))
+            else:
+                parts.append(torch.zeros(sh))
+        # start wide: t0 near t_near, t1 near t_far
+        parts[-1] = torch.tensor([-3.0, 3.0])
+        self.params = torch.cat(parts).to(device).contiguous()
+        assert self.params.numel() == PROP_PARAMS
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.grad = torch.zeros_like(self.params)
+        self.bf16 = self.params.to(torch.bfloat16).view(torch.int16).contiguous()
+        self.loss = torch.zeros(2, device=device)
+        self.step = 0
 
 
 class RenderFunction(torch.autograd.Function):
