@@ -141,6 +141,37 @@ def algorithmic(kernel, N, Nv, P, R, S, K, F, dims, U):
     return table[kernel]
 
 
+# DRAM bytes (read + write) of one launch, from one ncu capture of
+# `bench.py --steps 1 --warmup 1` at 800x800 (first view), keyed by the
+# profiler's kernel name.  Each entry carries the SHA-256 of the sources the
+# kernel is compiled from when it was captured; once those change the figure
+# no longer describes the kernel and the roofline reports traffic = null.
+NCU_TRAFFIC = {
+    "k_search_select": {"bytes": 53920256 + 52001536,
+                        "sources": ("hp_search.cu", "hp_common.cuh", "hp_kernels.cuh"),
+                        "sha256": "dbdd1547d59219f0d77fa440e6de10723b39e61c98b2df8c3aab6d435c3c8f0e"},
+    "k_aggregate_decode": {"bytes": 78054656 + 1039616,
+                           "sources": ("hp_decode_tc.cu", "hp_tc.cuh", "hp_common.cuh", "hp_kernels.cuh"),
+                           "sha256": "79162e6cc5f3761f284e75d85c79d43076e04e31c0b6a78b9ada1cb964754c37"},
+}
+
+
+def sources_sha256(names):
+    import hashlib
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2404_14044_b300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def ncu_traffic(kernel):
+    e = NCU_TRAFFIC.get(kernel)
+    if e is None or e["sha256"] is None or sources_sha256(e["sources"]) != e["sha256"]:
+        return None
+    return e["bytes"]
+
+
 def agg_gather_bytes(S, K, F, U):
     return 8 * K * S + 4 * F * U + 16 * S
 
@@ -307,6 +338,25 @@ def proposal_section(hp, H, pts_np, feats_np, params, dims, mlp_np, cams, steps,
 
 # ------------------------------------------------------------------ GPU side
 
+def rank_views(n_views, rank, world):
+    """View indices a rank renders, in order: rank r takes views r, r + N,
+    r + 2N, ... (mod the view count), so every rank does the same per-step
+    work (weak scaling) and no data crosses ranks."""
+    return [(rank + i * world) % n_views for i in range(n_views)]
+
+
+def job_rate(local_ms, rays_per_step, steps, world, device):
+    """Whole-job throughput: the slowest rank's time (max over ranks) against
+    the rays all ranks processed.  Returns (rays/s, max ms)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return world * rays_per_step * steps / (ms / 1e3), ms
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -333,7 +383,7 @@ def run_gpu(args):
     rgb = torch.empty(R, 3, dtype=torch.float32, device=dev)
     wsum = torch.empty(R, dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    views = [cams[(rank + i * world) % N_VIEWS] for i in range(N_VIEWS)]
+    views = [cams[i] for i in rank_views(N_VIEWS, rank, world)]
 
     def frame(cam, p=pts):
         hp.build_table(p, cam, params.r)
@@ -371,11 +421,7 @@ def run_gpu(args):
     code, detail = hp.status()
     if code != 0:
         raise SystemExit(f"device status after timed pass: {H.status_string(code)} ({detail})")
-    t = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    dev_ms_max = float(t.item())
-    value = world * R * args.steps / (dev_ms_max / 1e3)
+    value, dev_ms_max = job_rate(dev_ms, R, args.steps, world, dev)
 
     # per-frame sizes (last view) for the algorithmic traffic
     S = int(smp.sample_offset[R].item())
@@ -404,14 +450,14 @@ def run_gpu(args):
         peak = fp32_peak_tflops(148, clock)
         achieved = units / (dom_ms / 1e3) / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": ncu_traffic(dom),
                 "peak_source": "derived: 148 SMs x 128 FP32 FMA lanes x 2 FLOP x 2032 MHz",
                 "gather_bytes_per_launch": agg_gather_bytes(S, params.K, 32, U)}
     else:
         peak = pk.get("hbm_gbs", 6400.0)
         achieved = units / (dom_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": ncu_traffic(dom),
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in pk else "fallback 6400 GB/s"}
 
     # ---- end to end: per-frame point positions H2D from pinned memory, image D2H
@@ -438,10 +484,7 @@ def run_gpu(args):
         e1.record()
         barrier()
         e2e_ms = e0.elapsed_time(e1)
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * R * args.steps / (float(t.item()) / 1e3), "unit": "rays/s",
+        e2e = {"value": job_rate(e2e_ms, R, args.steps, world, dev)[0], "unit": "rays/s",
                "h2d_bytes_per_step": int(host_pts.numel() * 4), "d2h_bytes_per_step": int(R * 16),
                "what": "per step: point positions H2D (pinned), table+search+render through the C-ABI, "
                        "rgb+weight-sum D2H (pinned); features and MLP weights resident"}
