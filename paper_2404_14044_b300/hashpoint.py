@@ -432,7 +432,10 @@ class ProposalState:
     """FP32 master weights, Adam moments, gradient, BF16 copy and loss of the
     proposal MLP (device tensors)."""
 
-    def __init__(self, device, seed: int = 0):
+    def __init__(self, device, seed: int = 0, init: Optional[torch.Tensor] = None):
+        if init is not None:
+            self._set(device, init.detach().float().reshape(-1))
+            return
         g = torch.Generator().manual_seed(seed)
         shapes = [(32, PROP_BINS), (32,), (32, 32), (32,), (2, 32), (2,)]
         parts = []
@@ -444,7 +447,10 @@ class ProposalState:
                 parts.append(torch.zeros(sh))
         # start wide: t0 near t_near, t1 near t_far
         parts[-1] = torch.tensor([-3.0, 3.0])
-        self.params = torch.cat(parts).to(device).contiguous()
+        self._set(device, torch.cat(parts))
+
+    def _set(self, device, params):
+        self.params = params.to(device).contiguous()
         assert self.params.numel() == PROP_PARAMS
         self.m = torch.zeros_like(self.params)
         self.v = torch.zeros_like(self.params)

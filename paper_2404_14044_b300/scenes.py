@@ -341,6 +341,18 @@ def random_mlp(dims: List[int], seed: int, sigma_bias: float = 0.0) -> np.ndarra
     return np.ascontiguousarray(np.concatenate(parts).astype(np.float32))
 
 
+def proposal_params(seed: int, out_bias=(-3.0, 3.0), scale: float = 1.0) -> np.ndarray:
+    """Parameters of the 16-32-32-2 depth-interval network in the packed
+    layout above (He-uniform weights times ``scale``, zero hidden biases);
+    the output biases start the interval wide (t0 near t_near, t1 near
+    t_far) by default."""
+    th = random_mlp([16, 32, 32, 2], seed).astype(np.float64) * scale
+    th[-2:] = out_bias
+    out = th.astype(np.float32)
+    assert out.size == 1666
+    return out
+
+
 def mlp_param_count(dims: List[int]) -> int:
     return sum(dims[l] * dims[l + 1] + dims[l + 1] for l in range(len(dims) - 1))
 
