@@ -289,7 +289,7 @@ hp_status hp_debug_fault(hp_ctx *ctx, int32_t skip_tile, int32_t spin_limit);
  * and launch counts per kernel into ms[HP_PROF_KERNELS] and
  * launches[HP_PROF_KERNELS] (either may be NULL), and stops recording.
  * Kernel ids: see hp_profile_kernel_name. */
-#define HP_PROF_KERNELS 12
+#define HP_PROF_KERNELS 13
 hp_status hp_profile_start(hp_ctx *ctx, int32_t max_launches);
 hp_status hp_profile_stop(hp_ctx *ctx, double *ms, int32_t *launches);
 const char *hp_profile_kernel_name(int32_t id);

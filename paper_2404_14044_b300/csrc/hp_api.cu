@@ -153,7 +153,8 @@ size_t search_region_bytes(int64_t R, int n_max, int K)
 {
     const size_t slots = (size_t)(R > 0 ? R : 1) * n_max;
     return al(256) + al(8 * (size_t)div_up(R > 0 ? R : 1, 256)) + 3 * al(4 * slots) + 2 * al(4 * slots * K) +
-           al(4 * (size_t)(R > 0 ? R : 1));          // fallback list of the proposal-restricted search
+           al(4 * (size_t)(R > 0 ? R : 1)) +         // fallback list of the proposal-restricted search
+           al(4 * (size_t)(R > 0 ? R : 1));          // rays handed to the warp-per-ray search
 }
 
 // decoded samples, then the backward's per-sample scratch
@@ -310,7 +311,8 @@ const char *hp_profile_kernel_name(int32_t id)
     static const char *names[KID_COUNT] = {"k_project_count", "k_scan", "k_scatter", "k_bucket_sort",
                                            "k_search_select", "k_pack_samples", "k_aggregate_decode",
                                            "k_composite", "k_composite_bwd", "k_decode_bwd", "k_prop_infer",
-                                           "k_search_select_fallback"};
+                                           "k_search_select_fallback", "k_search_select_wide"};
+    static_assert(KID_COUNT == HP_PROF_KERNELS, "profiler kernel count");
     return (id >= 0 && id < KID_COUNT) ? names[id] : "unknown";
 }
 
@@ -508,8 +510,13 @@ static hp_status search_impl(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n
         a.slot_delta = reinterpret_cast<float *>(base + o);  o += al(4 * slots);
         a.slot_nbr = reinterpret_cast<int32_t *>(base + o);  o += al(4 * slots * K);
         a.slot_dist = reinterpret_cast<float *>(base + o);   o += al(4 * slots * K);
-        a.fallback = reinterpret_cast<int32_t *>(base + o);
+        a.fallback = reinterpret_cast<int32_t *>(base + o);  o += al(4 * (size_t)n_rays);
         a.fallback_count = a.ticket + 1;
+        a.wide = reinterpret_cast<int32_t *>(base + o);
+        a.wide_count = a.ticket + 2;
+        a.pull = reinterpret_cast<unsigned long long *>(a.ticket + 4);
+        a.lane_units = a.ticket + 3;
+        a.n_sm = ctx->num_sms;
         a.interval = reinterpret_cast<const float2 *>(d_interval);
         if (d_interval) {
             // per-ray window bound of the restricted search (same terms as derive_window)

@@ -13,7 +13,6 @@ constexpr int kHMax = 64;            // largest window half-width
 constexpr int kCandCap = 128;        // candidate buffer per ray (power of two)
 constexpr int kMaxK = 32;            // neighbours per candidate
 constexpr int kMaxSamples = 16;      // samples per ray
-constexpr int kSearchRaysPerBlock = 32;   // rays per search block (warps pull them one at a time)
 constexpr int kSearchWarps = 8;
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;        // per thread: tile = 2048 entries

@@ -8,7 +8,7 @@ namespace hp {
 // Kernel ids of the per-kernel profiler (hp_profile_*).
 enum KernelId {
     KID_PROJECT = 0, KID_SCAN, KID_SCATTER, KID_SORT, KID_SEARCH, KID_PACK, KID_DECODE, KID_COMPOSITE,
-    KID_COMPOSITE_BWD, KID_DECODE_BWD, KID_PROP_INFER, KID_SEARCH_FALLBACK, KID_COUNT
+    KID_COMPOSITE_BWD, KID_DECODE_BWD, KID_PROP_INFER, KID_SEARCH_FALLBACK, KID_SEARCH_WIDE, KID_COUNT
 };
 
 // Optional CUDA-event pairs around each launch, on the launching stream.
@@ -72,6 +72,11 @@ struct SearchArgs {
     float win_fx, cos_max, sin_max;  // per-ray window bound of the restricted search (fixed radius)
     int32_t *fallback;       // rays whose restricted search kept nothing (original indices)
     uint32_t *fallback_count;
+    int32_t *wide;           // rays with more candidates than a lane holds (original indices)
+    uint32_t *wide_count;
+    unsigned long long *pull;    // next listed ray of the warp-per-ray search
+    uint32_t *lane_units;    // next tile / group of 32 rays of the lane-per-ray search
+    int n_sm;                // multiprocessors of the device (grid sizing)
     const int32_t *ray_map;  // fallback pass: original index of listed ray i
     const uint32_t *count_ptr;   // fallback pass: number of listed rays (device)
     const int32_t *rays;     // NULL: ray i is pixel i

@@ -1,23 +1,35 @@
 // Window search (Sec. 3.2 "Searching") and adaptive primary surface sampling
-// (Sec. 3.3), fused in one kernel.
+// (Sec. 3.3), fused.
 //
-// A block owns kSearchRaysPerBlock consecutive rays and its warps take them
-// one at a time.  For a ray through
-// pixel (u, v) the s x s window of buckets is s rows of the padded table;
-// the buckets of one row are adjacent keys, so each row's points are one
-// contiguous run of the reordered list [start[k], start[k+s]).  A warp reads
-// the concatenated runs 32 points at a time (coalesced 16-byte loads), tests
-// the radius predicate in every lane and appends the accepted points with a
-// ballot prefix into its shared-memory candidate buffer.  The buffer is
-// sorted by (t, id) with a warp bitonic sort; then each lane takes one
-// candidate j, finds the K nearest candidates within r(t_j) of the sample
-// (register top-K over shared-memory broadcasts) and forms d_j and alpha_j;
-// the weights w_j and the primary-cluster rule are applied in depth order,
-// stopping when the cluster ends or when gamma * T_j <= eps_w (no later
-// weight can pass).  Each ray writes its samples into its own n_samples
-// slots of a scratch area; K6 packs them ray by ray (scan + copy), so the
-// output order is independent of scheduling and blocks never wait on one
-// another while they search.
+// k_search_select: one thread per ray.  A warp owns an 8 x 4 tile of pixels
+// (whole frames) or 32 consecutive listed rays, so its lanes' windows overlap
+// and their point loads hit the same cache lines.  For a ray through pixel
+// (u, v) the s x s window of buckets is s rows of the padded table; the
+// buckets of one row are adjacent keys, so each row's points are one
+// contiguous run of the reordered list [start[k], start[k+s]).  The lane
+// tests every point of its s runs and inserts the accepted ones into its own
+// (t, id)-sorted list in shared memory (column `lane` of a [capacity][32]
+// array: conflict-free whatever the list lengths).  It then walks its
+// candidates in depth order: for candidate j it collects the K nearest
+// candidates within r(t_j) of the sample (only those within that distance in
+// t can qualify), forms d_j and alpha_j, applies the weight and the primary-
+// cluster rule, and stops when the cluster ends, when n samples are kept or
+// when gamma * T_j <= eps_w (no later weight can pass).  Rays with more
+// accepted points than a lane holds are listed and searched again by
+// k_search_select_wide.
+//
+// k_search_select_wide: one warp per ray, for those listed rays.  The warp
+// reads the concatenated runs 32 points at a time, appends the accepted ones
+// with a ballot prefix into its shared-memory buffer (keeping the cand_cap
+// smallest (t, id)), sorts them, and lanes take one candidate each for the
+// neighbour search.
+//
+// Each ray writes its samples into its own n_samples slots of a scratch
+// area; K6 packs them ray by ray (scan + copy), so the output order is
+// independent of scheduling and blocks never wait on one another while they
+// search.
+#include <algorithm>
+
 #include "hp_kernels.cuh"
 
 namespace hp {
@@ -143,17 +155,12 @@ __global__ void __launch_bounds__(256) k_ray_table(Cam cam, int mode, float rdd,
 }
 
 template <int KB>
-__global__ void __launch_bounds__(kSearchWarps * 32) k_search_select(const SearchArgs a)
+__global__ void __launch_bounds__(kSearchWarps * 32) k_search_select_wide(const SearchArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_next;
     const SearchSmem L = search_layout();
-    const int rpc = kSearchRaysPerBlock;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
-    if (tid == 0) s_next = 0;
-    __syncthreads();
-    const int64_t tile = blockIdx.x;
 
     float4 *cp = reinterpret_cast<float4 *>(smem + L.cp) + warp * kCandCap;
     uint64_t *ck = reinterpret_cast<uint64_t *>(smem + L.ck) + warp * kCandCap;
@@ -163,13 +170,15 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select(const Searc
     const int64_t npix = (int64_t)a.cam.width * a.cam.height;
     const int64_t R_eff = a.count_ptr ? (int64_t)*a.count_ptr : a.R;
 
+    // every warp pulls the next listed ray from a grid-wide counter, so heavy
+    // rays never hold up a block; blocks past the list's end leave at once
+    if ((int64_t)blockIdx.x * kSearchWarps >= R_eff) return;
     for (;;) {
-        int rl = 0;
-        if (lane == 0) rl = atomicAdd(&s_next, 1);
+        unsigned long long rl = 0;
+        if (lane == 0) rl = atomicAdd(a.pull, 1ull);
         rl = __shfl_sync(kFull, rl, 0);
-        if (rl >= rpc) break;
-        const int64_t rl_idx = tile * rpc + rl;
-        if (rl_idx >= R_eff) break;
+        if ((int64_t)rl >= R_eff) break;
+        const int64_t rl_idx = (int64_t)rl;
         // ri: the ray's index in the outputs (fallback pass: from the list)
         const int64_t ri = a.ray_map ? (int64_t)__ldg(a.ray_map + rl_idx) : rl_idx;
         const int pix = a.rays ? __ldg(a.rays + ri) : (int)ri;
@@ -461,6 +470,278 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select(const Searc
     }
 }
 
+// Lane-per-ray search.  A lane appends its accepted points, unsorted, to
+// its own column of a [kLaneCap][32] shared-memory array (a few instructions
+// per point, so lanes that accept at different times cost the warp little),
+// then takes its candidates in (t, id) order, finding each next one with a
+// scan of the column -- the selection usually stops after a few.  A ray with
+// more accepted points than the column holds is listed for the warp-per-ray
+// search instead, as soon as the column overflows.
+constexpr int kLaneWarps = 4;
+constexpr int kLaneCap = 48;
+
+// resident blocks per SM for each K bucket (shared memory: 48 KB per block)
+__host__ __device__ constexpr int lane_blocks_per_sm(int KB) { return KB <= 8 ? 4 : KB <= 16 ? 4 : 3; }
+
+__host__ __device__ constexpr size_t lane_smem_bytes() { return (size_t)kLaneWarps * kLaneCap * 32 * 8; }
+
+__device__ __forceinline__ int point_id(const SearchArgs &a, uint32_t idx) { return __float_as_int(__ldg(&a.spts[idx].w)); }
+
+// One ray on one lane; lt / li point at this lane's column (depth lt[c * 32],
+// table index li[c * 32]).  Returns false when the ray must go to the
+// warp-per-ray search.
+template <int KB>
+__device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pix, float *lt, uint32_t *li)
+{
+    const int W = a.cam.width;
+    const int pv = pix / W, pu = pix - pv * W;
+    const float4 rt = __ldg(a.raytab + pix);
+    Ray ray;
+    ray.dx = rt.x;
+    ray.dy = rt.y;
+    ray.dz = rt.z;
+    ray.c = rt.w;
+
+    // depth range and window of this ray (plain: [t_near, t_far] and h;
+    // restricted: the ray's interval and the window bound of its t0, D12)
+    float tn = a.cam.t_near, tf = a.cam.t_far;
+    int hr = a.h;
+    bool full_window_empty = false;
+    if (a.interval) {
+        const float2 iv = __ldg(a.interval + ri);
+        tn = fmaxf(tn, iv.x);
+        tf = fminf(tf, iv.y);
+        if (a.mode == HP_RADIUS_FIXED) {
+            const float zlo = fmaxf(dsub(dmul(tn, a.cos_max), dmul(a.r, a.sin_max)), a.cam.z_near);
+            const float lim = dadd(dmul(ddiv(a.win_fx, zlo), 1.001f), 1e-3f);
+            if (lim < (float)a.h) hr = min(a.h, (int)floorf(dadd(lim, 0.5f)));
+        }
+        const int fspan = 2 * a.h + 1;
+        uint32_t flen = 0;
+        for (int q = 0; q < fspan; ++q) {
+            const int64_t kb = (int64_t)(pv + q) * a.Wp + pu;
+            flen |= __ldg(a.start + kb + fspan) - __ldg(a.start + kb);
+        }
+        full_window_empty = flen == 0;
+    }
+    const int span = 2 * hr + 1, off = a.h - hr;
+
+    // ---- window walk: s runs, the next row's bounds loaded one row ahead,
+    // kPtBatch points of a run loaded before any of them is used
+    constexpr int kPtBatch = 8;
+    int total = 0;
+    float t_max = 0.0f;
+    bool early_hit = false, late_hit = false;
+    const int64_t kb0 = (int64_t)(pv + off) * a.Wp + pu + off;
+    uint32_t nlo = __ldg(a.start + kb0), nhi = __ldg(a.start + kb0 + span);
+    for (int q = 0; q < span; ++q) {
+        const uint32_t lo = nlo, hi = nhi;
+        if (q + 1 < span) {
+            const int64_t kb = kb0 + (int64_t)(q + 1) * a.Wp;
+            nlo = __ldg(a.start + kb);
+            nhi = __ldg(a.start + kb + span);
+        }
+        for (uint32_t i0 = lo; i0 < hi; i0 += kPtBatch) {
+            float4 pb[kPtBatch];
+#pragma unroll
+            for (int k = 0; k < kPtBatch; ++k)
+                if (i0 + k < hi) pb[k] = __ldg(a.spts + i0 + k);
+#pragma unroll
+            for (int k = 0; k < kPtBatch; ++k) {
+                if (i0 + k >= hi) break;
+                float t = 0.0f;
+                bool acc;
+                if (!a.interval) {
+                    acc = accept_point(a, ray, pb[k], tn, tf, t);
+                } else {
+                    const bool plain = accept_point(a, ray, pb[k], a.cam.t_near, a.cam.t_far, t);
+                    acc = plain && t >= tn && t <= tf;
+                    early_hit |= plain && t < tn;
+                    late_hit |= plain && t > tf;
+                }
+                if (!acc) continue;
+                // more accepted points than the column holds: the warp-per-ray
+                // search takes the ray, so stop walking
+                if (total == kLaneCap) return false;
+                lt[total * 32] = t;
+                li[total * 32] = i0 + k;
+                ++total;
+                t_max = fmaxf(t_max, t);
+            }
+        }
+    }
+    if (total > a.cand_cap) return false;      // the cap rule is the warp search's
+    const int C = total;
+
+    // ---- adaptive primary surface sampling, candidates in (t, id) order
+    const int K = a.K, n_max = a.n_max;
+    float T = 1.0f, t_prev = 0.0f, t_sel = 0.0f;
+    int jstar = -1, ns = 0, prim = -1;
+    bool done = false;
+    float t_last = -1.0f;                      // the previous candidate's (t, id)
+    int id_last = -1;
+    const int64_t slot0 = ri * n_max;
+    for (int j = 0; j < C; ++j) {
+        // next candidate: the smallest (t, id) above (t_last, id_last); ids
+        // are looked up only for equal depths
+        float tj = __int_as_float(0x7f800000);
+        uint32_t ij = 0;
+        int idj = -2;                          // -2: not looked up yet
+        for (int c = 0; c < C; ++c) {
+            const float tc = lt[c * 32];
+            if (tc < t_last || tc > tj) continue;
+            const uint32_t ic = li[c * 32];
+            if (tc == t_last || tc == tj) {
+                const int idc = point_id(a, ic);
+                if (tc == t_last && idc <= id_last) continue;
+                if (tc == tj) {
+                    if (idj == -2) idj = point_id(a, ij);
+                    if (idc >= idj) continue;
+                }
+                tj = tc;
+                ij = ic;
+                idj = idc;
+            } else {
+                tj = tc;
+                ij = ic;
+                idj = -2;
+            }
+        }
+        const float4 pj = __ldg(a.spts + ij);
+        t_last = tj;
+        id_last = __float_as_int(pj.w);
+        if (jstar >= 0 && a.gap_k > 0.0f) {
+            const float gap = dsub(tj, t_prev);
+            if (!(gap <= dmul(a.gap_k, radius_at(a.mode, a.r, ray, t_prev)))) {
+                done = true;
+                break;
+            }
+        }
+        const float rad = radius_at(a.mode, a.r, ray, tj);
+        const float rad2 = dmul(rad, rad);
+        // |x_j - P_i| >= |t_j - t_i| up to float32 rounding (~1e-6 (1 + t)),
+        // far inside the margin, so only candidates within lim in depth qualify
+        const float lim = rad * 1.001f + 1e-5f * (1.0f + tj);
+        uint64_t keys[KB];
+#pragma unroll
+        for (int m = 0; m < KB; ++m) keys[m] = ~0ull;
+        for (int c = 0; c < C; ++c) {
+            if (fabsf(lt[c * 32] - tj) > lim) continue;
+            const float4 Pi = __ldg(a.spts + li[c * 32]);
+            const float ax = dfma(tj, ray.dx, -Pi.x);
+            const float ay = dfma(tj, ray.dy, -Pi.y);
+            const float az = dfma(tj, ray.dz, -Pi.z);
+            const float d2 = dadd(dadd(dmul(ax, ax), dmul(ay, ay)), dmul(az, az));
+            if (d2 <= rad2) knn_insert<KB>(keys, ((uint64_t)__float_as_uint(d2) << 32) | (uint32_t)__float_as_int(Pi.w));
+        }
+        float s = 0.0f;
+        int kp = 0;
+#pragma unroll
+        for (int m = 0; m < KB; ++m) {
+            if (m < K && keys[m] != ~0ull) {
+                s = dadd(s, dsqrt(__uint_as_float((uint32_t)(keys[m] >> 32))));
+                ++kp;
+            }
+        }
+        const float dj = ddiv(s, (float)kp);
+        const float alpha = dmul(a.gamma, exp32(-ddiv(dmul(dj, dj), a.beta2)));
+        const float w = dmul(alpha, T);
+        T = dmul(T, dsub(1.0f, alpha));
+        if (w > a.eps_w) {
+            if (jstar < 0) {
+                jstar = j;
+                prim = (int)pixel_key(a.cam, a.h, make_float3(pj.x, pj.y, pj.z));
+            }
+            const int64_t slot = slot0 + ns;
+            a.slot_t[slot] = tj;
+            a.slot_src[slot] = id_last;
+            if (ns > 0) a.slot_delta[slot - 1] = tj - t_sel;
+            t_sel = tj;
+#pragma unroll
+            for (int m = 0; m < KB; ++m) {
+                if (m < K) {
+                    const bool ok = keys[m] != ~0ull;
+                    a.slot_nbr[slot * K + m] = ok ? (int)(uint32_t)keys[m] : -1;
+                    a.slot_dist[slot * K + m] = ok ? dsqrt(__uint_as_float((uint32_t)(keys[m] >> 32))) : 0.0f;
+                }
+            }
+            if (++ns == n_max) {
+                done = true;
+                break;
+            }
+        }
+        t_prev = tj;
+        if (!(dmul(a.gamma, T) > a.eps_w)) {
+            done = true;
+            break;
+        }
+    }
+    if (ns > 0) a.slot_delta[slot0 + ns - 1] = 2.0f * radius_at(a.mode, a.r, ray, t_sel);
+    a.n_s[ri] = ns;
+    a.primary[ri] = prim;
+    a.cand_count[ri] = total;
+    if (a.interval && a.fallback) {
+        // fallback rule of the restricted search (D12); the last candidate's
+        // depth is the largest accepted depth (total <= cand_cap here)
+        bool late_ok = false;
+        if (jstar >= 0 && a.gap_k > 0.0f && total > 0)
+            late_ok = dsub(tf, t_max) > dmul(fmaxf(a.gap_k, 1.0f), radius_at(a.mode, a.r, ray, t_max));
+        const bool miss = (ns == 0 && !full_window_empty) || early_hit || (!done && late_hit && !late_ok);
+        if (miss) a.fallback[atomicAdd(a.fallback_count, 1u)] = (int32_t)ri;
+    }
+    return true;
+}
+
+// Warps pull work units from a grid-wide counter: an 8 x 4 pixel tile (whole
+// frames; ray i is pixel i) or 32 consecutive listed rays.
+template <int KB>
+__global__ void __launch_bounds__(kLaneWarps * 32, lane_blocks_per_sm(KB)) k_search_select(const SearchArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // this lane's candidate list: depth lt[c * 32] and table index li[c * 32]
+    float *lt = reinterpret_cast<float *>(smem) + warp * (kLaneCap * 32) + lane;
+    uint32_t *li = reinterpret_cast<uint32_t *>(smem) + kLaneWarps * kLaneCap * 32 + warp * (kLaneCap * 32) + lane;
+
+    const int W = a.cam.width, H = a.cam.height;
+    const int64_t npix = (int64_t)W * H;
+    const bool frame = !a.rays && !a.ray_map;
+    const int tiles_x = (W + 7) >> 3;
+    const int64_t n_units = frame ? (int64_t)tiles_x * ((H + 3) >> 2)
+                                  : ((a.count_ptr ? (int64_t)*a.count_ptr : a.R) + 31) / 32;
+    const int64_t R_eff = frame ? npix : (a.count_ptr ? (int64_t)*a.count_ptr : a.R);
+    for (;;) {
+        unsigned int u = 0;
+        if (lane == 0) u = atomicAdd(a.lane_units, 1u);
+        u = __shfl_sync(kFull, u, 0);
+        if ((int64_t)u >= n_units) break;
+        int64_t ri;
+        int pix;
+        if (frame) {
+            const int64_t ty = (int64_t)u / tiles_x;
+            const int pu = (int)((int64_t)u - ty * tiles_x) * 8 + (lane & 7);
+            const int64_t pv = ty * 4 + (lane >> 3);
+            if (pu >= W || pv >= H) continue;
+            ri = pv * W + pu;
+            pix = (int)ri;
+        } else {
+            const int64_t rl = (int64_t)u * 32 + lane;
+            if (rl >= R_eff) continue;
+            ri = a.ray_map ? (int64_t)__ldg(a.ray_map + rl) : rl;
+            pix = a.rays ? __ldg(a.rays + ri) : (int)ri;
+        }
+        if (pix < 0 || pix >= npix) {
+            set_error(a.err, HP_ERR_BAD_RAY, ri);
+            a.n_s[ri] = 0;
+            a.primary[ri] = -1;
+            a.cand_count[ri] = 0;
+            continue;
+        }
+        // more candidates than this lane may answer for: the warp-per-ray search takes the ray
+        if (!lane_ray<KB>(a, ri, pix, lt, li)) a.wide[atomicAdd(a.wide_count, 1u)] = (int32_t)ri;
+    }
+}
+
 // Packing (K6): exclusive scan of n_s with a decoupled look-back over
 // uniform tiles of 256 rays, then each thread copies its ray's sample slots
 // (a contiguous run of n_s rows) to the packed outputs.
@@ -524,10 +805,52 @@ __global__ void __launch_bounds__(256) k_pack_samples(const SearchArgs a)
 
 size_t search_smem_bytes() { return search_layout().total; }
 
+namespace {
+
+// One search pass over the rays `a` describes: the lane-per-ray kernel, then
+// the warp-per-ray kernel over the rays the lanes listed as too wide.
+cudaError_t search_pass(const SearchArgs &a, cudaStream_t st, Prof *prof, int kid)
+{
+    cudaError_t e;
+    auto lane_k = a.K <= 4 ? k_search_select<4> : a.K <= 8 ? k_search_select<8>
+                : a.K <= 16 ? k_search_select<16> : k_search_select<32>;
+    auto wide_k = a.K <= 4 ? k_search_select_wide<4> : a.K <= 8 ? k_search_select_wide<8>
+                : a.K <= 16 ? k_search_select_wide<16> : k_search_select_wide<32>;
+    const size_t lsm = lane_smem_bytes(), wsm = search_smem_bytes();
+    if ((e = cudaFuncSetAttribute(lane_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(wide_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemsetAsync(a.wide_count, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(a.pull, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(a.lane_units, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+    int64_t units;
+    if (!a.rays && !a.ray_map)
+        units = div_up((int64_t)a.cam.width, 8) * div_up((int64_t)a.cam.height, 4);
+    else
+        units = div_up(a.R, 32);
+    // persistent warps: as many blocks as stay resident, fewer for small work
+    const int KB = a.K <= 4 ? 4 : a.K <= 8 ? 8 : a.K <= 16 ? 16 : 32;
+    const int64_t blocks = std::min<int64_t>(div_up(units, kLaneWarps), (int64_t)a.n_sm * lane_blocks_per_sm(KB));
+    prof_begin(prof, st, kid);
+    lane_k<<<(unsigned)blocks, kLaneWarps * 32, lsm, st>>>(a);
+    prof_end(prof, st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    SearchArgs b = a;
+    b.ray_map = a.wide;
+    b.count_ptr = a.wide_count;
+    const int64_t wblocks = std::min<int64_t>(div_up(a.R, kSearchWarps), (int64_t)a.n_sm * 4);
+    prof_begin(prof, st, KID_SEARCH_WIDE);
+    wide_k<<<(unsigned)wblocks, kSearchWarps * 32, wsm, st>>>(b);
+    prof_end(prof, st);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof)
 {
     cudaError_t e;
-    const int64_t blocks = div_up(a.R, kSearchRaysPerBlock);
     if (a.raytab_stale) {
         const int64_t npix = (int64_t)a.cam.width * a.cam.height;
         k_ray_table<<<(unsigned)div_up(npix, 256), 256, 0, st>>>(a.cam, a.mode, a.rdd, a.raytab);
@@ -535,30 +858,17 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof)
     }
     const int64_t tiles = div_up(a.R, 256);
     if ((e = cudaMemsetAsync(a.flags, 0, sizeof(uint64_t) * (size_t)tiles, st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(a.ticket, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
-    const size_t smem = search_smem_bytes();
-    auto kern = a.K <= 4 ? k_search_select<4> : a.K <= 8 ? k_search_select<8>
-              : a.K <= 16 ? k_search_select<16> : k_search_select<32>;
-    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-        return e;
-    if (a.interval && a.fallback_count &&
-        (e = cudaMemsetAsync(a.fallback_count, 0, sizeof(uint32_t), st)) != cudaSuccess)
-        return e;
-    prof_begin(prof, st, KID_SEARCH);
-    kern<<<(unsigned)blocks, kSearchWarps * 32, smem, st>>>(a);
-    prof_end(prof, st);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // pack ticket, fallback count, wide-ray count
+    if ((e = cudaMemsetAsync(a.ticket, 0, 3 * sizeof(uint32_t), st)) != cudaSuccess) return e;
+    if ((e = search_pass(a, st, prof, KID_SEARCH)) != cudaSuccess) return e;
     if (a.interval && a.fallback) {
-        // plain search for the rays the restricted search left empty
+        // plain search for the rays the restricted search flagged
         SearchArgs b = a;
         b.interval = nullptr;
         b.ray_map = a.fallback;
         b.count_ptr = a.fallback_count;
         b.raytab_stale = 0;
-        prof_begin(prof, st, KID_SEARCH_FALLBACK);
-        kern<<<(unsigned)blocks, kSearchWarps * 32, smem, st>>>(b);
-        prof_end(prof, st);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = search_pass(b, st, prof, KID_SEARCH_FALLBACK)) != cudaSuccess) return e;
     }
     prof_begin(prof, st, KID_PACK);
     k_pack_samples<<<(unsigned)tiles, 256, 0, st>>>(a);
