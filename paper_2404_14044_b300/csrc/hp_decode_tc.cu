@@ -1,8 +1,10 @@
 // Radiance-MLP decode on the 5th-generation tensor cores (tcgen05 + TMEM).
 //
-// k_decode_tc (persistent, one 256-thread block per SM, 128 samples per
+// k_decode_tc (persistent, one 512-thread block per SM, 128 samples per
 // tile): the block stages the hidden layers' weights once in shared memory as
-// K-major FP16 (or BF16) operands; per tile it gathers and inverse-distance
+// K-major FP16 (or BF16) operands.  The neighbour lists (ids and distances)
+// of the next tile are fetched by a bulk copy on the TMA engine while the
+// current tile computes.  Per tile the block gathers and inverse-distance
 // blends the samples' neighbour features straight into the first A operand,
 // then for every hidden layer one thread issues tcgen05.mma (M = 128 samples,
 // N = layer width, K = 16 per instruction) into TMEM; the whole block reads
@@ -36,10 +38,14 @@ struct TcLayout {
     int wl;                              // float offset of the output layer's W [4][fi]
     int f32_block;                       // byte offset of the FP32 block
     int a_hi, a_lo;                      // byte offsets of the activation operand
-    int comb;                            // byte offset of the [128][4] combine buffer
-    int mbar, tslot;
+    int comb;                            // byte offset of the [4][128][4] combine buffer
+    int ids, dists;                      // byte offsets of the staged neighbour lists
+    int prefetch;                        // neighbour lists staged per tile (they fit)
+    int mbar, tslot;                     // two mbarriers (MMA, list copy), TMEM address
     int total;
 };
+
+constexpr int kSmemLimit = 227 * 1024;
 
 inline int up16(int x) { return (x + 15) & ~15; }
 
@@ -70,8 +76,23 @@ TcLayout tc_layout(const RenderArgs &a, bool bf16)
     L.wl = f;
     f += 4 * a.dims[a.n_layers - 1];
     o += up16(f * 4);
-    L.comb = o;
-    o += 4 * kTcTile * 4 * 4;                // [column group][row][4]
+    // the output layer's combine buffer reuses the activation operand, which
+    // is idle after the last hidden layer's MMAs
+    const int comb_bytes = 4 * kTcTile * 4 * 4;
+    if (kTcTile * maxw * 2 * (bf16 ? 1 : 2) >= comb_bytes) {
+        L.comb = L.a_hi;
+    } else {
+        L.comb = o;
+        o += comb_bytes;
+    }
+    const int list_bytes = kTcTile * a.K * 4;
+    L.prefetch = o + 2 * list_bytes + 32 <= kSmemLimit;
+    if (L.prefetch) {
+        L.ids = o;
+        o += list_bytes;
+        L.dists = o;
+        o += list_bytes;
+    }
     L.mbar = o;
     o += 16;
     L.tslot = o;
@@ -123,12 +144,15 @@ __device__ __forceinline__ void store_operand4(unsigned char *hi_base, unsigned 
 }  // namespace
 
 template <bool kBF16>
-__global__ void __launch_bounds__(kTcThreads, 1) k_decode_tc(const RenderArgs a, const TcLayout L)
+__global__ void __launch_bounds__(kTcThreads, 1) k_decode_tc(const RenderArgs a, const TcLayout L, int bulk_ok)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float *f32 = reinterpret_cast<float *>(smem + L.f32_block);
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L.mbar);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L.mbar);       // MMA completion
+    uint64_t *lbar = mbar + 1;                                           // list copy completion
+    int *s_ids = reinterpret_cast<int *>(smem + L.ids);
+    float *s_dst = reinterpret_cast<float *>(smem + L.dists);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + L.tslot);
     unsigned char *A_hi = smem + L.a_hi;
     unsigned char *A_lo = smem + L.a_lo;
@@ -164,6 +188,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_decode_tc(const RenderArgs a,
     }
     if (tid == 0) {
         tc::mbar_init(mbar, 1);
+        tc::mbar_init(lbar, 1);
         tc::mbar_fence_init();
     }
     if (warp == 0) tc::tmem_alloc(tslot, kTmemCols);
@@ -177,6 +202,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_decode_tc(const RenderArgs a,
     const int64_t S_all = __ldg(a.sample_offset + a.R);
     const int64_t S = S_all < a.capacity ? S_all : a.capacity;
     const int F = a.F, K = a.K;
+    const uint32_t list_bytes = (uint32_t)(kTcTile * K * 4);
+    // a tile's lists come by bulk copy when the whole 128-sample block of the
+    // (16-byte aligned) arrays lies inside their allocation
+    auto bulk_tile = [&](int64_t b) { return L.prefetch && bulk_ok && b < S && b + kTcTile <= a.capacity; };
+    uint32_t lphase = 0;
+    bool pending = bulk_tile((int64_t)blockIdx.x * kTcTile);   // a list copy in flight (all threads agree)
+    if (tid == 0 && pending) {
+        const int64_t b = (int64_t)blockIdx.x * kTcTile;
+        tc::mbar_arrive_expect_tx(lbar, 2 * list_bytes);
+        tc::bulk_g2s(s_ids, a.nbr + b * K, list_bytes, lbar);
+        tc::bulk_g2s(s_dst, a.nbr_dist + b * K, list_bytes, lbar);
+    }
     const int lpr = F >> 2, spw = 32 / lpr;                   // lanes per feature row, samples per warp step
     const int sub = lane / lpr, chunk = lane - sub * lpr;
     const float4 *feats4 = reinterpret_cast<const float4 *>(a.feats);
@@ -187,6 +224,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_decode_tc(const RenderArgs a,
     bool ok = true;
 
     for (int64_t base = (int64_t)blockIdx.x * kTcTile; base < S && ok; base += (int64_t)gridDim.x * kTcTile) {
+        // ---- this tile's neighbour lists: staged (bulk copy issued during
+        // the previous tile) or read directly
+        const bool staged = L.prefetch != 0;
+        if (staged) {
+            if (bulk_tile(base)) {
+                if (!tc::mbar_wait(lbar, lphase, kMbarLimit)) {
+                    ok = false;
+                    set_error(a.err, HP_ERR_TIMEOUT, -4);
+                }
+                lphase ^= 1u;
+                pending = false;
+            } else {
+                for (int e = tid; e < kTcTile * K; e += kTcThreads) {
+                    const int64_t g = base * K + e;
+                    const bool in = g < S * (int64_t)K;
+                    s_ids[e] = in ? __ldg(a.nbr + g) : -1;
+                    s_dst[e] = in ? __ldg(a.nbr_dist + g) : 1.0f;
+                }
+            }
+            ok = __syncthreads_and(ok) != 0;
+            if (!ok) break;
+        }
         // ---- gather + inverse-distance blend -> first A operand (K = F).
         // Lane (s, c) of a warp owns sample s of the group and the 16-byte
         // chunk c of its feature row and walks the K neighbours itself, so
@@ -197,13 +256,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_decode_tc(const RenderArgs a,
             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
             if (sl < kTcTile && g < S) {
                 float wsum = 0.0f;
-                const int *nb = a.nbr + g * K;
-                const float *nd = a.nbr_dist + g * K;
+                const int *nb = staged ? s_ids + sl * K : a.nbr + g * K;
+                const float *nd = staged ? s_dst + sl * K : a.nbr_dist + g * K;
 #pragma unroll 8
                 for (int k = 0; k < K; ++k) {
-                    const int id = __ldg(nb + k);
+                    const int id = nb[k];
                     if (id >= 0) {
-                        const float w = 1.0f / fmaxf(__ldg(nd + k), a.eps_d);
+                        const float w = 1.0f / fmaxf(nd[k], a.eps_d);
                         const float4 f = __ldg(feats4 + (int64_t)id * lpr + chunk);
                         acc.x = fmaf(w, f.x, acc.x);
                         acc.y = fmaf(w, f.y, acc.y);
@@ -220,6 +279,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_decode_tc(const RenderArgs a,
         tc::fence_async_smem();
         tc::fence_before_sync();
         __syncthreads();
+        // the lists are consumed: fetch the next tile's while this one computes
+        pending = bulk_tile(base + (int64_t)gridDim.x * kTcTile);
+        if (tid == 0 && pending) {
+            const int64_t b = base + (int64_t)gridDim.x * kTcTile;
+            tc::mbar_arrive_expect_tx(lbar, 2 * list_bytes);
+            tc::bulk_g2s(s_ids, a.nbr + b * K, list_bytes, lbar);
+            tc::bulk_g2s(s_dst, a.nbr_dist + b * K, list_bytes, lbar);
+        }
 
         float o4[4] = {0.f, 0.f, 0.f, 0.f};
         for (int l = 0; l < L.nh && ok; ++l) {
@@ -257,28 +324,41 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_decode_tc(const RenderArgs a,
             const int span = fo / ngroups, c0 = cg * span;
             const float *bias = f32 + L.bias[l];
             const bool last = (l + 1 == L.nh);
-            for (int c = c0; cg < ngroups && c < c0 + span; c += 8) {
-                float v1[8], v2[8];
-                tc::ld8(d1 + lane_off + (uint32_t)c, v1);
-                if constexpr (!kBF16) tc::ld8(d2 + lane_off + (uint32_t)c, v2);
-                tc::wait_ld();
-                float h[8];
+            if (cg < ngroups) {
+                // all of this thread's columns (up to 4 groups of 8) leave TMEM
+                // together, then one wait
+                const int n8 = span / 8;
+                float v1[4][8], v2[4][8];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    float x = v1[i];
-                    if constexpr (!kBF16) x = fmaf(v2[i], 1.0f / 2048.0f, x);
-                    h[i] = fmaxf(x + bias[c + i], 0.0f);
+                for (int j = 0; j < 4; ++j) {
+                    if (j < n8) {
+                        tc::ld8(d1 + lane_off + (uint32_t)(c0 + 8 * j), v1[j]);
+                        if constexpr (!kBF16) tc::ld8(d2 + lane_off + (uint32_t)(c0 + 8 * j), v2[j]);
+                    }
                 }
-                if (!last) {
-                    store_operand8<kBF16>(A_hi, A_lo, tc::kmajor_off(row, c, fo), h);
-                } else {
-                    const float *W = f32 + L.wl;
+                tc::wait_ld();
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (j >= n8) break;
+                    const int c = c0 + 8 * j;
+                    float h[8];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
-                        o4[0] = fmaf(h[i], W[0 * fo + c + i], o4[0]);
-                        o4[1] = fmaf(h[i], W[1 * fo + c + i], o4[1]);
-                        o4[2] = fmaf(h[i], W[2 * fo + c + i], o4[2]);
-                        o4[3] = fmaf(h[i], W[3 * fo + c + i], o4[3]);
+                        float x = v1[j][i];
+                        if constexpr (!kBF16) x = fmaf(v2[j][i], 1.0f / 2048.0f, x);
+                        h[i] = fmaxf(x + bias[c + i], 0.0f);
+                    }
+                    if (!last) {
+                        store_operand8<kBF16>(A_hi, A_lo, tc::kmajor_off(row, c, fo), h);
+                    } else {
+                        const float *W = f32 + L.wl;
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            o4[0] = fmaf(h[i], W[0 * fo + c + i], o4[0]);
+                            o4[1] = fmaf(h[i], W[1 * fo + c + i], o4[1]);
+                            o4[2] = fmaf(h[i], W[2 * fo + c + i], o4[2]);
+                            o4[3] = fmaf(h[i], W[3 * fo + c + i], o4[3]);
+                        }
                     }
                 }
             }
@@ -307,6 +387,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_decode_tc(const RenderArgs a,
         __syncthreads();
     }
 
+    // a list copy still in flight (the loop left early) lands before exit
+    if (pending) tc::mbar_wait(lbar, lphase, kMbarLimit);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -379,7 +461,7 @@ bool decode_tc_supported(const RenderArgs &a, bool bf16, size_t *smem)
     }
     const TcLayout L = tc_layout(a, bf16);
     if (smem) *smem = (size_t)L.total;
-    return L.total <= 227 * 1024;
+    return L.total <= kSmemLimit;
 }
 
 cudaError_t launch_decode_tc(const RenderArgs &a, bool bf16, cudaStream_t st)
@@ -392,7 +474,8 @@ cudaError_t launch_decode_tc(const RenderArgs &a, bool bf16, cudaStream_t st)
     int64_t grid = a.num_sms;
     const int64_t tiles = div_up(a.capacity > 0 ? a.capacity : 1, kTcTile);
     if (grid > tiles) grid = tiles;
-    kern<<<(unsigned)grid, kTcThreads, L.total, st>>>(a, L);
+    const int bulk_ok = ((uintptr_t)a.nbr % 16 == 0) && ((uintptr_t)a.nbr_dist % 16 == 0);
+    kern<<<(unsigned)grid, kTcThreads, L.total, st>>>(a, L, bulk_ok);
     return cudaGetLastError();
 }
 

@@ -129,6 +129,23 @@ __device__ __forceinline__ void ld8(uint32_t taddr, float (&v)[8])
 
 __device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// mbarrier arrive that also announces `bytes` of asynchronous transactions.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// Bulk (untiled) copy global -> shared on the TMA engine, completing `bytes`
+// of transactions on `bar`.  Both addresses 16-byte aligned, bytes a
+// multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // Byte offset of element (row, k) of a K-major operand with Kt columns in
 // the core-matrix layout (LBO = 128, SBO = Kt * 16), 2-byte elements.
 __host__ __device__ __forceinline__ uint32_t kmajor_off(int row, int k, int Kt)
