@@ -252,6 +252,17 @@ hp_status hp_search_sample_proposal(hp_ctx *ctx, const int32_t *d_ray_pixels, in
                                     int32_t n_samples, const float *d_interval, const hp_samples *out,
                                     uint32_t *d_fallback_count, void *stream);
 
+/* hp_search_sample_proposal with the intervals inferred inside the search
+ * (no interval buffer, no separate inference launch): each ray computes the
+ * interval hp_proposal_infer would give it from d_weights_bf16 (the 1666
+ * BF16 proposal weights, device) with the same arithmetic, so the results
+ * equal hp_proposal_infer followed by hp_search_sample_proposal bit for bit.
+ * The proposal is not part of the paper's method (see hp_proposal_infer).
+ * Errors as hp_search_sample; HP_ERR_INVALID_ARG when d_weights_bf16 is NULL. */
+hp_status hp_search_sample_learned(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n_rays, int32_t K,
+                                   int32_t n_samples, const uint16_t *d_weights_bf16, const hp_samples *out,
+                                   uint32_t *d_fallback_count, void *stream);
+
 /* Backward of hp_aggregate_render (Sec. 3.4 + Eq. 2) with respect to the point
  * features and the point positions, the discrete structure of the last
  * hp_search_sample (neighbour sets, samples) held fixed -- it is not

@@ -154,7 +154,8 @@ size_t search_region_bytes(int64_t R, int n_max, int K)
     const size_t slots = (size_t)(R > 0 ? R : 1) * n_max;
     return al(256) + al(8 * (size_t)div_up(R > 0 ? R : 1, 256)) + 3 * al(4 * slots) + 2 * al(4 * slots * K) +
            al(4 * (size_t)(R > 0 ? R : 1)) +         // fallback list of the proposal-restricted search
-           al(4 * (size_t)(R > 0 ? R : 1));          // rays handed to the warp-per-ray search
+           al(4 * (size_t)(R > 0 ? R : 1)) +         // rays handed to the warp-per-ray search
+           al(8 * (size_t)(R > 0 ? R : 1));          // intervals the learned search inferred for them
 }
 
 // decoded samples, then the backward's per-sample scratch
@@ -467,8 +468,8 @@ hp_status hp_table_copy(const hp_ctx *ctx, uint32_t *d_start, float *d_points, v
 }
 
 static hp_status search_impl(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n_rays, int32_t K, int32_t n_samples,
-                             const hp_samples *out, const float *d_interval, uint32_t *d_fallback_count,
-                             void *stream)
+                             const hp_samples *out, const float *d_interval, const uint16_t *d_prop_w,
+                             uint32_t *d_fallback_count, void *stream)
 {
     if (!ctx || !out) return HP_ERR_INVALID_ARG;
     if (!ctx->built) return HP_ERR_NOT_BUILT;
@@ -512,13 +513,15 @@ static hp_status search_impl(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n
         a.slot_dist = reinterpret_cast<float *>(base + o);   o += al(4 * slots * K);
         a.fallback = reinterpret_cast<int32_t *>(base + o);  o += al(4 * (size_t)n_rays);
         a.fallback_count = a.ticket + 1;
-        a.wide = reinterpret_cast<int32_t *>(base + o);
+        a.wide = reinterpret_cast<int32_t *>(base + o);      o += al(4 * (size_t)n_rays);
+        a.interval_buf = reinterpret_cast<float2 *>(base + o);
+        a.prop_w = d_prop_w;
         a.wide_count = a.ticket + 2;
         a.pull = reinterpret_cast<unsigned long long *>(a.ticket + 4);
         a.lane_units = a.ticket + 3;
         a.n_sm = ctx->num_sms;
         a.interval = reinterpret_cast<const float2 *>(d_interval);
-        if (d_interval) {
+        if (d_interval || d_prop_w) {
             // per-ray window bound of the restricted search (same terms as derive_window)
             const double fx = ctx->cam.fx, fy = ctx->cam.fy, cx = ctx->cam.cx, cy = ctx->cam.cy;
             const double ax = std::fmax(std::fabs(0.5 - cx), std::fabs(((double)ctx->cam.width - 0.5) - cx)) / fx;
@@ -535,7 +538,7 @@ static hp_status search_impl(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n
             return HP_ERR_CUDA;
         }
         ctx->raytab_valid = true;
-        if (d_interval && d_fallback_count &&
+        if ((d_interval || d_prop_w) && d_fallback_count &&
             cudaMemcpyAsync(d_fallback_count, a.fallback_count, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st) !=
                 cudaSuccess) {
             cudaGetLastError();
@@ -554,7 +557,7 @@ static hp_status search_impl(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n
 hp_status hp_search_sample(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n_rays, int32_t K, int32_t n_samples,
                            const hp_samples *out, void *stream)
 {
-    return search_impl(ctx, d_ray_pixels, n_rays, K, n_samples, out, nullptr, nullptr, stream);
+    return search_impl(ctx, d_ray_pixels, n_rays, K, n_samples, out, nullptr, nullptr, nullptr, stream);
 }
 
 hp_status hp_search_sample_proposal(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n_rays, int32_t K,
@@ -562,7 +565,16 @@ hp_status hp_search_sample_proposal(hp_ctx *ctx, const int32_t *d_ray_pixels, in
                                     uint32_t *d_fallback_count, void *stream)
 {
     if (!d_interval) return HP_ERR_INVALID_ARG;
-    return search_impl(ctx, d_ray_pixels, n_rays, K, n_samples, out, d_interval, d_fallback_count, stream);
+    return search_impl(ctx, d_ray_pixels, n_rays, K, n_samples, out, d_interval, nullptr, d_fallback_count, stream);
+}
+
+hp_status hp_search_sample_learned(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n_rays, int32_t K,
+                                   int32_t n_samples, const uint16_t *d_weights_bf16, const hp_samples *out,
+                                   uint32_t *d_fallback_count, void *stream)
+{
+    if (!d_weights_bf16) return HP_ERR_INVALID_ARG;
+    return search_impl(ctx, d_ray_pixels, n_rays, K, n_samples, out, nullptr, d_weights_bf16, d_fallback_count,
+                       stream);
 }
 
 static PropArgs prop_args(const hp_ctx *ctx, const int32_t *d_rays, int64_t n_rays)

@@ -69,6 +69,8 @@ struct SearchArgs {
     float4 *raytab;          // [W*H] per-pixel (dx, dy, dz, cone c)
     int raytab_stale;        // recompute the ray table before searching
     const float2 *interval;  // per-ray [t0, t1] (proposal-restricted search), NULL: plain
+    const uint16_t *prop_w;  // proposal weights (BF16): the search infers each ray's interval itself
+    float2 *interval_buf;    // ... and leaves it here for the rays it hands to the warp-per-ray search
     float win_fx, cos_max, sin_max;  // per-ray window bound of the restricted search (fixed radius)
     int32_t *fallback;       // rays whose restricted search kept nothing (original indices)
     uint32_t *fallback_count;

@@ -17,55 +17,18 @@
 #include <cuda_bf16.h>
 
 #include "hp_kernels.cuh"
+#include "hp_proposal.cuh"
 
 namespace hp {
 
 namespace {
 
-constexpr int kIn = HP_PROP_BINS, kHid = 32;
-constexpr int oW0 = 0, oB0 = oW0 + kHid * kIn, oW1 = oB0 + kHid, oB1 = oW1 + kHid * kHid, oW2 = oB1 + kHid,
-              oB2 = oW2 + 2 * kHid, kNP = oB2 + 2;
-static_assert(kNP == HP_PROP_PARAMS, "parameter count");
+using namespace prop;
 
 // Loss shape: softplus hinges (sharpness kKappa) that push t0 below the first
 // sample and t1 above the last by kMargin (fractions of t_far - t_near), plus
 // kLambda times the interval width.
 constexpr float kKappa = 200.0f, kMargin = 0.01f, kLambda = 0.05f;
-
-__device__ __forceinline__ void histogram(const PropArgs &a, int pu, int pv, float (&x)[kIn])
-{
-#pragma unroll
-    for (int b = 0; b < kIn; ++b) x[b] = 0.0f;
-    const float scale = (float)kIn / (a.cam.t_far - a.cam.t_near);
-    uint32_t lo[3], hi[3];
-    const int c0 = max(pu + a.h - 1, 0), c1 = min(pu + a.h + 1, a.Wp - 1);
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {                      // the three row runs, loads issued together
-        const int row = pv + a.h + q - 1;
-        lo[q] = hi[q] = 0;
-        if (row >= 0 && row < a.Hp) {
-            const int64_t k0 = (int64_t)row * a.Wp;
-            lo[q] = __ldg(a.start + k0 + c0);
-            hi[q] = __ldg(a.start + k0 + c1 + 1);
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-#pragma unroll 4
-        for (uint32_t i = lo[q]; i < hi[q]; ++i) {
-            const float z = __ldg(&a.spts[i].z);
-            int b = (int)floorf((z - a.cam.t_near) * scale);
-            b = b < 0 ? 0 : (b >= kIn ? kIn - 1 : b);
-            // registers need static indices: accumulate through a compare chain
-#pragma unroll
-            for (int q = 0; q < kIn; ++q) x[q] += (q == b) ? 1.0f : 0.0f;
-        }
-    }
-#pragma unroll
-    for (int b = 0; b < kIn; ++b) x[b] = log1pf(x[b]);
-}
-
-__device__ __forceinline__ float sigm(float x) { return 1.0f / (1.0f + expf(-x)); }
 
 __device__ __forceinline__ int ray_pixel(const PropArgs &a, int64_t r) { return a.rays ? a.rays[r] : (int)r; }
 
@@ -74,12 +37,10 @@ __device__ __forceinline__ int ray_pixel(const PropArgs &a, int64_t r) { return 
 __global__ void __launch_bounds__(256) k_prop_infer(const PropArgs a)
 {
     __shared__ __align__(16) float w[kNP + 2];
-    for (int e = threadIdx.x; e < kNP; e += blockDim.x)
-        w[e] = __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(a.weights_bf16)[e]);
+    load_weights(a.weights_bf16, w);
     __syncthreads();
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= a.R) return;
-    const float4 *w4 = reinterpret_cast<const float4 *>(w);   // weight rows are multiples of 4 floats
     const int pix = ray_pixel(a, r);
     const int64_t npix = (int64_t)a.cam.width * a.cam.height;
     if (pix < 0 || pix >= npix) {
@@ -87,54 +48,9 @@ __global__ void __launch_bounds__(256) k_prop_infer(const PropArgs a)
         return;
     }
     const int pv = pix / a.cam.width, pu = pix - pv * a.cam.width;
-    float x[kIn], h1[kHid], h2[kHid];
-    histogram(a, pu, pv, x);
-    float any = 0.0f;
-#pragma unroll
-    for (int b = 0; b < kIn; ++b) any += x[b];
-    if (any == 0.0f) {
-        // no point around the pixel: the full range, i.e. the plain search
-        a.interval[r] = make_float2(a.cam.t_near, a.cam.t_far);
-        return;
-    }
-#pragma unroll
-    for (int o = 0; o < kHid; ++o) {
-        float z = w[oB0 + o];
-#pragma unroll
-        for (int i = 0; i < kIn; i += 4) {
-            const float4 q = w4[(oW0 + o * kIn + i) / 4];
-            z = fmaf(q.x, x[i], z);
-            z = fmaf(q.y, x[i + 1], z);
-            z = fmaf(q.z, x[i + 2], z);
-            z = fmaf(q.w, x[i + 3], z);
-        }
-        h1[o] = fmaxf(z, 0.0f);
-    }
-#pragma unroll 4
-    for (int o = 0; o < kHid; ++o) {
-        float z = w[oB1 + o];
-#pragma unroll
-        for (int i = 0; i < kHid; i += 4) {
-            const float4 q = w4[(oW1 + o * kHid + i) / 4];
-            z = fmaf(q.x, h1[i], z);
-            z = fmaf(q.y, h1[i + 1], z);
-            z = fmaf(q.z, h1[i + 2], z);
-            z = fmaf(q.w, h1[i + 3], z);
-        }
-        h2[o] = fmaxf(z, 0.0f);
-    }
-    float o0 = w[oB2], o1 = w[oB2 + 1];
-#pragma unroll
-    for (int i = 0; i < kHid; i += 4) {
-        const float4 q0 = w4[(oW2 + i) / 4], q1 = w4[(oW2 + kHid + i) / 4];
-        o0 = fmaf(q0.x, h2[i], fmaf(q0.y, h2[i + 1], fmaf(q0.z, h2[i + 2], fmaf(q0.w, h2[i + 3], o0))));
-        o1 = fmaf(q1.x, h2[i], fmaf(q1.y, h2[i + 1], fmaf(q1.z, h2[i + 2], fmaf(q1.w, h2[i + 3], o1))));
-    }
-    const float u0 = sigm(o0), u1 = sigm(o1);
-    const float span = a.cam.t_far - a.cam.t_near;
-    const float t0 = a.cam.t_near + span * u0;
-    const float t1 = t0 + (a.cam.t_far - t0) * u1;
-    a.interval[r] = make_float2(t0, t1);
+    float x[kIn];
+    histogram(a.cam, a.start, a.spts, a.h, a.Wp, a.Hp, pu, pv, x);
+    a.interval[r] = interval(w, x, a.cam);
 }
 
 __global__ void __launch_bounds__(256) k_prop_train(const PropArgs a)
@@ -156,7 +72,7 @@ __global__ void __launch_bounds__(256) k_prop_train(const PropArgs a)
             s0 = a.t[o];
             s1 = a.t[o + n - 1];
             const int pv = pix / a.cam.width, pu = pix - pv * a.cam.width;
-            histogram(a, pu, pv, x);
+            histogram(a.cam, a.start, a.spts, a.h, a.Wp, a.Hp, pu, pv, x);
         }
     }
     float g[kNP];   // per-thread gradient (registers / local)

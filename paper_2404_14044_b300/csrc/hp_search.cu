@@ -31,6 +31,7 @@
 #include <algorithm>
 
 #include "hp_kernels.cuh"
+#include "hp_proposal.cuh"
 
 namespace hp {
 
@@ -490,8 +491,9 @@ __device__ __forceinline__ int point_id(const SearchArgs &a, uint32_t idx) { ret
 // One ray on one lane; lt / li point at this lane's column (depth lt[c * 32],
 // table index li[c * 32]).  Returns false when the ray must go to the
 // warp-per-ray search.
-template <int KB>
-__device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pix, float *lt, uint32_t *li)
+template <int KB, bool kLearned>
+__device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pix, float *lt, uint32_t *li,
+                                         const float *prop_w)
 {
     const int W = a.cam.width;
     const int pv = pix / W, pu = pix - pv * W;
@@ -503,12 +505,21 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
     ray.c = rt.w;
 
     // depth range and window of this ray (plain: [t_near, t_far] and h;
-    // restricted: the ray's interval and the window bound of its t0, D12)
+    // restricted: the ray's interval -- given, or inferred here by the
+    // proposal network -- and the window bound of its t0, D12)
+    const bool restricted = kLearned || a.interval;
     float tn = a.cam.t_near, tf = a.cam.t_far;
+    float2 iv = make_float2(tn, tf);
     int hr = a.h;
     bool full_window_empty = false;
-    if (a.interval) {
-        const float2 iv = __ldg(a.interval + ri);
+    if (restricted) {
+        if constexpr (kLearned) {
+            float x[prop::kIn];
+            prop::histogram(a.cam, a.start, a.spts, a.h, a.Wp, a.cam.height + 2 * a.h, pu, pv, x);
+            iv = prop::interval(prop_w, x, a.cam);
+        } else {
+            iv = __ldg(a.interval + ri);
+        }
         tn = fmaxf(tn, iv.x);
         tf = fminf(tf, iv.y);
         if (a.mode == HP_RADIUS_FIXED) {
@@ -551,7 +562,7 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
                 if (i0 + k >= hi) break;
                 float t = 0.0f;
                 bool acc;
-                if (!a.interval) {
+                if (!restricted) {
                     acc = accept_point(a, ray, pb[k], tn, tf, t);
                 } else {
                     const bool plain = accept_point(a, ray, pb[k], a.cam.t_near, a.cam.t_far, t);
@@ -562,7 +573,10 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
                 if (!acc) continue;
                 // more accepted points than the column holds: the warp-per-ray
                 // search takes the ray, so stop walking
-                if (total == kLaneCap) return false;
+                if (total == kLaneCap) {
+                    if (kLearned) a.interval_buf[ri] = iv;
+                    return false;
+                }
                 lt[total * 32] = t;
                 li[total * 32] = i0 + k;
                 ++total;
@@ -570,7 +584,10 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
             }
         }
     }
-    if (total > a.cand_cap) return false;      // the cap rule is the warp search's
+    if (total > a.cand_cap) {                  // the cap rule is the warp search's
+        if (kLearned) a.interval_buf[ri] = iv;
+        return false;
+    }
     const int C = total;
 
     // ---- adaptive primary surface sampling, candidates in (t, id) order
@@ -680,7 +697,7 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
     a.n_s[ri] = ns;
     a.primary[ri] = prim;
     a.cand_count[ri] = total;
-    if (a.interval && a.fallback) {
+    if (restricted && a.fallback) {
         // fallback rule of the restricted search (D12); the last candidate's
         // depth is the largest accepted depth (total <= cand_cap here)
         bool late_ok = false;
@@ -694,7 +711,7 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
 
 // Warps pull work units from a grid-wide counter: an 8 x 4 pixel tile (whole
 // frames; ray i is pixel i) or 32 consecutive listed rays.
-template <int KB>
+template <int KB, bool kLearned>
 __global__ void __launch_bounds__(kLaneWarps * 32, lane_blocks_per_sm(KB)) k_search_select(const SearchArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -702,6 +719,13 @@ __global__ void __launch_bounds__(kLaneWarps * 32, lane_blocks_per_sm(KB)) k_sea
     // this lane's candidate list: depth lt[c * 32] and table index li[c * 32]
     float *lt = reinterpret_cast<float *>(smem) + warp * (kLaneCap * 32) + lane;
     uint32_t *li = reinterpret_cast<uint32_t *>(smem) + kLaneWarps * kLaneCap * 32 + warp * (kLaneCap * 32) + lane;
+    // proposal weights (FP32 copy of the BF16 ones) behind the columns
+    float *pw = nullptr;
+    if constexpr (kLearned) {
+        pw = reinterpret_cast<float *>(smem + lane_smem_bytes());
+        prop::load_weights(a.prop_w, pw);
+        __syncthreads();
+    }
 
     const int W = a.cam.width, H = a.cam.height;
     const int64_t npix = (int64_t)W * H;
@@ -738,7 +762,7 @@ __global__ void __launch_bounds__(kLaneWarps * 32, lane_blocks_per_sm(KB)) k_sea
             continue;
         }
         // more candidates than this lane may answer for: the warp-per-ray search takes the ray
-        if (!lane_ray<KB>(a, ri, pix, lt, li)) a.wide[atomicAdd(a.wide_count, 1u)] = (int32_t)ri;
+        if (!lane_ray<KB, kLearned>(a, ri, pix, lt, li, pw)) a.wide[atomicAdd(a.wide_count, 1u)] = (int32_t)ri;
     }
 }
 
@@ -812,11 +836,13 @@ namespace {
 cudaError_t search_pass(const SearchArgs &a, cudaStream_t st, Prof *prof, int kid)
 {
     cudaError_t e;
-    auto lane_k = a.K <= 4 ? k_search_select<4> : a.K <= 8 ? k_search_select<8>
-                : a.K <= 16 ? k_search_select<16> : k_search_select<32>;
+    auto lane_k = a.prop_w ? (a.K <= 4 ? k_search_select<4, true> : a.K <= 8 ? k_search_select<8, true>
+                              : a.K <= 16 ? k_search_select<16, true> : k_search_select<32, true>)
+                           : (a.K <= 4 ? k_search_select<4, false> : a.K <= 8 ? k_search_select<8, false>
+                              : a.K <= 16 ? k_search_select<16, false> : k_search_select<32, false>);
     auto wide_k = a.K <= 4 ? k_search_select_wide<4> : a.K <= 8 ? k_search_select_wide<8>
                 : a.K <= 16 ? k_search_select_wide<16> : k_search_select_wide<32>;
-    const size_t lsm = lane_smem_bytes(), wsm = search_smem_bytes();
+    const size_t lsm = lane_smem_bytes() + (a.prop_w ? (size_t)(prop::kNP + 4) * 4 : 0), wsm = search_smem_bytes();
     if ((e = cudaFuncSetAttribute(lane_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm)) != cudaSuccess)
         return e;
     if ((e = cudaFuncSetAttribute(wide_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm)) != cudaSuccess)
@@ -839,6 +865,11 @@ cudaError_t search_pass(const SearchArgs &a, cudaStream_t st, Prof *prof, int ki
     SearchArgs b = a;
     b.ray_map = a.wide;
     b.count_ptr = a.wide_count;
+    if (a.prop_w) {
+        // the lanes left the inferred intervals of the rays they handed over
+        b.interval = a.interval_buf;
+        b.prop_w = nullptr;
+    }
     const int64_t wblocks = std::min<int64_t>(div_up(a.R, kSearchWarps), (int64_t)a.n_sm * 4);
     prof_begin(prof, st, KID_SEARCH_WIDE);
     wide_k<<<(unsigned)wblocks, kSearchWarps * 32, wsm, st>>>(b);
@@ -861,14 +892,23 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof)
     // pack ticket, fallback count, wide-ray count
     if ((e = cudaMemsetAsync(a.ticket, 0, 3 * sizeof(uint32_t), st)) != cudaSuccess) return e;
     if ((e = search_pass(a, st, prof, KID_SEARCH)) != cudaSuccess) return e;
-    if (a.interval && a.fallback) {
-        // plain search for the rays the restricted search flagged
+    if ((a.interval || a.prop_w) && a.fallback) {
+        // plain search for the rays the restricted search flagged: few and
+        // scattered rays, so one warp per ray
         SearchArgs b = a;
         b.interval = nullptr;
+        b.prop_w = nullptr;
         b.ray_map = a.fallback;
         b.count_ptr = a.fallback_count;
         b.raytab_stale = 0;
-        if ((e = search_pass(b, st, prof, KID_SEARCH_FALLBACK)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(a.pull, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+        auto wide_k = a.K <= 4 ? k_search_select_wide<4> : a.K <= 8 ? k_search_select_wide<8>
+                    : a.K <= 16 ? k_search_select_wide<16> : k_search_select_wide<32>;
+        const int64_t wblocks = std::min<int64_t>(div_up(a.R, kSearchWarps), (int64_t)a.n_sm * 4);
+        prof_begin(prof, st, KID_SEARCH_FALLBACK);
+        wide_k<<<(unsigned)wblocks, kSearchWarps * 32, search_smem_bytes(), st>>>(b);
+        prof_end(prof, st);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     prof_begin(prof, st, KID_PACK);
     k_pack_samples<<<(unsigned)tiles, 256, 0, st>>>(a);

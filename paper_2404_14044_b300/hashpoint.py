@@ -29,7 +29,7 @@ SYMBOLS = ("hp_create", "hp_destroy", "hp_workspace_size", "hp_window", "hp_set_
            "hp_aggregate_render_backward", "hp_get_status",
            "hp_debug_fault", "hp_profile_start", "hp_profile_stop", "hp_profile_kernel_name",
            "hp_selftest_mma", "hp_scan_noalloc", "hp_proposal_infer", "hp_proposal_train_step",
-           "hp_search_sample_proposal", "hp_status_string", "hp_version")
+           "hp_search_sample_proposal", "hp_search_sample_learned", "hp_status_string", "hp_version")
 PROF_KERNELS = 13
 PROP_PARAMS = 1666
 PROP_BINS = 16
@@ -107,6 +107,7 @@ def lib():
         L.hp_proposal_train_step.argtypes = [vp, vp, i64, C.POINTER(Samples), vp, vp, vp, vp, vp, i32, C.c_float, vp,
                                              vp]
         L.hp_search_sample_proposal.argtypes = [vp, vp, i64, i32, i32, vp, C.POINTER(Samples), vp, vp]
+        L.hp_search_sample_learned.argtypes = [vp, vp, i64, i32, i32, vp, C.POINTER(Samples), vp, vp]
         L.hp_selftest_mma.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp]
         L.hp_status_string.argtypes = [i32]
         L.hp_status_string.restype = C.c_char_p
@@ -316,6 +317,23 @@ class HashPoint:
         _check(lib().hp_search_sample_proposal(self._ctx, _ptr(rays), R, int(K), int(n_samples), _ptr(interval),
                                                C.byref(s), _ptr(fallback_count), _stream(stream)),
                "hp_search_sample_proposal")
+        self._R = R
+        return out
+
+    def search_sample_learned(self, rays: Optional[torch.Tensor], K: int, n_samples: int, weights_bf16: torch.Tensor,
+                              out: Optional[SampleBuffers] = None, fallback_count: Optional[torch.Tensor] = None,
+                              stream=None) -> SampleBuffers:
+        """search_sample_proposal with the intervals inferred inside the search
+        from the BF16 proposal weights (same results as proposal_infer followed
+        by search_sample_proposal)."""
+        assert weights_bf16.is_cuda and weights_bf16.numel() == PROP_PARAMS
+        R = rays.shape[0] if rays is not None else self._cam.width * self._cam.height
+        if out is None:
+            out = SampleBuffers.allocate(R, K, n_samples, self.device)
+        s = out.struct()
+        _check(lib().hp_search_sample_learned(self._ctx, _ptr(rays), R, int(K), int(n_samples), _ptr(weights_bf16),
+                                              C.byref(s), _ptr(fallback_count), _stream(stream)),
+               "hp_search_sample_learned")
         self._R = R
         return out
 

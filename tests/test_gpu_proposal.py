@@ -235,3 +235,34 @@ def test_training_loop_and_miss_rate():
     print(f"proposal miss rate {miss:.4f} on {hit.sum()} hit rays; losses {losses[0]:.4f} -> {losses[-1]:.4f}")
     assert miss < 0.10
     hp.close()
+
+
+@pytest.mark.parametrize("subset", [False, True])
+def test_learned_search_equals_infer_then_restricted(subset):
+    # the fused search infers each ray's interval with the inference
+    # kernel's arithmetic: identical results, bit for bit
+    H = _H()
+    dev = torch.device("cuda", 0)
+    sc = _scene()
+    cam, p = sc.camera, sc.params
+    R = cam.width * cam.height
+    rays = None
+    if subset:
+        rays = torch.from_numpy(scenes.random_rays(cam.width, cam.height, 5001, 3)).to(dev)
+        R = rays.shape[0]
+    theta = scenes.proposal_params(8, out_bias=(-0.3, 0.4))
+    hp = H.HashPoint(p, dev)
+    state = H.ProposalState(dev, init=torch.from_numpy(theta))
+    hp.build_table(torch.from_numpy(sc.points).to(dev), cam, p.r)
+    fa = torch.zeros(1, dtype=torch.int32, device=dev)
+    fb = torch.zeros(1, dtype=torch.int32, device=dev)
+    iv = hp.proposal_infer(rays, state.bf16)
+    a = hp.search_sample_proposal(rays, p.K, p.n_max, iv, fallback_count=fa).packed(R)
+    b = hp.search_sample_learned(rays, p.K, p.n_max, state.bf16, fallback_count=fb).packed(R)
+    assert hp.status() == (0, 0)
+    for k in ("n_s", "primary", "cand_count", "sample_offset", "t", "src", "nbr", "nbr_dist", "delta", "ray"):
+        x, y = a[k].numpy(), b[k].numpy()
+        assert np.array_equal(x.view(np.int32) if x.dtype == np.float32 else x,
+                              y.view(np.int32) if y.dtype == np.float32 else y), k
+    assert int(fa.item()) == int(fb.item()) > 0
+    hp.close()
