@@ -306,12 +306,14 @@ hp_status hp_profile_stop(hp_ctx *ctx, double *ms, int32_t *launches);
 const char *hp_profile_kernel_name(int32_t id);
 
 /* Self-test of the tensor-core path: D = A B^T for A (128 x K) and B (N x K),
- * row-major 16-bit inputs (FP16, or BF16 when bf16 != 0), D (128 x N) FP32,
- * all device pointers; K in 16..128 and N in 16..256, multiples of 16.  One
- * block stages both operands, issues K/16 tcgen05.mma and reads the TMEM
- * accumulator back.  A device-side timeout is reported by hp_get_status. */
+ * row-major 16-bit inputs, D (128 x N) FP32, all device pointers; K in
+ * 16..128 and N in 16..256, multiples of 16.  flags bit 0: BF16 inputs (else
+ * FP16); bit 1: A is placed in tensor memory (two elements per 32-bit column,
+ * row m in lane m) instead of shared memory.  One block stages the operands,
+ * issues K/16 tcgen05.mma and reads the TMEM accumulator back.  A device-side
+ * timeout is reported by hp_get_status. */
 hp_status hp_selftest_mma(hp_ctx *ctx, const uint16_t *d_a, const uint16_t *d_b, float *d_d, int32_t K, int32_t N,
-                          int32_t bf16, void *stream);
+                          int32_t flags, void *stream);
 
 /* Allocation-free exclusive prefix sum -- not part of the paper's method (the
  * paper has no counterpart); it is the bucket-count scan of hp_build_table

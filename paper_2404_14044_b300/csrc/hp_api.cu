@@ -703,11 +703,12 @@ hp_status hp_aggregate_render_backward(hp_ctx *ctx, const hp_samples *smp, int64
 }
 
 hp_status hp_selftest_mma(hp_ctx *ctx, const uint16_t *d_a, const uint16_t *d_b, float *d_d, int32_t K, int32_t N,
-                          int32_t bf16, void *stream)
+                          int32_t flags, void *stream)
 {
     if (!ctx || !d_a || !d_b || !d_d) return HP_ERR_INVALID_ARG;
-    if (K < 16 || K > 128 || K % 16 != 0 || N < 16 || N > 256 || N % 16 != 0) return HP_ERR_INVALID_ARG;
-    if (launch_mma_selftest(d_a, d_b, d_d, K, N, bf16, ctx->d_err, static_cast<cudaStream_t>(stream)) !=
+    if (K < 16 || K > 128 || K % 16 != 0 || N < 16 || N > 256 || N % 16 != 0 || (flags & ~3) != 0)
+        return HP_ERR_INVALID_ARG;
+    if (launch_mma_selftest(d_a, d_b, d_d, K, N, flags, ctx->d_err, static_cast<cudaStream_t>(stream)) !=
         cudaSuccess) {
         cudaGetLastError();
         return HP_ERR_CUDA;

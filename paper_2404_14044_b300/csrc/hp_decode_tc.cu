@@ -397,18 +397,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_decode_tc(const RenderArgs a,
 
 // One 128 x N x K product D = A B^T on the tensor cores (A: 128 x K, B: N x K,
 // row-major 16-bit inputs), for the library's self-test of the tcgen05 path.
+// flags bit 0: BF16 inputs; bit 1: A taken from tensor memory (written there
+// with tcgen05.st) instead of shared memory.
 __global__ void __launch_bounds__(128, 1) k_mma_selftest(const uint16_t *A, const uint16_t *B, float *D, int K, int N,
-                                                         int bf16, ErrWord *err)
+                                                         int flags, ErrWord *err)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool bf16 = (flags & 1) != 0, a_tmem = (flags & 2) != 0;
+    constexpr uint32_t kCols = 512, kAcol = 256;   // D in columns [0, N), A in [256, 256 + K/2)
     unsigned char *sa = smem;
     unsigned char *sb = smem + 128 * K * 2;
     uint64_t *mbar = reinterpret_cast<uint64_t *>(sb + N * K * 2);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
-    for (int e = tid; e < 128 * K; e += blockDim.x) {
-        const int r = e / K, k = e - r * K;
-        *reinterpret_cast<uint16_t *>(sa + tc::kmajor_off(r, k, K)) = A[e];
+    if (!a_tmem) {
+        for (int e = tid; e < 128 * K; e += blockDim.x) {
+            const int r = e / K, k = e - r * K;
+            *reinterpret_cast<uint16_t *>(sa + tc::kmajor_off(r, k, K)) = A[e];
+        }
     }
     for (int e = tid; e < N * K; e += blockDim.x) {
         const int r = e / K, k = e - r * K;
@@ -418,17 +424,37 @@ __global__ void __launch_bounds__(128, 1) k_mma_selftest(const uint16_t *A, cons
         tc::mbar_init(mbar, 1);
         tc::mbar_fence_init();
     }
-    if (warp == 0) tc::tmem_alloc(tslot, kTmemCols);
+    if (warp == 0) tc::tmem_alloc(tslot, kCols);
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tbase = *tslot;
+    const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+    if (a_tmem) {
+        // thread = row 32 warp + lane; two elements per column
+        const int r = 32 * warp + lane;
+        for (int c0 = 0; c0 < K / 2; c0 += 8) {
+            uint32_t v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                v[j] = (uint32_t)A[r * K + 2 * (c0 + j)] | ((uint32_t)A[r * K + 2 * (c0 + j) + 1] << 16);
+            tc::st8(tbase + lane_off + kAcol + (uint32_t)c0, v);
+        }
+        tc::wait_st();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    }
     if (tid == 0) {
-        const uint32_t idesc = tc::idesc_f16(128, N, bf16 != 0);
-        for (int kk = 0; kk < K / 16; ++kk)
-            tc::mma_f16(tbase, tc::sdesc(tc::smem_u32(sa) + kk * 256, 128, K * 16),
-                        tc::sdesc(tc::smem_u32(sb) + kk * 256, 128, K * 16), idesc, kk > 0);
+        const uint32_t idesc = tc::idesc_f16(128, N, bf16);
+        for (int kk = 0; kk < K / 16; ++kk) {
+            const uint64_t bd = tc::sdesc(tc::smem_u32(sb) + kk * 256, 128, K * 16);
+            if (a_tmem)
+                tc::mma_f16_ta(tbase, tbase + kAcol + (uint32_t)(kk * 8), bd, idesc, kk > 0);
+            else
+                tc::mma_f16(tbase, tc::sdesc(tc::smem_u32(sa) + kk * 256, 128, K * 16), bd, idesc, kk > 0);
+        }
         tc::commit(mbar);
     }
     const bool done = tc::mbar_wait(mbar, 0, kMbarLimit);
@@ -438,7 +464,7 @@ __global__ void __launch_bounds__(128, 1) k_mma_selftest(const uint16_t *A, cons
         const int r = 32 * warp + lane;
         for (int c = 0; c < N; c += 8) {
             float v[8];
-            tc::ld8(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, v);
+            tc::ld8(tbase + lane_off + (uint32_t)c, v);
             tc::wait_ld();
 #pragma unroll
             for (int i = 0; i < 8; ++i) D[r * N + c + i] = v[i];
@@ -447,7 +473,7 @@ __global__ void __launch_bounds__(128, 1) k_mma_selftest(const uint16_t *A, cons
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (warp == 0) tc::tmem_dealloc(tbase, kTmemCols);
+    if (warp == 0) tc::tmem_dealloc(tbase, kCols);
 }
 
 // Tensor-core decode possible for this MLP?  Hidden layers on tcgen05 need
@@ -479,7 +505,7 @@ cudaError_t launch_decode_tc(const RenderArgs &a, bool bf16, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_mma_selftest(const uint16_t *A, const uint16_t *B, float *D, int K, int N, int bf16, ErrWord *err,
+cudaError_t launch_mma_selftest(const uint16_t *A, const uint16_t *B, float *D, int K, int N, int flags, ErrWord *err,
                                 cudaStream_t st)
 {
     cudaError_t e;
@@ -487,7 +513,7 @@ cudaError_t launch_mma_selftest(const uint16_t *A, const uint16_t *B, float *D, 
     if ((e = cudaFuncSetAttribute(k_mma_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
         cudaSuccess)
         return e;
-    k_mma_selftest<<<1, 128, smem, st>>>(A, B, D, K, N, bf16, err);
+    k_mma_selftest<<<1, 128, smem, st>>>(A, B, D, K, N, flags, err);
     return cudaGetLastError();
 }
 

@@ -195,7 +195,7 @@ size_t render_smem_bytes(const RenderArgs &a);
 cudaError_t launch_render(const RenderArgs &a, cudaStream_t st, Prof *prof);
 bool decode_tc_supported(const RenderArgs &a, bool bf16, size_t *smem);
 cudaError_t launch_decode_tc(const RenderArgs &a, bool bf16, cudaStream_t st);
-cudaError_t launch_mma_selftest(const uint16_t *A, const uint16_t *B, float *D, int K, int N, int bf16, ErrWord *err,
+cudaError_t launch_mma_selftest(const uint16_t *A, const uint16_t *B, float *D, int K, int N, int flags, ErrWord *err,
                                 cudaStream_t st);
 
 }  // namespace hp

@@ -419,11 +419,14 @@ class HashPoint:
                                                   _ptr(grad_points), _stream(stream)), "hp_aggregate_render_backward")
         return grad_feats, grad_points
 
-    def selftest_mma(self, A: torch.Tensor, B: torch.Tensor, bf16: bool = False, stream=None) -> torch.Tensor:
-        """D = A B^T on the tensor cores (A 128 x K, B N x K, fp16 or bf16)."""
+    def selftest_mma(self, A: torch.Tensor, B: torch.Tensor, bf16: bool = False, a_tmem: bool = False,
+                     stream=None) -> torch.Tensor:
+        """D = A B^T on the tensor cores (A 128 x K, B N x K, fp16 or bf16;
+        a_tmem: A read from tensor memory)."""
         assert A.shape[0] == 128 and A.shape[1] == B.shape[1] and A.is_contiguous() and B.is_contiguous()
         D = torch.empty(128, B.shape[0], dtype=torch.float32, device=A.device)
-        _check(lib().hp_selftest_mma(self._ctx, _ptr(A), _ptr(B), _ptr(D), A.shape[1], B.shape[0], int(bf16),
+        flags = (1 if bf16 else 0) | (2 if a_tmem else 0)
+        _check(lib().hp_selftest_mma(self._ctx, _ptr(A), _ptr(B), _ptr(D), A.shape[1], B.shape[0], flags,
                                      _stream(stream)), "hp_selftest_mma")
         return D
 

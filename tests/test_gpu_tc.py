@@ -17,7 +17,8 @@ def _H():
 
 @pytest.mark.parametrize("K,N", [(16, 16), (32, 128), (128, 128), (64, 256), (128, 48)])
 @pytest.mark.parametrize("bf16", [False, True])
-def test_mma_selftest_matches_matmul(K, N, bf16):
+@pytest.mark.parametrize("a_tmem", [False, True])
+def test_mma_selftest_matches_matmul(K, N, bf16, a_tmem):
     H = _H()
     dev = torch.device("cuda", 0)
     g = torch.Generator(device="cpu").manual_seed(K * 1000 + N)
@@ -25,7 +26,8 @@ def test_mma_selftest_matches_matmul(K, N, bf16):
     A = torch.randn(128, K, generator=g).to(dt)
     B = torch.randn(N, K, generator=g).to(dt)
     hp = H.HashPoint(scenes.Params(), dev)
-    D = hp.selftest_mma(A.to(dev).view(torch.int16).contiguous(), B.to(dev).view(torch.int16).contiguous(), bf16)
+    D = hp.selftest_mma(A.to(dev).view(torch.int16).contiguous(), B.to(dev).view(torch.int16).contiguous(), bf16,
+                        a_tmem)
     assert hp.status() == (0, 0)
     ref = A.double() @ B.double().T                    # products exact in FP32; FP32 sums
     err = (D.cpu().double() - ref).abs().max().item()
