@@ -318,29 +318,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_decode_tc(const RenderArgs a,
             if (!ok) break;
             tc::fence_after_sync();
 
-            // ---- epilogue: this thread's sample row, a quarter of the columns
-            // (groups of 8 columns when the layer is narrower than 32)
-            const int ngroups = fo >= 32 ? 4 : fo / 8;
-            const int span = fo / ngroups, c0 = cg * span;
+            // ---- epilogue: this thread's sample row; the layer's 8-column
+            // chunks go round-robin to the 4 column groups (chunks cg, cg+4, ...)
             const float *bias = f32 + L.bias[l];
             const bool last = (l + 1 == L.nh);
-            if (cg < ngroups) {
-                // all of this thread's columns (up to 4 groups of 8) leave TMEM
-                // together, then one wait
-                const int n8 = span / 8;
+            {
+                const int nch = fo / 8;
+                // all of this thread's chunks (up to 4) leave TMEM together, then one wait
                 float v1[4][8], v2[4][8];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    if (j < n8) {
-                        tc::ld8(d1 + lane_off + (uint32_t)(c0 + 8 * j), v1[j]);
-                        if constexpr (!kBF16) tc::ld8(d2 + lane_off + (uint32_t)(c0 + 8 * j), v2[j]);
+                    const int ch = cg + 4 * j;
+                    if (ch < nch) {
+                        tc::ld8(d1 + lane_off + (uint32_t)(8 * ch), v1[j]);
+                        if constexpr (!kBF16) tc::ld8(d2 + lane_off + (uint32_t)(8 * ch), v2[j]);
                     }
                 }
                 tc::wait_ld();
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    if (j >= n8) break;
-                    const int c = c0 + 8 * j;
+                    const int ch = cg + 4 * j;
+                    if (ch >= nch) break;
+                    const int c = 8 * ch;
                     float h[8];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
@@ -476,6 +475,391 @@ __global__ void __launch_bounds__(128, 1) k_mma_selftest(const uint16_t *A, cons
     if (warp == 0) tc::tmem_dealloc(tbase, kCols);
 }
 
+// ---------------------------------------------------------------------------
+// k_decode_ws: the same decode, warp-specialized.  16 consumer warps run the
+// layers of tile i (4 TMEM lane quarters x 4 column groups) while 8 producer
+// warps gather and blend tile i+1 into the second of two shared-memory buffers
+// of the first A operand.  Hidden activations never touch shared memory: the
+// epilogue writes them back into tensor memory (two 16-bit values per
+// column) and the next layer's tcgen05.mma reads its A operand from there.
+// Tensor memory: D1 [0,128), D2 [128,256), A_hi [256,320), A_lo [320,384).
+// Hand-offs: full[b] (producers -> consumers, 8 warp arrivals), empty[b]
+// (tcgen05.commit after the layer-0 MMAs that read buffer b), lbar[b] (bulk
+// copy of a tile's neighbour lists), mma (per layer).  Every wait is bounded.
+constexpr int kWsConsumerWarps = 16;
+constexpr int kWsProducerWarps = 8;
+constexpr int kWsThreads = (kWsConsumerWarps + kWsProducerWarps) * 32;
+constexpr uint32_t kWsCols = 512, kColAH = 256, kColAL = 320;
+
+struct WsLayout {
+    int nh;
+    int fi[HP_MLP_MAX_LAYERS], fo[HP_MLP_MAX_LAYERS];
+    int w_hi[HP_MLP_MAX_LAYERS], w_lo[HP_MLP_MAX_LAYERS];
+    int bias[HP_MLP_MAX_LAYERS + 1];
+    int wl, f32_block;
+    int a0[2], a0_lo;                    // first A operand buffers; lo part at +a0_lo
+    int ids[2], dists[2];                // neighbour list buffers
+    int comb, bars, tslot, total;
+    int ok;                              // the layout fits this kernel
+};
+
+WsLayout ws_layout(const RenderArgs &a, bool bf16)
+{
+    WsLayout L{};
+    L.nh = a.n_layers - 1;
+    L.ok = L.nh >= 1;
+    int o = 0;
+    for (int l = 0; l < L.nh; ++l) {
+        L.fi[l] = a.dims[l];
+        L.fo[l] = a.dims[l + 1];
+        if (L.fo[l] > 128 || L.fi[l] > 128) L.ok = 0;
+        L.w_hi[l] = o;
+        o += L.fi[l] * L.fo[l] * 2;
+        L.w_lo[l] = o;
+        if (!bf16) o += L.fi[l] * L.fo[l] * 2;
+    }
+    const int a0_bytes = kTcTile * a.dims[0] * 2;
+    L.a0_lo = a0_bytes;
+    for (int b = 0; b < 2; ++b) {
+        L.a0[b] = o;
+        o += a0_bytes * (bf16 ? 1 : 2);
+    }
+    L.f32_block = o;
+    int f = 0;
+    for (int l = 0; l < a.n_layers; ++l) {
+        L.bias[l] = f;
+        f += a.dims[l + 1];
+    }
+    L.wl = f;
+    f += 4 * a.dims[a.n_layers - 1];
+    o += up16(f * 4);
+    const int list_bytes = kTcTile * a.K * 4;
+    for (int b = 0; b < 2; ++b) {
+        L.ids[b] = o;
+        o += list_bytes;
+        L.dists[b] = o;
+        o += list_bytes;
+    }
+    L.comb = o;
+    o += 4 * kTcTile * 4 * 4;
+    L.bars = o;
+    o += 8 * 8;                           // full[2], empty[2], lbar[2], mma
+    L.tslot = o;
+    o += 16;
+    L.total = o;
+    if (L.total > kSmemLimit) L.ok = 0;
+    // the gather maps 16-byte chunks of a feature row to lanes
+    if (a.dims[0] % 16 != 0 || a.dims[0] > 128) L.ok = 0;
+    return L;
+}
+
+template <bool kBF16>
+__global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a, const WsLayout L, int bulk_ok)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float *f32 = reinterpret_cast<float *>(smem + L.f32_block);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.bars);
+    uint64_t *full = bars, *empty = bars + 2, *lbar = bars + 4, *mbar = bars + 6;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + L.tslot);
+    float *comb = reinterpret_cast<float *>(smem + L.comb);
+
+    // ---- stage weights (global W is [out][in] FP32) and FP32 biases
+    {
+        int g = 0;
+        for (int l = 0; l < a.n_layers; ++l) {
+            const int fi = a.dims[l], fo = a.dims[l + 1];
+            const int nw = fi * fo;
+            if (l < L.nh) {
+                for (int e = tid; e < nw; e += blockDim.x) {
+                    const int o = e / fi, i = e - o * fi;
+                    const float w = __ldg(a.mlp + g + e);
+                    const uint32_t off = tc::kmajor_off(o, i, fi);
+                    if constexpr (kBF16) {
+                        *reinterpret_cast<__nv_bfloat16 *>(smem + L.w_hi[l] + off) = __float2bfloat16_rn(w);
+                    } else {
+                        __half h, lo;
+                        tc::split_f16(w, h, lo);
+                        *reinterpret_cast<__half *>(smem + L.w_hi[l] + off) = h;
+                        *reinterpret_cast<__half *>(smem + L.w_lo[l] + off) = lo;
+                    }
+                }
+            } else {
+                for (int e = tid; e < nw; e += blockDim.x) f32[L.wl + e] = __ldg(a.mlp + g + e);
+            }
+            g += nw;
+            for (int e = tid; e < fo; e += blockDim.x) f32[L.bias[l] + e] = __ldg(a.mlp + g + e);
+            g += fo;
+        }
+    }
+    if (tid == 0) {
+        tc::mbar_init(&full[0], kWsProducerWarps);
+        tc::mbar_init(&full[1], kWsProducerWarps);
+        tc::mbar_init(&empty[0], 1);
+        tc::mbar_init(&empty[1], 1);
+        tc::mbar_init(&lbar[0], 1);
+        tc::mbar_init(&lbar[1], 1);
+        tc::mbar_init(mbar, 1);
+        tc::mbar_fence_init();
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, kWsCols);
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = *tslot;
+
+    const int64_t S_all = __ldg(a.sample_offset + a.R);
+    const int64_t S = S_all < a.capacity ? S_all : a.capacity;
+    const int F = a.F, K = a.K;
+    const int64_t stride = (int64_t)gridDim.x * kTcTile;
+    const uint32_t list_bytes = (uint32_t)(kTcTile * K * 4);
+    auto bulk_tile = [&](int64_t b) { return bulk_ok && b < S && b + kTcTile <= a.capacity; };
+
+    if (warp >= kWsConsumerWarps) {
+        // =============================== producers: gather + blend
+        const int ptid = tid - kWsConsumerWarps * 32, pw = warp - kWsConsumerWarps;
+        const int lpr = F >> 2, spw = 32 / lpr;
+        const int sub = lane / lpr, chunk = lane - sub * lpr;
+        const float4 *feats4 = reinterpret_cast<const float4 *>(a.feats);
+        uint32_t lph = 0u, eph = 3u;   // parity bit per buffer; a fresh barrier's previous phase counts as done
+        uint32_t pend = 0u;            // list copies in flight, per buffer (leader only)
+        bool ok = true;
+        const int64_t first = (int64_t)blockIdx.x * kTcTile;
+        if (ptid == 0 && bulk_tile(first)) {
+            pend |= 1u;
+            tc::mbar_arrive_expect_tx(&lbar[0], 2 * list_bytes);
+            tc::bulk_g2s(smem + L.ids[0], a.nbr + first * K, list_bytes, &lbar[0]);
+            tc::bulk_g2s(smem + L.dists[0], a.nbr_dist + first * K, list_bytes, &lbar[0]);
+        }
+        int it = 0;
+        for (int64_t base = first; base < S; base += stride, ++it) {
+            const int b = it & 1;
+            int *s_ids = reinterpret_cast<int *>(smem + L.ids[b]);
+            float *s_dst = reinterpret_cast<float *>(smem + L.dists[b]);
+            // the next tile's lists into the other buffer (its readers finished:
+            // producer barrier at the end of the previous iteration)
+            if (ptid == 0 && bulk_tile(base + stride)) {
+                const int64_t nb = base + stride;
+                pend |= 2u >> b;
+                tc::mbar_arrive_expect_tx(&lbar[b ^ 1], 2 * list_bytes);
+                tc::bulk_g2s(smem + L.ids[b ^ 1], a.nbr + nb * K, list_bytes, &lbar[b ^ 1]);
+                tc::bulk_g2s(smem + L.dists[b ^ 1], a.nbr_dist + nb * K, list_bytes, &lbar[b ^ 1]);
+            }
+            if (bulk_tile(base)) {
+                if (!tc::mbar_wait(&lbar[b], (lph >> b) & 1u, kMbarLimit)) {
+                    ok = false;
+                    set_error(a.err, HP_ERR_TIMEOUT, -5);
+                }
+                lph ^= 1u << b;
+                pend &= ~(1u << b);
+            } else {
+                for (int e = ptid; e < kTcTile * K; e += kWsProducerWarps * 32) {
+                    const int64_t g = base * K + e;
+                    const bool in = g < S * (int64_t)K;
+                    s_ids[e] = in ? __ldg(a.nbr + g) : -1;
+                    s_dst[e] = in ? __ldg(a.nbr_dist + g) : 1.0f;
+                }
+                ok = tc::bar_and(2, kWsProducerWarps * 32, ok);
+            }
+            // the buffer is free once the layer-0 MMAs of tile it-2 are done
+            if (ok && !tc::mbar_wait(&empty[b], (eph >> b) & 1u, kMbarLimit)) {
+                ok = false;
+                set_error(a.err, HP_ERR_TIMEOUT, -6);
+            }
+            eph ^= 1u << b;
+            ok = tc::bar_and(2, kWsProducerWarps * 32, ok);   // every producer leaves together
+            if (!ok) break;
+            unsigned char *A_hi = smem + L.a0[b];
+            unsigned char *A_lo = A_hi + L.a0_lo;
+            for (int s0 = pw * spw; s0 < kTcTile; s0 += kWsProducerWarps * spw) {
+                const int sl = s0 + sub;
+                const int64_t g = base + sl;
+                float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (g < S) {
+                    float wsum = 0.0f;
+                    const int *nb = s_ids + sl * K;
+                    const float *nd = s_dst + sl * K;
+#pragma unroll 8
+                    for (int k = 0; k < K; ++k) {
+                        const int id = nb[k];
+                        if (id >= 0) {
+                            const float w = 1.0f / fmaxf(nd[k], a.eps_d);
+                            const float4 f = __ldg(feats4 + (int64_t)id * lpr + chunk);
+                            acc.x = fmaf(w, f.x, acc.x);
+                            acc.y = fmaf(w, f.y, acc.y);
+                            acc.z = fmaf(w, f.z, acc.z);
+                            acc.w = fmaf(w, f.w, acc.w);
+                            wsum += w;
+                        }
+                    }
+                    const float inv = 1.0f / wsum;
+                    acc.x *= inv; acc.y *= inv; acc.z *= inv; acc.w *= inv;
+                }
+                store_operand4<kBF16>(A_hi, A_lo, tc::kmajor_off(sl, 4 * chunk, F), acc);
+            }
+            tc::fence_async_smem();                  // generic stores -> tensor-core reads
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&full[b]);
+            ok = tc::bar_and(2, kWsProducerWarps * 32, ok);
+            if (!ok) break;
+        }
+        // a list copy still in flight lands before exit
+        for (int b = 0; b < 2; ++b)
+            if (ptid == 0 && ((pend >> b) & 1u)) tc::mbar_wait(&lbar[b], (lph >> b) & 1u, kMbarLimit);
+    } else {
+        // =============================== consumers: MMA + epilogues
+        const int q = warp & 3, cg = warp >> 2;
+        const int row = 32 * q + lane;
+        const uint32_t lane_off = (uint32_t)(32 * q) << 16;
+        const uint32_t d1 = tbase, d2 = tbase + 128, ah = tbase + kColAH, al = tbase + kColAL;
+        uint32_t fph = 0u, mph = 0u;             // parity bit per buffer
+        bool ok = true;
+        int it = 0;
+        for (int64_t base = (int64_t)blockIdx.x * kTcTile; base < S; base += stride, ++it) {
+            const int b = it & 1;
+            if (!tc::mbar_wait(&full[b], (fph >> b) & 1u, kMbarLimit)) {
+                ok = false;
+                set_error(a.err, HP_ERR_TIMEOUT, -7);
+            }
+            fph ^= 1u << b;
+            ok = tc::bar_and(1, kWsConsumerWarps * 32, ok);
+            if (!ok) break;
+            tc::fence_after_sync();
+            float o4[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int l = 0; l < L.nh; ++l) {
+                const int fi = L.fi[l], fo = L.fo[l];
+                if (tid == 0) {
+                    const uint32_t idesc = tc::idesc_f16(kTcTile, fo, kBF16);
+                    const uint32_t wh = tc::smem_u32(smem + L.w_hi[l]), wl = tc::smem_u32(smem + L.w_lo[l]);
+                    const uint32_t sbo = (uint32_t)fi * 16;
+                    if (l == 0) {
+                        const uint32_t a0h = tc::smem_u32(smem + L.a0[b]), a0l = a0h + (uint32_t)L.a0_lo;
+                        for (int kk = 0; kk < fi / 16; ++kk) {
+                            const uint64_t dah = tc::sdesc(a0h + kk * 256, 128, sbo);
+                            const uint64_t dbh = tc::sdesc(wh + kk * 256, 128, sbo);
+                            tc::mma_f16(d1, dah, dbh, idesc, kk > 0);
+                            if constexpr (!kBF16) {
+                                tc::mma_f16(d2, dah, tc::sdesc(wl + kk * 256, 128, sbo), idesc, kk > 0);
+                                tc::mma_f16(d2, tc::sdesc(a0l + kk * 256, 128, sbo), dbh, idesc, 1);
+                            }
+                        }
+                        tc::commit(&empty[b]);        // buffer b may be refilled once these are done
+                    } else {
+                        for (int kk = 0; kk < fi / 16; ++kk) {
+                            const uint64_t dbh = tc::sdesc(wh + kk * 256, 128, sbo);
+                            tc::mma_f16_ta(d1, ah + (uint32_t)(kk * 8), dbh, idesc, kk > 0);
+                            if constexpr (!kBF16) {
+                                tc::mma_f16_ta(d2, ah + (uint32_t)(kk * 8), tc::sdesc(wl + kk * 256, 128, sbo), idesc,
+                                               kk > 0);
+                                tc::mma_f16_ta(d2, al + (uint32_t)(kk * 8), dbh, idesc, 1);
+                            }
+                        }
+                    }
+                    tc::commit(mbar);
+                }
+                if (!tc::mbar_wait(mbar, mph, kMbarLimit)) {
+                    ok = false;
+                    set_error(a.err, HP_ERR_TIMEOUT, -8);
+                }
+                mph ^= 1u;
+                ok = tc::bar_and(1, kWsConsumerWarps * 32, ok);
+                if (!ok) break;
+                tc::fence_after_sync();
+
+                // ---- epilogue: this thread's row; 8-column chunks round-robin
+                // over the column groups, two at a time (TMEM -> registers -> TMEM)
+                const float *bias = f32 + L.bias[l];
+                const bool last = (l + 1 == L.nh);
+                const int nch = fo / 8;
+                for (int ch0 = cg; ch0 < nch; ch0 += 8) {
+                    float v1[2][8], v2[2][8];
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const int ch = ch0 + 4 * j;
+                        if (ch < nch) {
+                            tc::ld8(d1 + lane_off + (uint32_t)(8 * ch), v1[j]);
+                            if constexpr (!kBF16) tc::ld8(d2 + lane_off + (uint32_t)(8 * ch), v2[j]);
+                        }
+                    }
+                    tc::wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const int ch = ch0 + 4 * j;
+                        if (ch >= nch) break;
+                        const int c = 8 * ch;
+                        float h[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            float x = v1[j][i];
+                            if constexpr (!kBF16) x = fmaf(v2[j][i], 1.0f / 2048.0f, x);
+                            h[i] = fmaxf(x + bias[c + i], 0.0f);
+                        }
+                        if (!last) {
+                            // next layer's A: columns c/2 .. c/2+3 of A_hi (and A_lo)
+                            uint32_t ph[4], pl[4];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                if constexpr (kBF16) {
+                                    const uint32_t x0 = __bfloat16_as_ushort(__float2bfloat16_rn(h[2 * i]));
+                                    const uint32_t x1 = __bfloat16_as_ushort(__float2bfloat16_rn(h[2 * i + 1]));
+                                    ph[i] = x0 | (x1 << 16);
+                                    pl[i] = 0u;
+                                } else {
+                                    __half x0h, x0l, x1h, x1l;
+                                    tc::split_f16(h[2 * i], x0h, x0l);
+                                    tc::split_f16(h[2 * i + 1], x1h, x1l);
+                                    ph[i] = (uint32_t)__half_as_ushort(x0h) | ((uint32_t)__half_as_ushort(x1h) << 16);
+                                    pl[i] = (uint32_t)__half_as_ushort(x0l) | ((uint32_t)__half_as_ushort(x1l) << 16);
+                                }
+                            }
+                            tc::st4(ah + lane_off + (uint32_t)(c / 2), ph);
+                            if constexpr (!kBF16) tc::st4(al + lane_off + (uint32_t)(c / 2), pl);
+                        } else {
+                            const float *W = f32 + L.wl;
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) {
+                                o4[0] = fmaf(h[i], W[0 * fo + c + i], o4[0]);
+                                o4[1] = fmaf(h[i], W[1 * fo + c + i], o4[1]);
+                                o4[2] = fmaf(h[i], W[2 * fo + c + i], o4[2]);
+                                o4[3] = fmaf(h[i], W[3 * fo + c + i], o4[3]);
+                            }
+                        }
+                    }
+                }
+                if (!last) tc::wait_st();
+                tc::fence_before_sync();
+                tc::bar_and(1, kWsConsumerWarps * 32, true);
+                tc::fence_after_sync();
+            }
+            if (!ok) break;
+
+            // ---- output layer: combine the column groups, activations
+            if (cg > 0) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) comb[(cg * kTcTile + row) * 4 + i] = o4[i];
+            }
+            tc::bar_and(1, kWsConsumerWarps * 32, true);
+            if (cg == 0) {
+                const float *bl = f32 + L.bias[a.n_layers - 1];
+                float o[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    o[i] = ((o4[i] + comb[(kTcTile + row) * 4 + i]) + comb[(2 * kTcTile + row) * 4 + i]) +
+                           comb[(3 * kTcTile + row) * 4 + i] + bl[i];
+                const int64_t g = base + row;
+                if (g < S)
+                    a.sample_out[g] = make_float4(softplus_f(o[0]), sigmoid_f(o[1]), sigmoid_f(o[2]), sigmoid_f(o[3]));
+            }
+        }
+    }
+
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tbase, kWsCols);
+}
+
 // Tensor-core decode possible for this MLP?  Hidden layers on tcgen05 need
 // K (fan-in) multiple of 16 and N (width) in 16..128 step 16.
 bool decode_tc_supported(const RenderArgs &a, bool bf16, size_t *smem)
@@ -493,6 +877,18 @@ bool decode_tc_supported(const RenderArgs &a, bool bf16, size_t *smem)
 cudaError_t launch_decode_tc(const RenderArgs &a, bool bf16, cudaStream_t st)
 {
     cudaError_t e;
+    const int bulk_ok_ws = ((uintptr_t)a.nbr % 16 == 0) && ((uintptr_t)a.nbr_dist % 16 == 0);
+    const WsLayout W = ws_layout(a, bf16);
+    if (W.ok) {
+        auto kern = bf16 ? k_decode_ws<true> : k_decode_ws<false>;
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, W.total)) != cudaSuccess)
+            return e;
+        int64_t grid = a.num_sms;
+        const int64_t tiles = div_up(a.capacity > 0 ? a.capacity : 1, kTcTile);
+        if (grid > tiles) grid = tiles;
+        kern<<<(unsigned)grid, kWsThreads, W.total, st>>>(a, W, bulk_ok_ws);
+        return cudaGetLastError();
+    }
     const TcLayout L = tc_layout(a, bf16);
     auto kern = bf16 ? k_decode_tc<true> : k_decode_tc<false>;
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total)) != cudaSuccess)
