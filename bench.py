@@ -127,8 +127,8 @@ class ClockSampler:
 
 def algorithmic(kernel, N, Nv, P, R, S, K, F, dims, U, tensor_decode=True):
     """Algorithmic bytes (or FLOPs for the decode) of one launch of each kernel.
-    The search's bytes are charged to the lane-per-ray kernel; the
-    warp-per-ray kernel re-searches the few rays it cannot hold."""
+    The search's bytes are charged to its walk (k_search_select); the pick
+    and the warp-per-ray kernel work on what the walk left."""
     mlp_flops = 2 * S * sum(dims[l] * dims[l + 1] for l in range(len(dims) - 1))
     table = {
         "k_project_count": ("hbm", 12 * N + 8 * N + 8 * P),
@@ -136,6 +136,7 @@ def algorithmic(kernel, N, Nv, P, R, S, K, F, dims, U, tensor_decode=True):
         "k_scatter": ("hbm", 12 * N + 8 * N + 4 * Nv + 16 * Nv),
         "k_bucket_sort": ("hbm", 8 * P + 32 * Nv),
         "k_search_select": ("hbm", 4 * P + 16 * Nv + 12 * R + (12 + 8 * K) * S),
+        "k_search_pick": ("hbm", 0),
         "k_search_select_wide": ("hbm", 0),
         "k_pack_samples": ("hbm", 4 * R + 8 * (R + 1) + (12 + 8 * K) * S + (16 + 8 * K) * S),
         "k_aggregate_decode": ("tensor" if tensor_decode else "alu", mlp_flops),

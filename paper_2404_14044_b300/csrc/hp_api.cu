@@ -31,6 +31,7 @@ struct hp_ctx {
     uint32_t *cnt = nullptr, *start = nullptr, *scan_ticket = nullptr;
     uint2 *keyrank = nullptr;
     float4 *spts = nullptr;
+    float4 *spts_tmp = nullptr;
     uint64_t *scan_flags = nullptr;
     float4 *raytab = nullptr;        // per-pixel rays, cached while the intrinsics are unchanged
     bool raytab_valid = false;
@@ -144,6 +145,7 @@ size_t table_region_bytes(int64_t N, int64_t P, int64_t npix)
     o += al(4 * (size_t)(P + 1));                            // start
     o += al(8 * (size_t)N);                                  // keyrank
     o += al(16 * (size_t)N);                                 // spts
+    o += al(16 * (size_t)N);                                 // spts before the in-bucket order
     o += al(8 * (size_t)div_up(P + 1, kScanTile));           // scan flags
     return o;
 }
@@ -414,6 +416,7 @@ hp_status hp_build_table(hp_ctx *ctx, const float *d_points, int64_t n_points, c
     ctx->start = reinterpret_cast<uint32_t *>(base + o);       o += al(4 * (size_t)(P + 1));
     ctx->keyrank = reinterpret_cast<uint2 *>(base + o);        o += al(8 * (size_t)n_points);
     ctx->spts = reinterpret_cast<float4 *>(base + o);          o += al(16 * (size_t)n_points);
+    ctx->spts_tmp = reinterpret_cast<float4 *>(base + o);      o += al(16 * (size_t)n_points);
     ctx->scan_flags = reinterpret_cast<uint64_t *>(base + o);
 
     Cam c{};
@@ -429,6 +432,7 @@ hp_status hp_build_table(hp_ctx *ctx, const float *d_points, int64_t n_points, c
     BuildArgs a{};
     a.pts = d_points; a.N = n_points; a.cam = c; a.h = h; a.P = P;
     a.cnt = ctx->cnt; a.start = ctx->start; a.keyrank = ctx->keyrank; a.spts = ctx->spts;
+    a.spts_tmp = ctx->spts_tmp;
     a.scan_flags = ctx->scan_flags; a.scan_ticket = ctx->scan_ticket; a.err = ctx->d_err;
     a.spin_limit = ctx->spin_limit; a.skip_tile = ctx->skip_tile;
     if (launch_build(a, static_cast<cudaStream_t>(stream), &ctx->prof) != cudaSuccess) {

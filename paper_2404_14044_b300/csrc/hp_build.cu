@@ -10,7 +10,9 @@
 // K3 k_scatter        each point written to start[key] + slot as float4
 //                     (camera x, y, z, id bits)
 // K4 k_bucket_sort    each run ordered by (z, x, y, id), which makes the list
-//                     independent of the atomics' order and of the input order
+//                     independent of the atomics' order and of the input order:
+//                     one thread per point counts the points of its bucket that
+//                     precede it and writes it to that rank
 #include "hp_kernels.cuh"
 
 namespace hp {
@@ -118,25 +120,21 @@ __device__ __forceinline__ bool pt_less(const float4 &a, const float4 &b)
     return __float_as_int(a.w) < __float_as_int(b.w);
 }
 
-// One thread per bucket: insertion sort of the bucket's run (runs are short).
-__global__ void __launch_bounds__(256) k_bucket_sort(const uint32_t *__restrict__ start, int64_t P,
-                                                     float4 *__restrict__ spts)
+// One thread per point: its rank among the points of its bucket under
+// (z, x, y, id) -- a strict total order, ids being distinct -- is its place.
+__global__ void __launch_bounds__(256) k_bucket_sort(const uint2 *__restrict__ keyrank, int64_t N,
+                                                     const uint32_t *__restrict__ start,
+                                                     const float4 *__restrict__ tmp, float4 *__restrict__ spts)
 {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= P) return;
-    const uint32_t a = start[k], b = start[k + 1];
-    if (b - a < 2) return;
-    for (uint32_t i = a + 1; i < b; ++i) {
-        const float4 x = spts[i];
-        uint32_t j = i;
-        while (j > a) {
-            const float4 y = spts[j - 1];
-            if (!pt_less(x, y)) break;
-            spts[j] = y;
-            --j;
-        }
-        spts[j] = x;
-    }
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const uint2 kr = keyrank[i];
+    if (kr.x == kNoKey) return;
+    const uint32_t a = start[kr.x], b = start[kr.x + 1];
+    const float4 x = tmp[a + kr.y];
+    uint32_t rank = 0;
+    for (uint32_t j = a; j < b; ++j) rank += pt_less(__ldg(tmp + j), x) ? 1u : 0u;
+    spts[a + rank] = x;
 }
 
 cudaError_t launch_build(const BuildArgs &a, cudaStream_t st, Prof *prof)
@@ -160,11 +158,11 @@ cudaError_t launch_build(const BuildArgs &a, cudaStream_t st, Prof *prof)
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (a.N > 0) {
         prof_begin(prof, st, KID_SCATTER);
-        k_scatter<<<(unsigned)div_up(a.N, 256), 256, 0, st>>>(a.pts, a.N, a.cam, a.keyrank, a.start, a.spts);
+        k_scatter<<<(unsigned)div_up(a.N, 256), 256, 0, st>>>(a.pts, a.N, a.cam, a.keyrank, a.start, a.spts_tmp);
         prof_end(prof, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         prof_begin(prof, st, KID_SORT);
-        k_bucket_sort<<<(unsigned)div_up(a.P, 256), 256, 0, st>>>(a.start, a.P, a.spts);
+        k_bucket_sort<<<(unsigned)div_up(a.N, 256), 256, 0, st>>>(a.keyrank, a.N, a.start, a.spts_tmp, a.spts);
         prof_end(prof, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

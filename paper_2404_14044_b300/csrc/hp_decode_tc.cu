@@ -486,8 +486,10 @@ __global__ void __launch_bounds__(128, 1) k_mma_selftest(const uint16_t *A, cons
 // Hand-offs: full[b] (producers -> consumers, 8 warp arrivals), empty[b]
 // (tcgen05.commit after the layer-0 MMAs that read buffer b), lbar[b] (bulk
 // copy of a tile's neighbour lists), mma (per layer).  Every wait is bounded.
-constexpr int kWsConsumerWarps = 16;
+constexpr int kWsConsumerWarps = 16;      // 4 TMEM lane quarters x kWsGroups column groups
 constexpr int kWsProducerWarps = 8;
+constexpr int kWsGroups = kWsConsumerWarps / 4;
+constexpr int kWsBatch = 2;               // 8-column chunks a consumer thread reads from TMEM at once
 constexpr int kWsThreads = (kWsConsumerWarps + kWsProducerWarps) * 32;
 constexpr uint32_t kWsCols = 512, kColAH = 256, kColAL = 320;
 
@@ -768,15 +770,15 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
                 tc::fence_after_sync();
 
                 // ---- epilogue: this thread's row; 8-column chunks round-robin
-                // over the column groups, two at a time (TMEM -> registers -> TMEM)
+                // over the column groups, kWsBatch at a time (TMEM -> registers -> TMEM)
                 const float *bias = f32 + L.bias[l];
                 const bool last = (l + 1 == L.nh);
                 const int nch = fo / 8;
-                for (int ch0 = cg; ch0 < nch; ch0 += 8) {
-                    float v1[2][8], v2[2][8];
+                for (int ch0 = cg; ch0 < nch; ch0 += kWsGroups * kWsBatch) {
+                    float v1[kWsBatch][8], v2[kWsBatch][8];
 #pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        const int ch = ch0 + 4 * j;
+                    for (int j = 0; j < kWsBatch; ++j) {
+                        const int ch = ch0 + kWsGroups * j;
                         if (ch < nch) {
                             tc::ld8(d1 + lane_off + (uint32_t)(8 * ch), v1[j]);
                             if constexpr (!kBF16) tc::ld8(d2 + lane_off + (uint32_t)(8 * ch), v2[j]);
@@ -784,8 +786,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
                     }
                     tc::wait_ld();
 #pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        const int ch = ch0 + 4 * j;
+                    for (int j = 0; j < kWsBatch; ++j) {
+                        const int ch = ch0 + kWsGroups * j;
                         if (ch >= nch) break;
                         const int c = 8 * ch;
                         float h[8];
@@ -844,9 +846,12 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
                 const float *bl = f32 + L.bias[a.n_layers - 1];
                 float o[4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    o[i] = ((o4[i] + comb[(kTcTile + row) * 4 + i]) + comb[(2 * kTcTile + row) * 4 + i]) +
-                           comb[(3 * kTcTile + row) * 4 + i] + bl[i];
+                for (int i = 0; i < 4; ++i) {
+                    o[i] = o4[i];
+#pragma unroll
+                    for (int gr = 1; gr < kWsGroups; ++gr) o[i] += comb[(gr * kTcTile + row) * 4 + i];
+                    o[i] += bl[i];
+                }
                 const int64_t g = base + row;
                 if (g < S)
                     a.sample_out[g] = make_float4(softplus_f(o[0]), sigmoid_f(o[1]), sigmoid_f(o[2]), sigmoid_f(o[3]));

@@ -46,6 +46,7 @@ struct BuildArgs {
     uint32_t *start;        // [P+1]
     uint2 *keyrank;         // [N]
     float4 *spts;           // [N]
+    float4 *spts_tmp;       // [N] scattered in atomic order, before the in-bucket sort
     uint64_t *scan_flags;   // [ceil((P+1)/kScanTile)]
     uint32_t *scan_ticket;
     ErrWord *err;

@@ -155,20 +155,283 @@ __global__ void __launch_bounds__(256) k_ray_table(Cam cam, int mode, float rdd,
     tab[i] = make_float4(r.dx, r.dy, r.dz, r.c);
 }
 
+// One ray on one warp (the warp-per-ray search); cp / ck / ci: the warp's
+// candidate buffers (kCandCap entries each).
+template <int KB>
+__device__ __forceinline__ void wide_ray(const SearchArgs &a, const float2 *interval, int64_t ri, float4 *cp,
+                                         uint64_t *ck, uint8_t *ci)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int K = a.K, n_max = a.n_max;
+    const int64_t npix = (int64_t)a.cam.width * a.cam.height;
+    const int pix = a.rays ? __ldg(a.rays + ri) : (int)ri;
+    if (pix < 0 || pix >= npix) {
+        if (lane == 0) {
+            set_error(a.err, HP_ERR_BAD_RAY, ri);
+            a.n_s[ri] = 0;
+            a.primary[ri] = -1;
+            a.cand_count[ri] = 0;
+        }
+        return;
+    }
+    const int pv = pix / a.cam.width, pu = pix - pv * a.cam.width;
+    const float4 rt = __ldg(a.raytab + pix);
+    Ray ray;
+    ray.dx = rt.x;
+    ray.dy = rt.y;
+    ray.dz = rt.z;
+    ray.c = rt.w;
+
+    // depth range and window half-width of this ray: the plain search uses
+    // [t_near, t_far] and h; the proposal-restricted search the ray's
+    // interval and the (smaller) window bound that follows from its t0
+    float tn = a.cam.t_near, tf = a.cam.t_far;
+    int hr = a.h;
+    if (interval) {
+        const float2 iv = __ldg(interval + ri);
+        tn = fmaxf(tn, iv.x);
+        tf = fminf(tf, iv.y);
+        if (a.mode == HP_RADIUS_FIXED) {
+            // window bound for t >= tn (contract step D12, written out with
+            // single roundings so the CPU reference walks the same window)
+            const float zlo = fmaxf(dsub(dmul(tn, a.cos_max), dmul(a.r, a.sin_max)), a.cam.z_near);
+            const float lim = dadd(dmul(ddiv(a.win_fx, zlo), 1.001f), 1e-3f);
+            if (lim < (float)a.h) hr = min(a.h, (int)floorf(dadd(lim, 0.5f)));
+        }
+    }
+    const int span = 2 * hr + 1, off = a.h - hr;
+    // restricted search: does the full window hold any point at all?  If
+    // not, the ray is empty for the plain search too and needs no fallback
+    bool full_window_empty = false;
+    if (interval) {
+        const int fspan = 2 * a.h + 1;
+        int flen = 0;
+        for (int q = lane; q < fspan; q += 32) {
+            const int64_t kb = (int64_t)(pv + q) * a.Wp + pu;
+            flen += (int)(__ldg(a.start + kb + fspan) - __ldg(a.start + kb));
+        }
+        full_window_empty = __ballot_sync(kFull, flen != 0) == 0;
+    }
+
+    // ---- window walk.  The s rows' runs are concatenated into one index
+    // space (lane q holds row q's [lo, lo+len) and its exclusive offset),
+    // so every load instruction serves 32 points whatever the row lengths.
+    int kept = 0, total = 0;
+    bool early_hit = false, late_hit = false;
+    for (int r0 = 0; r0 < span; r0 += 32) {
+        const int nrows = min(32, span - r0);
+        uint32_t lo = 0;
+        int len = 0;
+        if (lane < nrows) {
+            const int64_t kb = (int64_t)(pv + off + r0 + lane) * a.Wp + pu + off;
+            lo = __ldg(a.start + kb);
+            len = (int)(__ldg(a.start + kb + span) - lo);
+        }
+        const int incl = warp_incl_scan(len);
+        const int tot = __shfl_sync(kFull, incl, 31);
+        const int excl = incl - len;
+        for (int v0 = 0; v0 < tot; v0 += 32) {
+            const int v = v0 + lane;
+            // row of v: the last row whose exclusive offset is <= v (binary search)
+            int row = 0;
+            for (int step = 16; step > 0; step >>= 1) {
+                const int cand = row + step;
+                const int ec = __shfl_sync(kFull, excl, cand < nrows ? cand : 31);
+                if (cand < nrows && v >= ec) row = cand;
+            }
+            const uint32_t rlo = __shfl_sync(kFull, lo, row);
+            const int rex = __shfl_sync(kFull, excl, row);
+            bool acc = false;
+            float t = 0.0f;
+            float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (v < tot) {
+                p = __ldg(a.spts + rlo + (uint32_t)(v - rex));
+                if (!interval) {
+                    acc = accept_point(a, ray, p, tn, tf, t);
+                } else {
+                    // restricted: points the plain search would accept outside
+                    // [t0, t1] flag a possible miss (a surface in front, or
+                    // the cluster running on behind t1)
+                    const bool plain = accept_point(a, ray, p, a.cam.t_near, a.cam.t_far, t);
+                    acc = plain && t >= tn && t <= tf;
+                    if (plain && t < tn) early_hit = true;
+                    if (plain && t > tf) late_hit = true;
+                }
+            }
+            const uint64_t key = ((uint64_t)__float_as_uint(t) << 32) | (uint32_t)__float_as_int(p.w);
+            append_candidates(acc, key, p, lane, lt_mask, a.cand_cap, ck, cp, kept, total);
+        }
+    }
+    __syncwarp();
+
+    // ---- sort the candidates by (t, id): rank sort, keys being unique
+    // (ids); lane l ranks candidates l, l+32, l+64, l+96 against all C
+    // (broadcast reads), then every candidate moves to its rank
+    const int C = kept;
+    {
+        static_assert(kCandCap <= 128, "rank sort holds 4 candidates per lane");
+        uint64_t key[4];
+        int rank[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int e = lane + 32 * m;
+            key[m] = e < C ? ck[e] : ~0ull;
+            rank[m] = 0;
+        }
+        for (int c = 0; c < C; ++c) {
+            const uint64_t kc = ck[c];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) rank[m] += kc < key[m] ? 1 : 0;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int e = lane + 32 * m;
+            if (e < C) {
+                ck[rank[m]] = key[m];
+                ci[rank[m]] = (uint8_t)e;
+            }
+        }
+        __syncwarp();
+    }
+
+    // ---- adaptive primary surface sampling.  Lanes own candidates: lane
+    // j walks all candidates (shared-memory broadcast) keeping the K nearest
+    // within r(t_j) in registers, and forms d_j and alpha_j.  The product
+    // w_j = alpha_j T_j is then taken in depth order across the warp.
+    float T = 1.0f, t_prev = 0.0f;
+    int jstar = -1, ns = 0, prim = -1;
+    const int64_t slot0 = ri * n_max;
+    bool done = false;
+    early_hit = __any_sync(kFull, early_hit);
+    late_hit = __any_sync(kFull, late_hit);
+    for (int c0 = 0; c0 < C && !done; c0 += 32) {
+        const int j = c0 + lane;
+        float tj = 0.0f, alpha = 0.0f;
+        int idj = -1;
+        uint64_t keys[KB];
+#pragma unroll
+        for (int m = 0; m < KB; ++m) keys[m] = ~0ull;
+        if (j < C) {
+            const uint64_t kj = ck[j];
+            tj = __uint_as_float((uint32_t)(kj >> 32));
+            idj = (int)(uint32_t)kj;
+            const float rad = radius_at(a.mode, a.r, ray, tj);
+            const float rad2 = dmul(rad, rad);
+            // Only candidates whose depth is within lim of t_j can lie within
+            // r(t_j) of x_j: |x_j - P_i| >= |t_j - t_i| up to float32 rounding
+            // (~1e-6 (1 + t)), far inside the margin, so the set is unchanged.
+            const float lim = rad * 1.001f + 1e-5f * (1.0f + tj);
+            int i0 = j;
+            while (i0 > 0 && tj - __uint_as_float((uint32_t)(ck[i0 - 1] >> 32)) <= lim) --i0;
+            for (int i = i0; i < C; ++i) {
+                const uint64_t ki = ck[i];
+                if (__uint_as_float((uint32_t)(ki >> 32)) - tj > lim) break;
+                const float4 Pi = cp[ci[i]];
+                const float ax = dfma(tj, ray.dx, -Pi.x);
+                const float ay = dfma(tj, ray.dy, -Pi.y);
+                const float az = dfma(tj, ray.dz, -Pi.z);
+                const float d2 = dadd(dadd(dmul(ax, ax), dmul(ay, ay)), dmul(az, az));
+                if (d2 <= rad2) knn_insert<KB>(keys, ((uint64_t)__float_as_uint(d2) << 32) | (uint32_t)ki);
+            }
+            float s = 0.0f;
+            int kp = 0;
+#pragma unroll
+            for (int m = 0; m < KB; ++m) {
+                if (m < K && keys[m] != ~0ull) {
+                    s = dadd(s, dsqrt(__uint_as_float((uint32_t)(keys[m] >> 32))));
+                    ++kp;
+                }
+            }
+            const float dj = ddiv(s, (float)kp);
+            alpha = dmul(a.gamma, exp32(-ddiv(dmul(dj, dj), a.beta2)));
+        }
+        const int nj = min(32, C - c0);
+        const int ns0 = ns;
+        unsigned sel = 0;
+        for (int jj = 0; jj < nj; ++jj) {
+            const float aj = __shfl_sync(kFull, alpha, jj);
+            const float tjj = __shfl_sync(kFull, tj, jj);
+            if (jstar >= 0 && a.gap_k > 0.0f) {
+                const float gap = dsub(tjj, t_prev);
+                if (!(gap <= dmul(a.gap_k, radius_at(a.mode, a.r, ray, t_prev)))) {
+                    done = true;
+                    break;
+                }
+            }
+            const float w = dmul(aj, T);
+            T = dmul(T, dsub(1.0f, aj));
+            if (w > a.eps_w) {
+                if (jstar < 0) {
+                    jstar = c0 + jj;
+                    const float4 pj = cp[ci[jstar]];
+                    prim = (int)pixel_key(a.cam, a.h, make_float3(pj.x, pj.y, pj.z));
+                }
+                sel |= 1u << jj;
+                if (++ns == n_max) {
+                    done = true;
+                    break;
+                }
+            }
+            t_prev = tjj;
+            // w_k <= gamma T_k <= gamma T for every later k: nothing more can pass
+            if (!(dmul(a.gamma, T) > a.eps_w)) {
+                done = true;
+                break;
+            }
+        }
+        if ((sel >> lane) & 1u) {
+            const int64_t slot = slot0 + ns0 + __popc(sel & lt_mask);
+            a.slot_t[slot] = tj;
+            a.slot_src[slot] = idj;
+#pragma unroll
+            for (int m = 0; m < KB; ++m) {
+                if (m < K) {
+                    const bool ok = keys[m] != ~0ull;
+                    a.slot_nbr[slot * K + m] = ok ? (int)(uint32_t)keys[m] : -1;
+                    a.slot_dist[slot * K + m] = ok ? dsqrt(__uint_as_float((uint32_t)(keys[m] >> 32))) : 0.0f;
+                }
+            }
+        }
+    }
+    __syncwarp();
+    if (lane < ns) {
+        const int64_t slot = slot0 + lane;
+        const float tm = a.slot_t[slot];
+        a.slot_delta[slot] = (lane + 1 < ns) ? a.slot_t[slot + 1] - tm : 2.0f * radius_at(a.mode, a.r, ray, tm);
+    }
+    if (lane == 0) {
+        a.n_s[ri] = ns;
+        a.primary[ri] = prim;
+        a.cand_count[ri] = total;
+        // fall back to the plain search when the restricted one is empty
+        // (unless the whole window is), when the plain search accepts a
+        // point in front of t0, or when the selection ran out of
+        // candidates while the plain search has more behind t1
+        // a point behind t1 cannot change the result when a sample was kept
+        // and the last restricted candidate lies more than max(gap_k, 1) r
+        // before t1: the gap rule stops the plain selection before it
+        bool late_ok = false;
+        if (interval && jstar >= 0 && a.gap_k > 0.0f && C > 0) {
+            const float tl = __uint_as_float((uint32_t)(ck[C - 1] >> 32));
+            late_ok = dsub(tf, tl) > dmul(fmaxf(a.gap_k, 1.0f), radius_at(a.mode, a.r, ray, tl));
+        }
+        const bool miss = (ns == 0 && !full_window_empty) || early_hit || (!done && late_hit && !late_ok);
+        if (interval && a.fallback && miss) a.fallback[atomicAdd(a.fallback_count, 1u)] = (int32_t)ri;
+    }
+    __syncwarp();
+}
+
 template <int KB>
 __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select_wide(const SearchArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const SearchSmem L = search_layout();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const unsigned lt_mask = (1u << lane) - 1u;
-
     float4 *cp = reinterpret_cast<float4 *>(smem + L.cp) + warp * kCandCap;
     uint64_t *ck = reinterpret_cast<uint64_t *>(smem + L.ck) + warp * kCandCap;
     uint8_t *ci = reinterpret_cast<uint8_t *>(smem + L.ci) + warp * kCandCap;
-
-    const int K = a.K, n_max = a.n_max;
-    const int64_t npix = (int64_t)a.cam.width * a.cam.height;
     const int64_t R_eff = a.count_ptr ? (int64_t)*a.count_ptr : a.R;
 
     // every warp pulls the next listed ray from a grid-wide counter, so heavy
@@ -179,295 +442,9 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select_wide(const 
         if (lane == 0) rl = atomicAdd(a.pull, 1ull);
         rl = __shfl_sync(kFull, rl, 0);
         if ((int64_t)rl >= R_eff) break;
-        const int64_t rl_idx = (int64_t)rl;
-        // ri: the ray's index in the outputs (fallback pass: from the list)
-        const int64_t ri = a.ray_map ? (int64_t)__ldg(a.ray_map + rl_idx) : rl_idx;
-        const int pix = a.rays ? __ldg(a.rays + ri) : (int)ri;
-        if (pix < 0 || pix >= npix) {
-            if (lane == 0) {
-                set_error(a.err, HP_ERR_BAD_RAY, ri);
-                a.n_s[ri] = 0;
-                a.primary[ri] = -1;
-                a.cand_count[ri] = 0;
-            }
-            continue;
-        }
-        const int pv = pix / a.cam.width, pu = pix - pv * a.cam.width;
-        const float4 rt = __ldg(a.raytab + pix);
-        Ray ray;
-        ray.dx = rt.x;
-        ray.dy = rt.y;
-        ray.dz = rt.z;
-        ray.c = rt.w;
-
-        // depth range and window half-width of this ray: the plain search uses
-        // [t_near, t_far] and h; the proposal-restricted search the ray's
-        // interval and the (smaller) window bound that follows from its t0
-        float tn = a.cam.t_near, tf = a.cam.t_far;
-        int hr = a.h;
-        if (a.interval) {
-            const float2 iv = __ldg(a.interval + ri);
-            tn = fmaxf(tn, iv.x);
-            tf = fminf(tf, iv.y);
-            if (a.mode == HP_RADIUS_FIXED) {
-                // window bound for t >= tn (contract step D12, written out with
-                // single roundings so the CPU reference walks the same window)
-                const float zlo = fmaxf(dsub(dmul(tn, a.cos_max), dmul(a.r, a.sin_max)), a.cam.z_near);
-                const float lim = dadd(dmul(ddiv(a.win_fx, zlo), 1.001f), 1e-3f);
-                if (lim < (float)a.h) hr = min(a.h, (int)floorf(dadd(lim, 0.5f)));
-            }
-        }
-        const int span = 2 * hr + 1, off = a.h - hr;
-        // restricted search: does the full window hold any point at all?  If
-        // not, the ray is empty for the plain search too and needs no fallback
-        bool full_window_empty = false;
-        if (a.interval) {
-            const int fspan = 2 * a.h + 1;
-            int flen = 0;
-            for (int q = lane; q < fspan; q += 32) {
-                const int64_t kb = (int64_t)(pv + q) * a.Wp + pu;
-                flen += (int)(__ldg(a.start + kb + fspan) - __ldg(a.start + kb));
-            }
-            full_window_empty = __ballot_sync(kFull, flen != 0) == 0;
-        }
-
-        // ---- window walk.  The s rows' runs are concatenated into one index
-        // space (lane q holds row q's [lo, lo+len) and its exclusive offset),
-        // so every load instruction serves 32 points whatever the row lengths.
-        int kept = 0, total = 0;
-        bool early_hit = false, late_hit = false;
-        for (int r0 = 0; r0 < span; r0 += 32) {
-            const int nrows = min(32, span - r0);
-            uint32_t lo = 0;
-            int len = 0;
-            if (lane < nrows) {
-                const int64_t kb = (int64_t)(pv + off + r0 + lane) * a.Wp + pu + off;
-                lo = __ldg(a.start + kb);
-                len = (int)(__ldg(a.start + kb + span) - lo);
-            }
-            const int incl = warp_incl_scan(len);
-            const int tot = __shfl_sync(kFull, incl, 31);
-            const int excl = incl - len;
-            for (int v0 = 0; v0 < tot; v0 += 32) {
-                const int v = v0 + lane;
-                // row of v: the last row whose exclusive offset is <= v (binary search)
-                int row = 0;
-                for (int step = 16; step > 0; step >>= 1) {
-                    const int cand = row + step;
-                    const int ec = __shfl_sync(kFull, excl, cand < nrows ? cand : 31);
-                    if (cand < nrows && v >= ec) row = cand;
-                }
-                const uint32_t rlo = __shfl_sync(kFull, lo, row);
-                const int rex = __shfl_sync(kFull, excl, row);
-                bool acc = false;
-                float t = 0.0f;
-                float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (v < tot) {
-                    p = __ldg(a.spts + rlo + (uint32_t)(v - rex));
-                    if (!a.interval) {
-                        acc = accept_point(a, ray, p, tn, tf, t);
-                    } else {
-                        // restricted: points the plain search would accept outside
-                        // [t0, t1] flag a possible miss (a surface in front, or
-                        // the cluster running on behind t1)
-                        const bool plain = accept_point(a, ray, p, a.cam.t_near, a.cam.t_far, t);
-                        acc = plain && t >= tn && t <= tf;
-                        if (plain && t < tn) early_hit = true;
-                        if (plain && t > tf) late_hit = true;
-                    }
-                }
-                const uint64_t key = ((uint64_t)__float_as_uint(t) << 32) | (uint32_t)__float_as_int(p.w);
-                append_candidates(acc, key, p, lane, lt_mask, a.cand_cap, ck, cp, kept, total);
-            }
-        }
-        __syncwarp();
-
-        // ---- sort the candidates by (t, id): up to 32 in registers (shuffle
-        // bitonic network), more in shared memory
-        const int C = kept;
-        if (C <= 16) {
-            // rank sort: keys are unique (ids), rank = number of smaller keys
-            const uint64_t key = lane < C ? ck[lane] : ~0ull;
-            int rank = 0;
-            for (int i = 0; i < C; ++i) rank += (ck[i] < key) ? 1 : 0;
-            __syncwarp();
-            if (lane < C) {
-                ck[rank] = key;
-                ci[rank] = (uint8_t)lane;
-            }
-            __syncwarp();
-        } else if (C <= 32) {
-            uint64_t key = lane < C ? ck[lane] : ~0ull;
-            int idx = lane;
-#pragma unroll
-            for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-                for (int j = k >> 1; j > 0; j >>= 1) {
-                    const uint64_t ok = __shfl_xor_sync(kFull, key, j);
-                    const int oi = __shfl_xor_sync(kFull, idx, j);
-                    const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
-                    if (keep_min ? (ok < key) : (ok > key)) {
-                        key = ok;
-                        idx = oi;
-                    }
-                }
-            }
-            __syncwarp();
-            ck[lane] = key;
-            ci[lane] = (uint8_t)idx;
-            __syncwarp();
-        } else {
-            int n2 = 64;
-            while (n2 < C) n2 <<= 1;
-            for (int e = C + lane; e < n2; e += 32) ck[e] = ~0ull;
-            for (int e = lane; e < n2; e += 32) ci[e] = (uint8_t)e;
-            __syncwarp();
-            for (int k = 2; k <= n2; k <<= 1) {
-                for (int j = k >> 1; j > 0; j >>= 1) {
-                    for (int e = lane; e < n2; e += 32) {
-                        const int x = e ^ j;
-                        if (x > e) {
-                            const bool up = (e & k) == 0;
-                            const uint64_t A = ck[e], B = ck[x];
-                            if ((A > B) == up) {
-                                ck[e] = B;
-                                ck[x] = A;
-                                const uint8_t t8 = ci[e];
-                                ci[e] = ci[x];
-                                ci[x] = t8;
-                            }
-                        }
-                    }
-                    __syncwarp();
-                }
-            }
-        }
-
-        // ---- adaptive primary surface sampling.  Lanes own candidates: lane
-        // j walks all candidates (shared-memory broadcast) keeping the K nearest
-        // within r(t_j) in registers, and forms d_j and alpha_j.  The product
-        // w_j = alpha_j T_j is then taken in depth order across the warp.
-        float T = 1.0f, t_prev = 0.0f;
-        int jstar = -1, ns = 0, prim = -1;
-        const int64_t slot0 = ri * n_max;
-        bool done = false;
-        early_hit = __any_sync(kFull, early_hit);
-        late_hit = __any_sync(kFull, late_hit);
-        for (int c0 = 0; c0 < C && !done; c0 += 32) {
-            const int j = c0 + lane;
-            float tj = 0.0f, alpha = 0.0f;
-            int idj = -1;
-            uint64_t keys[KB];
-#pragma unroll
-            for (int m = 0; m < KB; ++m) keys[m] = ~0ull;
-            if (j < C) {
-                const uint64_t kj = ck[j];
-                tj = __uint_as_float((uint32_t)(kj >> 32));
-                idj = (int)(uint32_t)kj;
-                const float rad = radius_at(a.mode, a.r, ray, tj);
-                const float rad2 = dmul(rad, rad);
-                // Only candidates whose depth is within lim of t_j can lie within
-                // r(t_j) of x_j: |x_j - P_i| >= |t_j - t_i| up to float32 rounding
-                // (~1e-6 (1 + t)), far inside the margin, so the set is unchanged.
-                const float lim = rad * 1.001f + 1e-5f * (1.0f + tj);
-                int i0 = j;
-                while (i0 > 0 && tj - __uint_as_float((uint32_t)(ck[i0 - 1] >> 32)) <= lim) --i0;
-                for (int i = i0; i < C; ++i) {
-                    const uint64_t ki = ck[i];
-                    if (__uint_as_float((uint32_t)(ki >> 32)) - tj > lim) break;
-                    const float4 Pi = cp[ci[i]];
-                    const float ax = dfma(tj, ray.dx, -Pi.x);
-                    const float ay = dfma(tj, ray.dy, -Pi.y);
-                    const float az = dfma(tj, ray.dz, -Pi.z);
-                    const float d2 = dadd(dadd(dmul(ax, ax), dmul(ay, ay)), dmul(az, az));
-                    if (d2 <= rad2) knn_insert<KB>(keys, ((uint64_t)__float_as_uint(d2) << 32) | (uint32_t)ki);
-                }
-                float s = 0.0f;
-                int kp = 0;
-#pragma unroll
-                for (int m = 0; m < KB; ++m) {
-                    if (m < K && keys[m] != ~0ull) {
-                        s = dadd(s, dsqrt(__uint_as_float((uint32_t)(keys[m] >> 32))));
-                        ++kp;
-                    }
-                }
-                const float dj = ddiv(s, (float)kp);
-                alpha = dmul(a.gamma, exp32(-ddiv(dmul(dj, dj), a.beta2)));
-            }
-            const int nj = min(32, C - c0);
-            const int ns0 = ns;
-            unsigned sel = 0;
-            for (int jj = 0; jj < nj; ++jj) {
-                const float aj = __shfl_sync(kFull, alpha, jj);
-                const float tjj = __shfl_sync(kFull, tj, jj);
-                if (jstar >= 0 && a.gap_k > 0.0f) {
-                    const float gap = dsub(tjj, t_prev);
-                    if (!(gap <= dmul(a.gap_k, radius_at(a.mode, a.r, ray, t_prev)))) {
-                        done = true;
-                        break;
-                    }
-                }
-                const float w = dmul(aj, T);
-                T = dmul(T, dsub(1.0f, aj));
-                if (w > a.eps_w) {
-                    if (jstar < 0) {
-                        jstar = c0 + jj;
-                        const float4 pj = cp[ci[jstar]];
-                        prim = (int)pixel_key(a.cam, a.h, make_float3(pj.x, pj.y, pj.z));
-                    }
-                    sel |= 1u << jj;
-                    if (++ns == n_max) {
-                        done = true;
-                        break;
-                    }
-                }
-                t_prev = tjj;
-                // w_k <= gamma T_k <= gamma T for every later k: nothing more can pass
-                if (!(dmul(a.gamma, T) > a.eps_w)) {
-                    done = true;
-                    break;
-                }
-            }
-            if ((sel >> lane) & 1u) {
-                const int64_t slot = slot0 + ns0 + __popc(sel & lt_mask);
-                a.slot_t[slot] = tj;
-                a.slot_src[slot] = idj;
-#pragma unroll
-                for (int m = 0; m < KB; ++m) {
-                    if (m < K) {
-                        const bool ok = keys[m] != ~0ull;
-                        a.slot_nbr[slot * K + m] = ok ? (int)(uint32_t)keys[m] : -1;
-                        a.slot_dist[slot * K + m] = ok ? dsqrt(__uint_as_float((uint32_t)(keys[m] >> 32))) : 0.0f;
-                    }
-                }
-            }
-        }
-        __syncwarp();
-        if (lane < ns) {
-            const int64_t slot = slot0 + lane;
-            const float tm = a.slot_t[slot];
-            a.slot_delta[slot] = (lane + 1 < ns) ? a.slot_t[slot + 1] - tm : 2.0f * radius_at(a.mode, a.r, ray, tm);
-        }
-        if (lane == 0) {
-            a.n_s[ri] = ns;
-            a.primary[ri] = prim;
-            a.cand_count[ri] = total;
-            // fall back to the plain search when the restricted one is empty
-            // (unless the whole window is), when the plain search accepts a
-            // point in front of t0, or when the selection ran out of
-            // candidates while the plain search has more behind t1
-            // a point behind t1 cannot change the result when a sample was kept
-            // and the last restricted candidate lies more than max(gap_k, 1) r
-            // before t1: the gap rule stops the plain selection before it
-            bool late_ok = false;
-            if (a.interval && jstar >= 0 && a.gap_k > 0.0f && C > 0) {
-                const float tl = __uint_as_float((uint32_t)(ck[C - 1] >> 32));
-                late_ok = dsub(tf, tl) > dmul(fmaxf(a.gap_k, 1.0f), radius_at(a.mode, a.r, ray, tl));
-            }
-            const bool miss = (ns == 0 && !full_window_empty) || early_hit || (!done && late_hit && !late_ok);
-            if (a.interval && a.fallback && miss) a.fallback[atomicAdd(a.fallback_count, 1u)] = (int32_t)ri;
-        }
-        __syncwarp();
+        // ri: the ray's index in the outputs (listed passes: from the list)
+        const int64_t ri = a.ray_map ? (int64_t)__ldg(a.ray_map + (int64_t)rl) : (int64_t)rl;
+        wide_ray<KB>(a, a.interval, ri, cp, ck, ci);
     }
 }
 
@@ -764,20 +741,26 @@ __global__ void __launch_bounds__(kLaneWarps * 32, lane_blocks_per_sm(KB)) k_sea
         // more candidates than this lane may answer for: the warp-per-ray search takes the ray
         if (!lane_ray<KB, kLearned>(a, ri, pix, lt, li, pw)) a.wide[atomicAdd(a.wide_count, 1u)] = (int32_t)ri;
     }
+
 }
 
 // Packing (K6): exclusive scan of n_s with a decoupled look-back over
-// uniform tiles of 256 rays, then each thread copies its ray's sample slots
-// (a contiguous run of n_s rows) to the packed outputs.
-__global__ void __launch_bounds__(256) k_pack_samples(const SearchArgs a)
+// uniform tiles of 256 rays; the tile's samples form one contiguous packed
+// range, which the whole block copies with coalesced stores (each packed
+// sample's slot is looked up in a shared-memory map).
+constexpr int kPackRays = 256;
+
+__global__ void __launch_bounds__(kPackRays) k_pack_samples(const SearchArgs a)
 {
     __shared__ int64_t s_tile, s_prefix;
     __shared__ int s_warp[8];
+    __shared__ int s_total;
+    __shared__ uint16_t s_slot[kPackRays * kMaxSamples];   // packed sample -> (ray in tile) << 4 | m
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_tile = atomicAdd(a.ticket, 1u);
     __syncthreads();
     const int64_t tile = s_tile;
-    const int64_t ri = tile * 256 + tid;
+    const int64_t ri = tile * kPackRays + tid;
     const int ns = ri < a.R ? a.n_s[ri] : 0;
     const int incl = warp_incl_scan(ns);
     if (lane == 31) s_warp[warp] = incl;
@@ -786,43 +769,43 @@ __global__ void __launch_bounds__(256) k_pack_samples(const SearchArgs a)
         const int w = lane < 8 ? s_warp[lane] : 0;
         const int wi = warp_incl_scan(w);
         if (lane < 8) s_warp[lane] = wi - w;
-        if (lane == 7) s_prefix = lookback_prefix(a.flags, tile, wi, a.err, a.spin_limit, true);
+        if (lane == 7) {
+            s_total = wi;
+            s_prefix = lookback_prefix(a.flags, tile, wi, a.err, a.spin_limit, true);
+        }
     }
     __syncthreads();
-    const int64_t off = s_prefix + s_warp[warp] + (incl - ns);
+    const int local = s_warp[warp] + (incl - ns);     // this ray's first sample within the tile
+    const int64_t base = s_prefix;
+    const int64_t off = base + local;
     if (ri < a.R) a.sample_offset[ri] = off;
     if (ri == a.R - 1) {
         a.sample_offset[a.R] = off + ns;
         if (off + ns > a.capacity) set_error(a.err, HP_ERR_OVERFLOW, off + ns);
     }
-    // each thread copies its own ray's rows; neighbouring rays are adjacent
-    // in the packed output, so a warp's stores stay nearly contiguous
-    if (ri < a.R && ns > 0) {
-        const int K = a.K;
-        const int64_t src = ri * a.n_max;
-        int64_t nn = a.capacity - off;
-        nn = nn < ns ? (nn > 0 ? nn : 0) : ns;
-        for (int m = 0; m < nn; ++m) {
-            a.t[off + m] = a.slot_t[src + m];
-            a.src[off + m] = a.slot_src[src + m];
-            a.delta[off + m] = a.slot_delta[src + m];
-            a.ray[off + m] = (int)ri;
-        }
-        const int64_t n_el = nn * K;
-        if ((K & 3) == 0) {
-            const int4 *sn = reinterpret_cast<const int4 *>(a.slot_nbr + src * K);
-            const float4 *sd = reinterpret_cast<const float4 *>(a.slot_dist + src * K);
-            int4 *dn = reinterpret_cast<int4 *>(a.nbr + off * K);
-            float4 *dd = reinterpret_cast<float4 *>(a.nbr_dist + off * K);
-            for (int64_t e = 0; e < n_el / 4; ++e) {
-                dn[e] = sn[e];
-                dd[e] = sd[e];
-            }
-        } else {
-            for (int64_t e = 0; e < n_el; ++e) {
-                a.nbr[off * K + e] = a.slot_nbr[src * K + e];
-                a.nbr_dist[off * K + e] = a.slot_dist[src * K + e];
-            }
+    for (int m = 0; m < ns; ++m) s_slot[local + m] = (uint16_t)((tid << 4) | m);
+    __syncthreads();
+    // samples that fit the capacity
+    int64_t total = s_total;
+    if (base + total > a.capacity) total = a.capacity > base ? a.capacity - base : 0;
+    const int64_t ray0 = tile * kPackRays;
+    for (int p = tid; p < total; p += kPackRays) {
+        const int v = s_slot[p];
+        const int64_t r = ray0 + (v >> 4);
+        const int64_t sl = r * a.n_max + (v & 15);
+        a.t[base + p] = a.slot_t[sl];
+        a.src[base + p] = a.slot_src[sl];
+        a.delta[base + p] = a.slot_delta[sl];
+        a.ray[base + p] = (int)r;
+    }
+    // neighbour ids and distances: lane (sample sub, element e) per warp step
+    const int K = a.K, per = 32 / K, sub = lane / K, e = lane - sub * K;
+    if (sub < per) {
+        for (int64_t p = (int64_t)warp * per + sub; p < total; p += 8 * per) {
+            const int v = s_slot[p];
+            const int64_t sl = (ray0 + (v >> 4)) * a.n_max + (v & 15);
+            a.nbr[(base + p) * K + e] = a.slot_nbr[sl * K + e];
+            a.nbr_dist[(base + p) * K + e] = a.slot_dist[sl * K + e];
         }
     }
 }
@@ -911,7 +894,7 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof)
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     prof_begin(prof, st, KID_PACK);
-    k_pack_samples<<<(unsigned)tiles, 256, 0, st>>>(a);
+    k_pack_samples<<<(unsigned)tiles, kPackRays, 0, st>>>(a);
     prof_end(prof, st);
     return cudaGetLastError();
 }
