@@ -151,12 +151,12 @@ def algorithmic(kernel, N, Nv, P, R, S, K, F, dims, U, tensor_decode=True):
 # kernel is compiled from when it was captured; once those change the figure
 # no longer describes the kernel and the roofline reports traffic = null.
 NCU_TRAFFIC = {
-    "k_search_select": {"bytes": 53920256 + 52001536,
+    "k_search_select": {"bytes": 54825472 + 57423104,
                         "sources": ("hp_search.cu", "hp_common.cuh", "hp_kernels.cuh"),
-                        "sha256": "dbdd1547d59219f0d77fa440e6de10723b39e61c98b2df8c3aab6d435c3c8f0e"},
-    "k_aggregate_decode": {"bytes": 78054656 + 1039616,
+                        "sha256": "c459b2948fec7d07ac810568a8d5dab2f4ee29d8f549758865a01a0a46099967"},
+    "k_aggregate_decode": {"bytes": 78131712 + 1125120,
                            "sources": ("hp_decode_tc.cu", "hp_tc.cuh", "hp_common.cuh", "hp_kernels.cuh"),
-                           "sha256": "79162e6cc5f3761f284e75d85c79d43076e04e31c0b6a78b9ada1cb964754c37"},
+                           "sha256": "881e39d5b0b910b61db659eb7cf5888c8065c276933fff53694f4004cf35651c"},
 
 }
 
