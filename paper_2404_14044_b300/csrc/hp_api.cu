@@ -154,7 +154,7 @@ size_t table_region_bytes(int64_t N, int64_t P, int64_t npix)
 size_t search_region_bytes(int64_t R, int n_max, int K)
 {
     const size_t slots = (size_t)(R > 0 ? R : 1) * n_max;
-    return al(256) + al(8 * (size_t)div_up(R > 0 ? R : 1, 256)) + 3 * al(4 * slots) + 2 * al(4 * slots * K) +
+    return al(256) + al(8 * (size_t)div_up(R > 0 ? R : 1, 256)) + al(16 * slots) + 2 * al(4 * slots * K) +
            al(4 * (size_t)(R > 0 ? R : 1)) +         // fallback list of the proposal-restricted search
            al(4 * (size_t)(R > 0 ? R : 1)) +         // rays handed to the warp-per-ray search
            al(8 * (size_t)(R > 0 ? R : 1));          // intervals the learned search inferred for them
@@ -510,9 +510,7 @@ static hp_status search_impl(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n
         size_t o = 0;
         a.ticket = reinterpret_cast<uint32_t *>(base + o);   o += al(256);
         a.flags = reinterpret_cast<uint64_t *>(base + o);    o += al(8 * (size_t)div_up(n_rays, 256));
-        a.slot_t = reinterpret_cast<float *>(base + o);      o += al(4 * slots);
-        a.slot_src = reinterpret_cast<int32_t *>(base + o);  o += al(4 * slots);
-        a.slot_delta = reinterpret_cast<float *>(base + o);  o += al(4 * slots);
+        a.slot_rec = reinterpret_cast<float4 *>(base + o);   o += al(16 * slots);
         a.slot_nbr = reinterpret_cast<int32_t *>(base + o);  o += al(4 * slots * K);
         a.slot_dist = reinterpret_cast<float *>(base + o);   o += al(4 * slots * K);
         a.fallback = reinterpret_cast<int32_t *>(base + o);  o += al(4 * (size_t)n_rays);

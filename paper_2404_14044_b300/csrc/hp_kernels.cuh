@@ -95,9 +95,7 @@ struct SearchArgs {
     int32_t *nbr;
     float *nbr_dist;
     int64_t capacity;
-    float *slot_t;           // [R * n_max] per-ray sample slots (scratch)
-    int32_t *slot_src;
-    float *slot_delta;
+    float4 *slot_rec;        // [R * n_max] per-ray sample slots (scratch): t, source id bits, delta
     int32_t *slot_nbr;       // [R * n_max * K]
     float *slot_dist;
     uint64_t *flags;         // [ceil(R / 256)] look-back words of the packing scan

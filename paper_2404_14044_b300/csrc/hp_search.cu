@@ -383,8 +383,8 @@ __device__ __forceinline__ void wide_ray(const SearchArgs &a, const float2 *inte
         }
         if ((sel >> lane) & 1u) {
             const int64_t slot = slot0 + ns0 + __popc(sel & lt_mask);
-            a.slot_t[slot] = tj;
-            a.slot_src[slot] = idj;
+            a.slot_rec[slot].x = tj;
+            a.slot_rec[slot].y = __int_as_float(idj);
 #pragma unroll
             for (int m = 0; m < KB; ++m) {
                 if (m < K) {
@@ -398,8 +398,8 @@ __device__ __forceinline__ void wide_ray(const SearchArgs &a, const float2 *inte
     __syncwarp();
     if (lane < ns) {
         const int64_t slot = slot0 + lane;
-        const float tm = a.slot_t[slot];
-        a.slot_delta[slot] = (lane + 1 < ns) ? a.slot_t[slot + 1] - tm : 2.0f * radius_at(a.mode, a.r, ray, tm);
+        const float tm = a.slot_rec[slot].x;
+        a.slot_rec[slot].z = (lane + 1 < ns) ? a.slot_rec[slot + 1].x - tm : 2.0f * radius_at(a.mode, a.r, ray, tm);
     }
     if (lane == 0) {
         a.n_s[ri] = ns;
@@ -647,9 +647,9 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
                 prim = (int)pixel_key(a.cam, a.h, make_float3(pj.x, pj.y, pj.z));
             }
             const int64_t slot = slot0 + ns;
-            a.slot_t[slot] = tj;
-            a.slot_src[slot] = id_last;
-            if (ns > 0) a.slot_delta[slot - 1] = tj - t_sel;
+            a.slot_rec[slot].x = tj;
+            a.slot_rec[slot].y = __int_as_float(id_last);
+            if (ns > 0) a.slot_rec[slot - 1].z = tj - t_sel;
             t_sel = tj;
 #pragma unroll
             for (int m = 0; m < KB; ++m) {
@@ -670,7 +670,7 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
             break;
         }
     }
-    if (ns > 0) a.slot_delta[slot0 + ns - 1] = 2.0f * radius_at(a.mode, a.r, ray, t_sel);
+    if (ns > 0) a.slot_rec[slot0 + ns - 1].z = 2.0f * radius_at(a.mode, a.r, ray, t_sel);
     a.n_s[ri] = ns;
     a.primary[ri] = prim;
     a.cand_count[ri] = total;
@@ -793,9 +793,10 @@ __global__ void __launch_bounds__(kPackRays) k_pack_samples(const SearchArgs a)
         const int v = s_slot[p];
         const int64_t r = ray0 + (v >> 4);
         const int64_t sl = r * a.n_max + (v & 15);
-        a.t[base + p] = a.slot_t[sl];
-        a.src[base + p] = a.slot_src[sl];
-        a.delta[base + p] = a.slot_delta[sl];
+        const float4 rec = a.slot_rec[sl];
+        a.t[base + p] = rec.x;
+        a.src[base + p] = __float_as_int(rec.y);
+        a.delta[base + p] = rec.z;
         a.ray[base + p] = (int)r;
     }
     // neighbour ids and distances: lane (sample sub, element e) per warp step
