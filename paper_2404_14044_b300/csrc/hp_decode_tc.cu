@@ -141,6 +141,25 @@ __device__ __forceinline__ void store_operand4(unsigned char *hi_base, unsigned 
     }
 }
 
+template <bool kBF16>
+__device__ __forceinline__ void store_operand4_ss(unsigned char *hi_base, unsigned char *lo_base, uint32_t off,
+                                                  float4 v)
+{
+    const float x[4] = {v.x, v.y, v.z, v.w};
+    if constexpr (kBF16) {
+        __nv_bfloat16 h[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) h[i] = __float2bfloat16_rn(x[i]);
+        *reinterpret_cast<uint2 *>(hi_base + off) = *reinterpret_cast<const uint2 *>(h);
+    } else {
+        __half h[4], l[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) tc::split_f16_same_scale(x[i], h[i], l[i]);
+        *reinterpret_cast<uint2 *>(hi_base + off) = *reinterpret_cast<const uint2 *>(h);
+        *reinterpret_cast<uint2 *>(lo_base + off) = *reinterpret_cast<const uint2 *>(l);
+    }
+}
+
 }  // namespace
 
 template <bool kBF16>
@@ -476,22 +495,28 @@ __global__ void __launch_bounds__(128, 1) k_mma_selftest(const uint16_t *A, cons
 }
 
 // ---------------------------------------------------------------------------
-// k_decode_ws: the same decode, warp-specialized.  16 consumer warps run the
-// layers of tile i (4 TMEM lane quarters x 4 column groups) while 8 producer
-// warps gather and blend tile i+1 into the second of two shared-memory buffers
-// of the first A operand.  Hidden activations never touch shared memory: the
-// epilogue writes them back into tensor memory (two 16-bit values per
+// k_decode_ws: the same decode, warp-specialized, one 1024-thread block per
+// SM.  16 producer warps gather and inverse-distance blend the samples of the
+// next tiles into two shared-memory buffers of the first A operand; 16
+// consumer warps in two groups of 8 (4 TMEM lane quarters x 2 column groups)
+// take alternate tiles (tile i in buffer i % 2), so one group's epilogues
+// overlap the other's MMAs.  Hidden activations never touch shared memory:
+// the epilogue writes them back into tensor memory (two 16-bit values per
 // column) and the next layer's tcgen05.mma reads its A operand from there.
-// Tensor memory: D1 [0,128), D2 [128,256), A_hi [256,320), A_lo [320,384).
-// Hand-offs: full[b] (producers -> consumers, 8 warp arrivals), empty[b]
+// FP32-accurate mode: A = A_hi + A_lo and B = B_hi + B_lo with lo the FP16
+// rounding of the remainder (unscaled), and A_hi B_hi + A_hi B_lo + A_lo B_hi
+// accumulate in one FP32 accumulator.  Tensor memory per group g:
+// D [256g, 256g+128), A_hi [256g+128, +64), A_lo [256g+192, +64).
+// Hand-offs: full[b] (producers -> consumers, one arrival per producer warp), empty[b]
 // (tcgen05.commit after the layer-0 MMAs that read buffer b), lbar[b] (bulk
 // copy of a tile's neighbour lists), mma (per layer).  Every wait is bounded.
-constexpr int kWsConsumerWarps = 16;      // 4 TMEM lane quarters x kWsGroups column groups
-constexpr int kWsProducerWarps = 8;
-constexpr int kWsGroups = kWsConsumerWarps / 4;
+constexpr int kWsConsumerWarps = 16;      // two groups, each 4 TMEM lane quarters x kWsGroups column groups
+constexpr int kWsProducerWarps = 16;
+constexpr int kWsGroupWarps = kWsConsumerWarps / 2;
+constexpr int kWsGroups = kWsGroupWarps / 4;
 constexpr int kWsBatch = 2;               // 8-column chunks a consumer thread reads from TMEM at once
 constexpr int kWsThreads = (kWsConsumerWarps + kWsProducerWarps) * 32;
-constexpr uint32_t kWsCols = 512, kColAH = 256, kColAL = 320;
+constexpr uint32_t kWsCols = 512, kColAH = 128, kColAL = 192;   // per consumer group, group g at 256 g
 
 struct WsLayout {
     int nh;
@@ -562,7 +587,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float *f32 = reinterpret_cast<float *>(smem + L.f32_block);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.bars);
-    uint64_t *full = bars, *empty = bars + 2, *lbar = bars + 4, *mbar = bars + 6;
+    uint64_t *full = bars, *empty = bars + 2, *lbar = bars + 4, *mbar = bars + 6;   // mbar: one per group
     uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + L.tslot);
     float *comb = reinterpret_cast<float *>(smem + L.comb);
 
@@ -581,7 +606,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
                         *reinterpret_cast<__nv_bfloat16 *>(smem + L.w_hi[l] + off) = __float2bfloat16_rn(w);
                     } else {
                         __half h, lo;
-                        tc::split_f16(w, h, lo);
+                        tc::split_f16_same_scale(w, h, lo);
                         *reinterpret_cast<__half *>(smem + L.w_hi[l] + off) = h;
                         *reinterpret_cast<__half *>(smem + L.w_lo[l] + off) = lo;
                     }
@@ -601,7 +626,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
         tc::mbar_init(&empty[1], 1);
         tc::mbar_init(&lbar[0], 1);
         tc::mbar_init(&lbar[1], 1);
-        tc::mbar_init(mbar, 1);
+        tc::mbar_init(&mbar[0], 1);
+        tc::mbar_init(&mbar[1], 1);
         tc::mbar_fence_init();
     }
     if (warp == 0) tc::tmem_alloc(tslot, kWsCols);
@@ -662,7 +688,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
                     s_ids[e] = in ? __ldg(a.nbr + g) : -1;
                     s_dst[e] = in ? __ldg(a.nbr_dist + g) : 1.0f;
                 }
-                ok = tc::bar_and(2, kWsProducerWarps * 32, ok);
+                ok = tc::bar_and(3, kWsProducerWarps * 32, ok);
             }
             // the buffer is free once the layer-0 MMAs of tile it-2 are done
             if (ok && !tc::mbar_wait(&empty[b], (eph >> b) & 1u, kMbarLimit)) {
@@ -670,7 +696,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
                 set_error(a.err, HP_ERR_TIMEOUT, -6);
             }
             eph ^= 1u << b;
-            ok = tc::bar_and(2, kWsProducerWarps * 32, ok);   // every producer leaves together
+            ok = tc::bar_and(3, kWsProducerWarps * 32, ok);   // every producer leaves together
             if (!ok) break;
             unsigned char *A_hi = smem + L.a0[b];
             unsigned char *A_lo = A_hi + L.a0_lo;
@@ -698,12 +724,12 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
                     const float inv = 1.0f / wsum;
                     acc.x *= inv; acc.y *= inv; acc.z *= inv; acc.w *= inv;
                 }
-                store_operand4<kBF16>(A_hi, A_lo, tc::kmajor_off(sl, 4 * chunk, F), acc);
+                store_operand4_ss<kBF16>(A_hi, A_lo, tc::kmajor_off(sl, 4 * chunk, F), acc);
             }
             tc::fence_async_smem();                  // generic stores -> tensor-core reads
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&full[b]);
-            ok = tc::bar_and(2, kWsProducerWarps * 32, ok);
+            ok = tc::bar_and(3, kWsProducerWarps * 32, ok);
             if (!ok) break;
         }
         // a list copy still in flight lands before exit
@@ -711,27 +737,32 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
             if (ptid == 0 && ((pend >> b) & 1u)) tc::mbar_wait(&lbar[b], (lph >> b) & 1u, kMbarLimit);
     } else {
         // =============================== consumers: MMA + epilogues
-        const int q = warp & 3, cg = warp >> 2;
+        const int grp = warp / kWsGroupWarps, wg = warp - grp * kWsGroupWarps;
+        const int gtid = tid - grp * kWsGroupWarps * 32;
+        const int barid = 1 + grp, nthr = kWsGroupWarps * 32;
+        const int q = wg & 3, cg = wg >> 2;
         const int row = 32 * q + lane;
         const uint32_t lane_off = (uint32_t)(32 * q) << 16;
-        const uint32_t d1 = tbase, d2 = tbase + 128, ah = tbase + kColAH, al = tbase + kColAL;
-        uint32_t fph = 0u, mph = 0u;             // parity bit per buffer
+        const uint32_t gbase = tbase + 256u * (uint32_t)grp;
+        const uint32_t d1 = gbase, ah = gbase + kColAH, al = gbase + kColAL;
+        uint64_t *gbar = &mbar[grp];
+        float *gcomb = comb + grp * (kWsGroups * kTcTile * 4);
+        uint32_t fph = 0u, mph = 0u;
         bool ok = true;
-        int it = 0;
-        for (int64_t base = (int64_t)blockIdx.x * kTcTile; base < S; base += stride, ++it) {
-            const int b = it & 1;
-            if (!tc::mbar_wait(&full[b], (fph >> b) & 1u, kMbarLimit)) {
+        const int b = grp;                       // this group's tiles all use A buffer grp
+        for (int64_t base = (int64_t)blockIdx.x * kTcTile + grp * stride; base < S; base += 2 * stride) {
+            if (!tc::mbar_wait(&full[b], fph, kMbarLimit)) {
                 ok = false;
                 set_error(a.err, HP_ERR_TIMEOUT, -7);
             }
-            fph ^= 1u << b;
-            ok = tc::bar_and(1, kWsConsumerWarps * 32, ok);
+            fph ^= 1u;
+            ok = tc::bar_and(barid, nthr, ok);
             if (!ok) break;
             tc::fence_after_sync();
             float o4[4] = {0.f, 0.f, 0.f, 0.f};
             for (int l = 0; l < L.nh; ++l) {
                 const int fi = L.fi[l], fo = L.fo[l];
-                if (tid == 0) {
+                if (gtid == 0) {
                     const uint32_t idesc = tc::idesc_f16(kTcTile, fo, kBF16);
                     const uint32_t wh = tc::smem_u32(smem + L.w_hi[l]), wl = tc::smem_u32(smem + L.w_lo[l]);
                     const uint32_t sbo = (uint32_t)fi * 16;
@@ -742,8 +773,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
                             const uint64_t dbh = tc::sdesc(wh + kk * 256, 128, sbo);
                             tc::mma_f16(d1, dah, dbh, idesc, kk > 0);
                             if constexpr (!kBF16) {
-                                tc::mma_f16(d2, dah, tc::sdesc(wl + kk * 256, 128, sbo), idesc, kk > 0);
-                                tc::mma_f16(d2, tc::sdesc(a0l + kk * 256, 128, sbo), dbh, idesc, 1);
+                                tc::mma_f16(d1, dah, tc::sdesc(wl + kk * 256, 128, sbo), idesc, 1);
+                                tc::mma_f16(d1, tc::sdesc(a0l + kk * 256, 128, sbo), dbh, idesc, 1);
                             }
                         }
                         tc::commit(&empty[b]);        // buffer b may be refilled once these are done
@@ -752,20 +783,20 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
                             const uint64_t dbh = tc::sdesc(wh + kk * 256, 128, sbo);
                             tc::mma_f16_ta(d1, ah + (uint32_t)(kk * 8), dbh, idesc, kk > 0);
                             if constexpr (!kBF16) {
-                                tc::mma_f16_ta(d2, ah + (uint32_t)(kk * 8), tc::sdesc(wl + kk * 256, 128, sbo), idesc,
-                                               kk > 0);
-                                tc::mma_f16_ta(d2, al + (uint32_t)(kk * 8), dbh, idesc, 1);
+                                tc::mma_f16_ta(d1, ah + (uint32_t)(kk * 8), tc::sdesc(wl + kk * 256, 128, sbo), idesc,
+                                               1);
+                                tc::mma_f16_ta(d1, al + (uint32_t)(kk * 8), dbh, idesc, 1);
                             }
                         }
                     }
-                    tc::commit(mbar);
+                    tc::commit(gbar);
                 }
-                if (!tc::mbar_wait(mbar, mph, kMbarLimit)) {
+                if (!tc::mbar_wait(gbar, mph, kMbarLimit)) {
                     ok = false;
                     set_error(a.err, HP_ERR_TIMEOUT, -8);
                 }
                 mph ^= 1u;
-                ok = tc::bar_and(1, kWsConsumerWarps * 32, ok);
+                ok = tc::bar_and(barid, nthr, ok);
                 if (!ok) break;
                 tc::fence_after_sync();
 
@@ -775,13 +806,12 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
                 const bool last = (l + 1 == L.nh);
                 const int nch = fo / 8;
                 for (int ch0 = cg; ch0 < nch; ch0 += kWsGroups * kWsBatch) {
-                    float v1[kWsBatch][8], v2[kWsBatch][8];
+                    float v1[kWsBatch][8];
 #pragma unroll
                     for (int j = 0; j < kWsBatch; ++j) {
                         const int ch = ch0 + kWsGroups * j;
                         if (ch < nch) {
                             tc::ld8(d1 + lane_off + (uint32_t)(8 * ch), v1[j]);
-                            if constexpr (!kBF16) tc::ld8(d2 + lane_off + (uint32_t)(8 * ch), v2[j]);
                         }
                     }
                     tc::wait_ld();
@@ -793,9 +823,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
                         float h[8];
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
-                            float x = v1[j][i];
-                            if constexpr (!kBF16) x = fmaf(v2[j][i], 1.0f / 2048.0f, x);
-                            h[i] = fmaxf(x + bias[c + i], 0.0f);
+                            h[i] = fmaxf(v1[j][i] + bias[c + i], 0.0f);
                         }
                         if (!last) {
                             // next layer's A: columns c/2 .. c/2+3 of A_hi (and A_lo)
@@ -809,8 +837,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
                                     pl[i] = 0u;
                                 } else {
                                     __half x0h, x0l, x1h, x1l;
-                                    tc::split_f16(h[2 * i], x0h, x0l);
-                                    tc::split_f16(h[2 * i + 1], x1h, x1l);
+                                    tc::split_f16_same_scale(h[2 * i], x0h, x0l);
+                                    tc::split_f16_same_scale(h[2 * i + 1], x1h, x1l);
                                     ph[i] = (uint32_t)__half_as_ushort(x0h) | ((uint32_t)__half_as_ushort(x1h) << 16);
                                     pl[i] = (uint32_t)__half_as_ushort(x0l) | ((uint32_t)__half_as_ushort(x1l) << 16);
                                 }
@@ -831,7 +859,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
                 }
                 if (!last) tc::wait_st();
                 tc::fence_before_sync();
-                tc::bar_and(1, kWsConsumerWarps * 32, true);
+                tc::bar_and(barid, nthr, true);
                 tc::fence_after_sync();
             }
             if (!ok) break;
@@ -839,9 +867,9 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
             // ---- output layer: combine the column groups, activations
             if (cg > 0) {
 #pragma unroll
-                for (int i = 0; i < 4; ++i) comb[(cg * kTcTile + row) * 4 + i] = o4[i];
+                for (int i = 0; i < 4; ++i) gcomb[(cg * kTcTile + row) * 4 + i] = o4[i];
             }
-            tc::bar_and(1, kWsConsumerWarps * 32, true);
+            tc::bar_and(barid, nthr, true);
             if (cg == 0) {
                 const float *bl = f32 + L.bias[a.n_layers - 1];
                 float o[4];
@@ -849,7 +877,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
                 for (int i = 0; i < 4; ++i) {
                     o[i] = o4[i];
 #pragma unroll
-                    for (int gr = 1; gr < kWsGroups; ++gr) o[i] += comb[(gr * kTcTile + row) * 4 + i];
+                    for (int gr = 1; gr < kWsGroups; ++gr) o[i] += gcomb[(gr * kTcTile + row) * 4 + i];
                     o[i] += bl[i];
                 }
                 const int64_t g = base + row;

@@ -567,43 +567,39 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
     }
     const int C = total;
 
-    // ---- adaptive primary surface sampling, candidates in (t, id) order
+    // ---- adaptive primary surface sampling, candidates in (t, id) order.
+    // Each pass over the column forms candidate j's neighbourhood and, in the
+    // same loop, finds candidate j+1: the smallest (t, id) above (t_j, id_j)
+    // (ids are looked up only for equal depths).
     const int K = a.K, n_max = a.n_max;
     float T = 1.0f, t_prev = 0.0f, t_sel = 0.0f;
     int jstar = -1, ns = 0, prim = -1;
     bool done = false;
-    float t_last = -1.0f;                      // the previous candidate's (t, id)
-    int id_last = -1;
     const int64_t slot0 = ri * n_max;
-    for (int j = 0; j < C; ++j) {
-        // next candidate: the smallest (t, id) above (t_last, id_last); ids
-        // are looked up only for equal depths
-        float tj = __int_as_float(0x7f800000);
-        uint32_t ij = 0;
-        int idj = -2;                          // -2: not looked up yet
-        for (int c = 0; c < C; ++c) {
-            const float tc = lt[c * 32];
-            if (tc < t_last || tc > tj) continue;
-            const uint32_t ic = li[c * 32];
-            if (tc == t_last || tc == tj) {
-                const int idc = point_id(a, ic);
-                if (tc == t_last && idc <= id_last) continue;
-                if (tc == tj) {
-                    if (idj == -2) idj = point_id(a, ij);
-                    if (idc >= idj) continue;
-                }
-                tj = tc;
-                ij = ic;
-                idj = idc;
-            } else {
-                tj = tc;
-                ij = ic;
-                idj = -2;
-            }
+    const float kInf = __int_as_float(0x7f800000);
+    // candidate 0: the smallest (t, id)
+    float tq = kInf;
+    uint32_t iq = 0;
+    int idq = -2;                              // -2: not looked up yet
+    for (int c = 0; c < C; ++c) {
+        const float tc = lt[c * 32];
+        if (tc > tq) continue;
+        const uint32_t ic = li[c * 32];
+        if (tc == tq) {
+            if (idq == -2) idq = point_id(a, iq);
+            const int idc = point_id(a, ic);
+            if (idc >= idq) continue;
+            idq = idc;
+        } else {
+            idq = -2;
         }
-        const float4 pj = __ldg(a.spts + ij);
-        t_last = tj;
-        id_last = __float_as_int(pj.w);
+        tq = tc;
+        iq = ic;
+    }
+    for (int j = 0; j < C; ++j) {
+        const float tj = tq;
+        const float4 pj = __ldg(a.spts + iq);
+        const int idj = __float_as_int(pj.w);
         if (jstar >= 0 && a.gap_k > 0.0f) {
             const float gap = dsub(tj, t_prev);
             if (!(gap <= dmul(a.gap_k, radius_at(a.mode, a.r, ray, t_prev)))) {
@@ -619,21 +615,46 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
         uint64_t keys[KB];
 #pragma unroll
         for (int m = 0; m < KB; ++m) keys[m] = ~0ull;
+        tq = kInf;
+        idq = -2;
         for (int c = 0; c < C; ++c) {
-            if (fabsf(lt[c * 32] - tj) > lim) continue;
-            const float4 Pi = __ldg(a.spts + li[c * 32]);
+            const float tc = lt[c * 32];
+            const uint32_t ic = li[c * 32];
+            // next candidate
+            if (tc >= tj && tc <= tq) {
+                bool take = true;
+                int idc = -2;
+                if (tc == tj || tc == tq) {
+                    idc = point_id(a, ic);
+                    if (tc == tj && idc <= idj) take = false;
+                    if (take && tc == tq) {
+                        if (idq == -2) idq = point_id(a, iq);
+                        if (idc >= idq) take = false;
+                    }
+                }
+                if (take) {
+                    tq = tc;
+                    iq = ic;
+                    idq = idc;
+                }
+            }
+            // neighbourhood of candidate j
+            if (fabsf(tc - tj) > lim) continue;
+            const float4 Pi = __ldg(a.spts + ic);
             const float ax = dfma(tj, ray.dx, -Pi.x);
             const float ay = dfma(tj, ray.dy, -Pi.y);
             const float az = dfma(tj, ray.dz, -Pi.z);
             const float d2 = dadd(dadd(dmul(ax, ax), dmul(ay, ay)), dmul(az, az));
             if (d2 <= rad2) knn_insert<KB>(keys, ((uint64_t)__float_as_uint(d2) << 32) | (uint32_t)__float_as_int(Pi.w));
         }
-        float s = 0.0f;
+        float s = 0.0f, dist[KB];
         int kp = 0;
 #pragma unroll
         for (int m = 0; m < KB; ++m) {
+            dist[m] = 0.0f;
             if (m < K && keys[m] != ~0ull) {
-                s = dadd(s, dsqrt(__uint_as_float((uint32_t)(keys[m] >> 32))));
+                dist[m] = dsqrt(__uint_as_float((uint32_t)(keys[m] >> 32)));
+                s = dadd(s, dist[m]);
                 ++kp;
             }
         }
@@ -648,7 +669,7 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
             }
             const int64_t slot = slot0 + ns;
             a.slot_rec[slot].x = tj;
-            a.slot_rec[slot].y = __int_as_float(id_last);
+            a.slot_rec[slot].y = __int_as_float(idj);
             if (ns > 0) a.slot_rec[slot - 1].z = tj - t_sel;
             t_sel = tj;
 #pragma unroll
@@ -656,7 +677,7 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
                 if (m < K) {
                     const bool ok = keys[m] != ~0ull;
                     a.slot_nbr[slot * K + m] = ok ? (int)(uint32_t)keys[m] : -1;
-                    a.slot_dist[slot * K + m] = ok ? dsqrt(__uint_as_float((uint32_t)(keys[m] >> 32))) : 0.0f;
+                    a.slot_dist[slot * K + m] = dist[m];
                 }
             }
             if (++ns == n_max) {

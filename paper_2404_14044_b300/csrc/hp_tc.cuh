@@ -210,6 +210,15 @@ __host__ __device__ __forceinline__ uint32_t kmajor_off(int row, int k, int Kt)
 // Yokota, "Recovering single precision accuracy from Tensor Cores while
 // surpassing the FP32 theoretical peak performance", 2022):
 // x ~= hi + lo * 2^-11, hi = fp16(x), lo = fp16((x - hi) * 2^11).
+// The same split with the second term unscaled, lo = fp16(x - hi), so that
+// A_hi B_hi + A_hi B_lo + A_lo B_hi can accumulate in one FP32 accumulator
+// (FP16 subnormals carry the small lo terms).
+__device__ __forceinline__ void split_f16_same_scale(float x, __half &hi, __half &lo)
+{
+    hi = __float2half_rn(x);
+    lo = __float2half_rn(x - __half2float(hi));
+}
+
 __device__ __forceinline__ void split_f16(float x, __half &hi, __half &lo)
 {
     hi = __float2half_rn(x);
