@@ -617,35 +617,58 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
         for (int m = 0; m < KB; ++m) keys[m] = ~0ull;
         tq = kInf;
         idq = -2;
-        for (int c = 0; c < C; ++c) {
-            const float tc = lt[c * 32];
-            const uint32_t ic = li[c * 32];
-            // next candidate
-            if (tc >= tj && tc <= tq) {
-                bool take = true;
-                int idc = -2;
-                if (tc == tj || tc == tq) {
-                    idc = point_id(a, ic);
-                    if (tc == tj && idc <= idj) take = false;
-                    if (take && tc == tq) {
-                        if (idq == -2) idq = point_id(a, iq);
-                        if (idc >= idq) take = false;
-                    }
-                }
-                if (take) {
-                    tq = tc;
-                    iq = ic;
-                    idq = idc;
+        // kNb column entries at a time: the positions of those within lim in
+        // depth are loaded together before any is used (their latencies overlap)
+        constexpr int kNb = 4;
+        for (int c0 = 0; c0 < C; c0 += kNb) {
+            float tcs[kNb];
+            uint32_t ics[kNb];
+            float4 P[kNb];
+#pragma unroll
+            for (int k = 0; k < kNb; ++k) {
+                tcs[k] = kInf;
+                ics[k] = 0;
+                if (c0 + k < C) {
+                    tcs[k] = lt[(c0 + k) * 32];
+                    ics[k] = li[(c0 + k) * 32];
                 }
             }
-            // neighbourhood of candidate j
-            if (fabsf(tc - tj) > lim) continue;
-            const float4 Pi = __ldg(a.spts + ic);
-            const float ax = dfma(tj, ray.dx, -Pi.x);
-            const float ay = dfma(tj, ray.dy, -Pi.y);
-            const float az = dfma(tj, ray.dz, -Pi.z);
-            const float d2 = dadd(dadd(dmul(ax, ax), dmul(ay, ay)), dmul(az, az));
-            if (d2 <= rad2) knn_insert<KB>(keys, ((uint64_t)__float_as_uint(d2) << 32) | (uint32_t)__float_as_int(Pi.w));
+#pragma unroll
+            for (int k = 0; k < kNb; ++k)
+                if (c0 + k < C && fabsf(tcs[k] - tj) <= lim) P[k] = __ldg(a.spts + ics[k]);
+#pragma unroll
+            for (int k = 0; k < kNb; ++k) {
+                if (c0 + k >= C) break;
+                const float tc = tcs[k];
+                const uint32_t ic = ics[k];
+                // next candidate
+                if (tc >= tj && tc <= tq) {
+                    bool take = true;
+                    int idc = -2;
+                    if (tc == tj || tc == tq) {
+                        idc = point_id(a, ic);
+                        if (tc == tj && idc <= idj) take = false;
+                        if (take && tc == tq) {
+                            if (idq == -2) idq = point_id(a, iq);
+                            if (idc >= idq) take = false;
+                        }
+                    }
+                    if (take) {
+                        tq = tc;
+                        iq = ic;
+                        idq = idc;
+                    }
+                }
+                // neighbourhood of candidate j
+                if (fabsf(tc - tj) > lim) continue;
+                const float4 Pi = P[k];
+                const float ax = dfma(tj, ray.dx, -Pi.x);
+                const float ay = dfma(tj, ray.dy, -Pi.y);
+                const float az = dfma(tj, ray.dz, -Pi.z);
+                const float d2 = dadd(dadd(dmul(ax, ax), dmul(ay, ay)), dmul(az, az));
+                if (d2 <= rad2)
+                    knn_insert<KB>(keys, ((uint64_t)__float_as_uint(d2) << 32) | (uint32_t)__float_as_int(Pi.w));
+            }
         }
         float s = 0.0f, dist[KB];
         int kp = 0;
