@@ -152,11 +152,11 @@ __device__ __forceinline__ void store_operand4_ss(unsigned char *hi_base, unsign
         for (int i = 0; i < 4; ++i) h[i] = __float2bfloat16_rn(x[i]);
         *reinterpret_cast<uint2 *>(hi_base + off) = *reinterpret_cast<const uint2 *>(h);
     } else {
-        __half h[4], l[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) tc::split_f16_same_scale(x[i], h[i], l[i]);
-        *reinterpret_cast<uint2 *>(hi_base + off) = *reinterpret_cast<const uint2 *>(h);
-        *reinterpret_cast<uint2 *>(lo_base + off) = *reinterpret_cast<const uint2 *>(l);
+        uint2 h, l;
+        tc::split_f16x2_same_scale(x[0], x[1], h.x, l.x);
+        tc::split_f16x2_same_scale(x[2], x[3], h.y, l.y);
+        *reinterpret_cast<uint2 *>(hi_base + off) = h;
+        *reinterpret_cast<uint2 *>(lo_base + off) = l;
     }
 }
 
@@ -820,10 +820,14 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
                         const int ch = ch0 + kWsGroups * j;
                         if (ch >= nch) break;
                         const int c = 8 * ch;
+                        // biases and output weights: 16-byte aligned rows (widths are multiples of 16)
+                        const float4 b0 = *reinterpret_cast<const float4 *>(bias + c);
+                        const float4 b1 = *reinterpret_cast<const float4 *>(bias + c + 4);
+                        const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
                         float h[8];
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
-                            h[i] = fmaxf(v1[j][i] + bias[c + i], 0.0f);
+                            h[i] = fmaxf(v1[j][i] + bb[i], 0.0f);
                         }
                         if (!last) {
                             // next layer's A: columns c/2 .. c/2+3 of A_hi (and A_lo)
@@ -831,16 +835,11 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
 #pragma unroll
                             for (int i = 0; i < 4; ++i) {
                                 if constexpr (kBF16) {
-                                    const uint32_t x0 = __bfloat16_as_ushort(__float2bfloat16_rn(h[2 * i]));
-                                    const uint32_t x1 = __bfloat16_as_ushort(__float2bfloat16_rn(h[2 * i + 1]));
-                                    ph[i] = x0 | (x1 << 16);
+                                    const __nv_bfloat162 x = __floats2bfloat162_rn(h[2 * i], h[2 * i + 1]);
+                                    ph[i] = *reinterpret_cast<const uint32_t *>(&x);
                                     pl[i] = 0u;
                                 } else {
-                                    __half x0h, x0l, x1h, x1l;
-                                    tc::split_f16_same_scale(h[2 * i], x0h, x0l);
-                                    tc::split_f16_same_scale(h[2 * i + 1], x1h, x1l);
-                                    ph[i] = (uint32_t)__half_as_ushort(x0h) | ((uint32_t)__half_as_ushort(x1h) << 16);
-                                    pl[i] = (uint32_t)__half_as_ushort(x0l) | ((uint32_t)__half_as_ushort(x1l) << 16);
+                                    tc::split_f16x2_same_scale(h[2 * i], h[2 * i + 1], ph[i], pl[i]);
                                 }
                             }
                             tc::st4(ah + lane_off + (uint32_t)(c / 2), ph);
@@ -848,11 +847,12 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
                         } else {
                             const float *W = f32 + L.wl;
 #pragma unroll
-                            for (int i = 0; i < 8; ++i) {
-                                o4[0] = fmaf(h[i], W[0 * fo + c + i], o4[0]);
-                                o4[1] = fmaf(h[i], W[1 * fo + c + i], o4[1]);
-                                o4[2] = fmaf(h[i], W[2 * fo + c + i], o4[2]);
-                                o4[3] = fmaf(h[i], W[3 * fo + c + i], o4[3]);
+                            for (int o = 0; o < 4; ++o) {
+                                const float4 w0 = *reinterpret_cast<const float4 *>(W + o * fo + c);
+                                const float4 w1 = *reinterpret_cast<const float4 *>(W + o * fo + c + 4);
+                                const float ww[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+                                for (int i = 0; i < 8; ++i) o4[o] = fmaf(h[i], ww[i], o4[o]);
                             }
                         }
                     }

@@ -219,6 +219,17 @@ __device__ __forceinline__ void split_f16_same_scale(float x, __half &hi, __half
     lo = __float2half_rn(x - __half2float(hi));
 }
 
+// The same split for two values at once, packed (x0 in the low half):
+// paired conversions, the same roundings as two split_f16_same_scale calls.
+__device__ __forceinline__ void split_f16x2_same_scale(float x0, float x1, uint32_t &hi, uint32_t &lo)
+{
+    const __half2 h = __floats2half2_rn(x0, x1);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
+}
+
 __device__ __forceinline__ void split_f16(float x, __half &hi, __half &lo)
 {
     hi = __float2half_rn(x);
