@@ -452,11 +452,15 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select_wide(const 
 // its own column of a [kLaneCap][32] shared-memory array (a few instructions
 // per point, so lanes that accept at different times cost the warp little),
 // then takes its candidates in (t, id) order, finding each next one with a
-// scan of the column -- the selection usually stops after a few.  A ray with
-// more accepted points than the column holds is listed for the warp-per-ray
-// search instead, as soon as the column overflows.
+// scan of the column -- the selection usually stops after a few.  A ray whose
+// window holds more than kLaneWalkMax points, or with more accepted points
+// than the column holds, is listed for the warp-per-ray search instead
+// (before walking, or as soon as the column overflows).
 constexpr int kLaneWarps = 4;
 constexpr int kLaneCap = 48;
+// most points a lane walks for one ray; windows holding more go to the
+// warp-per-ray search
+constexpr uint32_t kLaneWalkMax = 384;
 
 // resident blocks per SM for each K bucket (shared memory: 48 KB per block)
 __host__ __device__ constexpr int lane_blocks_per_sm(int KB) { return KB <= 8 ? 4 : KB <= 16 ? 4 : 3; }
@@ -513,6 +517,22 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
         full_window_empty = flen == 0;
     }
     const int span = 2 * hr + 1, off = a.h - hr;
+    const int64_t kb0 = (int64_t)(pv + off) * a.Wp + pu + off;
+
+    // a window holding many points (rays along a surface near a silhouette)
+    // would keep one lane walking while the rest of its warp idles: the
+    // warp-per-ray search, which walks 32 points at a time, takes the ray
+    {
+        uint32_t n_win = 0;
+        for (int q = 0; q < span; ++q) {
+            const int64_t kb = kb0 + (int64_t)q * a.Wp;
+            n_win += __ldg(a.start + kb + span) - __ldg(a.start + kb);
+        }
+        if (n_win > kLaneWalkMax) {
+            if (kLearned) a.interval_buf[ri] = iv;
+            return false;
+        }
+    }
 
     // ---- window walk: s runs, the next row's bounds loaded one row ahead,
     // kPtBatch points of a run loaded before any of them is used
@@ -520,7 +540,6 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
     int total = 0;
     float t_max = 0.0f;
     bool early_hit = false, late_hit = false;
-    const int64_t kb0 = (int64_t)(pv + off) * a.Wp + pu + off;
     uint32_t nlo = __ldg(a.start + kb0), nhi = __ldg(a.start + kb0 + span);
     for (int q = 0; q < span; ++q) {
         const uint32_t lo = nlo, hi = nhi;
@@ -782,7 +801,8 @@ __global__ void __launch_bounds__(kLaneWarps * 32, lane_blocks_per_sm(KB)) k_sea
             a.cand_count[ri] = 0;
             continue;
         }
-        // more candidates than this lane may answer for: the warp-per-ray search takes the ray
+        // a window too large for one lane, or more candidates than this lane
+        // may answer for: the warp-per-ray search takes the ray
         if (!lane_ray<KB, kLearned>(a, ri, pix, lt, li, pw)) a.wide[atomicAdd(a.wide_count, 1u)] = (int32_t)ri;
     }
 

@@ -147,6 +147,18 @@ def test_mlp_shapes():
         assert_parity(g, o, sc.params.K)
 
 
+@pytest.mark.parametrize("K", [8, 16])
+def test_wide_mlp_neighbour_counts(K):
+    # the widest supported MLP with 8 and 16 neighbours: the neighbour lists
+    # and the split weights together nearly fill the decode's shared memory
+    sc = _tiny(scenes.RADIUS_FIXED, res=32, n=8000, K=K, n_max=8)
+    sc.mlp_dims = [32, 128, 128, 128, 4]
+    sc.mlp_params = scenes.random_mlp(sc.mlp_dims, 6, sigma_bias=60.0)
+    g = gpu_render(sc)
+    o = oracle_render(sc)
+    assert_parity(g, o, sc.params.K)
+
+
 def test_feature_widths():
     sc = _tiny(scenes.RADIUS_FIXED, res=32, n=8000)
     for F in (4, 16, 64, 128):
