@@ -690,6 +690,14 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
                 }
                 ok = tc::bar_and(3, kWsProducerWarps * 32, ok);
             }
+            // BF16: the inverse-distance weights, each computed once, in place
+            // of the distances (read by other producers after the barrier
+            // below).  FP32 keeps the division in the gather loop: with the
+            // precomputed weights that variant spills at its 64 registers.
+            if constexpr (kBF16) {
+                for (int e = ptid; e < kTcTile * K; e += kWsProducerWarps * 32)
+                    s_dst[e] = s_ids[e] >= 0 ? 1.0f / fmaxf(s_dst[e], a.eps_d) : 0.0f;
+            }
             // the buffer is free once the layer-0 MMAs of tile it-2 are done
             if (ok && !tc::mbar_wait(&empty[b], (eph >> b) & 1u, kMbarLimit)) {
                 ok = false;
@@ -707,12 +715,12 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
                 if (g < S) {
                     float wsum = 0.0f;
                     const int *nb = s_ids + sl * K;
-                    const float *nd = s_dst + sl * K;
+                    const float *nw = s_dst + sl * K;
 #pragma unroll 8
                     for (int k = 0; k < K; ++k) {
                         const int id = nb[k];
                         if (id >= 0) {
-                            const float w = 1.0f / fmaxf(nd[k], a.eps_d);
+                            const float w = kBF16 ? nw[k] : 1.0f / fmaxf(nw[k], a.eps_d);
                             const float4 f = __ldg(feats4 + (int64_t)id * lpr + chunk);
                             acc.x = fmaf(w, f.x, acc.x);
                             acc.y = fmaf(w, f.y, acc.y);
