@@ -76,10 +76,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t *__restric
         int w = lane < kScanThreads / 32 ? s_warp[lane] : 0;
         int wi = warp_incl_scan(w);
         if (lane < kScanThreads / 32) s_warp[lane] = wi - w;      // exclusive warp offsets
-        if (lane == kScanThreads / 32 - 1) {
-            const int64_t agg = wi;
-            s_prefix = lookback_prefix(flags, tile, agg, err, spin_limit, tile != skip_tile);
-        }
+        const int64_t agg = __shfl_sync(0xffffffffu, wi, kScanThreads / 32 - 1);
+        const int64_t pre = lookback_prefix_warp(flags, tile, agg, err, spin_limit, tile != skip_tile);
+        if (lane == 0) s_prefix = pre;
     }
     __syncthreads();
     uint32_t run = (uint32_t)(s_prefix + s_warp[warp] + (incl - tsum));

@@ -161,34 +161,48 @@ __device__ __forceinline__ uint64_t ld_relaxed(const uint64_t *p)
     return v;
 }
 
-// Called by one thread of the tile; returns the exclusive prefix of the tile.
-__device__ __forceinline__ int64_t lookback_prefix(uint64_t *flags, int64_t tile, int64_t agg, ErrWord *err,
-                                                   uint32_t spin_limit, bool publish)
+// Decoupled look-back (flags: 2-bit state -- 0 nothing, 1 the tile's
+// aggregate, 2 its inclusive prefix -- over a 62-bit value), called by a
+// whole warp with the tile's aggregate agg: returns the tile's exclusive
+// prefix.  The warp inspects 32 predecessors per step, nearest in lane 0,
+// and stops at the nearest one that has published its inclusive prefix.
+__device__ __forceinline__ int64_t lookback_prefix_warp(uint64_t *flags, int64_t tile, int64_t agg, ErrWord *err,
+                                                        uint32_t spin_limit, bool publish)
 {
+    const int lane = threadIdx.x & 31;
     if (tile == 0) {
-        if (publish) st_relaxed(flags, kLbPre | (uint64_t)agg);
+        if (publish && lane == 0) st_relaxed(flags, kLbPre | (uint64_t)agg);
         return 0;
     }
-    if (publish) st_relaxed(flags + tile, kLbAgg | (uint64_t)agg);
+    if (publish && lane == 0) st_relaxed(flags + tile, kLbAgg | (uint64_t)agg);
     int64_t excl = 0;
-    int64_t j = tile - 1;
+    int64_t j0 = tile - 1;
     uint32_t spins = 0;
-    while (j >= 0) {
-        uint64_t v = ld_relaxed(flags + j);
-        uint64_t state = v >> 62;
-        if (state == 0) {
+    for (;;) {
+        const int64_t j = j0 - lane;
+        // before tile 0: an inclusive prefix of 0
+        const uint64_t v = j >= 0 ? ld_relaxed(flags + j) : kLbPre;
+        const uint64_t state = v >> 62;
+        const unsigned m2 = __ballot_sync(0xffffffffu, state == 2), m0 = __ballot_sync(0xffffffffu, state == 0);
+        const int first2 = m2 ? __ffs(m2) - 1 : 31;
+        const unsigned need = first2 == 31 ? 0xffffffffu : ((2u << first2) - 1u);   // lanes 0 .. first2
+        if (m0 & need) {
+            // a needed predecessor has published nothing yet
             if (++spins > spin_limit) {
-                set_error(err, HP_ERR_TIMEOUT, tile);
+                if (lane == 0) set_error(err, HP_ERR_TIMEOUT, tile);
                 break;
             }
             __nanosleep(64);
             continue;
         }
-        excl += (int64_t)(v & kLbVal);
-        if (state == 2) break;
-        --j;
+        int64_t x = lane <= first2 ? (int64_t)(v & kLbVal) : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        excl += x;
+        if (m2) break;
+        j0 -= 32;
     }
-    if (publish) st_relaxed(flags + tile, kLbPre | (uint64_t)(excl + agg));
+    if (publish && lane == 0) st_relaxed(flags + tile, kLbPre | (uint64_t)(excl + agg));
     return excl;
 }
 

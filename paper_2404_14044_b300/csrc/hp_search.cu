@@ -833,9 +833,11 @@ __global__ void __launch_bounds__(kPackRays) k_pack_samples(const SearchArgs a)
         const int w = lane < 8 ? s_warp[lane] : 0;
         const int wi = warp_incl_scan(w);
         if (lane < 8) s_warp[lane] = wi - w;
-        if (lane == 7) {
-            s_total = wi;
-            s_prefix = lookback_prefix(a.flags, tile, wi, a.err, a.spin_limit, true);
+        const int tot = __shfl_sync(kFull, wi, 7);
+        const int64_t pre = lookback_prefix_warp(a.flags, tile, tot, a.err, a.spin_limit, true);
+        if (lane == 0) {
+            s_total = tot;
+            s_prefix = pre;
         }
     }
     __syncthreads();
