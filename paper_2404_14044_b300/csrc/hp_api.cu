@@ -434,6 +434,7 @@ hp_status hp_build_table(hp_ctx *ctx, const float *d_points, int64_t n_points, c
     a.cnt = ctx->cnt; a.start = ctx->start; a.keyrank = ctx->keyrank; a.spts = ctx->spts;
     a.spts_tmp = ctx->spts_tmp;
     a.scan_flags = ctx->scan_flags; a.scan_ticket = ctx->scan_ticket; a.err = ctx->d_err;
+    a.zmin_enc = ctx->scan_ticket + 1;
     a.spin_limit = ctx->spin_limit; a.skip_tile = ctx->skip_tile;
     if (launch_build(a, static_cast<cudaStream_t>(stream), &ctx->prof) != cudaSuccess) {
         cudaGetLastError();
@@ -523,8 +524,9 @@ static hp_status search_impl(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n
         a.lane_units = a.ticket + 3;
         a.n_sm = ctx->num_sms;
         a.interval = reinterpret_cast<const float2 *>(d_interval);
-        if (d_interval || d_prop_w) {
-            // per-ray window bound of the restricted search (same terms as derive_window)
+        a.zmin_enc = ctx->scan_ticket + 1;
+        if (ctx->cfg.radius_mode == HP_RADIUS_FIXED) {
+            // window bound terms for a depth lower bound (same terms as derive_window)
             const double fx = ctx->cam.fx, fy = ctx->cam.fy, cx = ctx->cam.cx, cy = ctx->cam.cy;
             const double ax = std::fmax(std::fabs(0.5 - cx), std::fabs(((double)ctx->cam.width - 0.5) - cx)) / fx;
             const double ay = std::fmax(std::fabs(0.5 - cy), std::fabs(((double)ctx->cam.height - 0.5) - cy)) / fy;

@@ -18,17 +18,30 @@
 namespace hp {
 
 __global__ void __launch_bounds__(256) k_project_count(const float *__restrict__ pts, int64_t N, Cam cam, int h,
-                                                       uint32_t *__restrict__ cnt, uint2 *__restrict__ keyrank)
+                                                       uint32_t *__restrict__ cnt, uint2 *__restrict__ keyrank,
+                                                       uint32_t *__restrict__ zmin_enc)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const bool in = i < N;
     uint32_t key = kNoKey;
+    float X_z = 0.0f;
     if (in) {
         float3 X = cam_point(cam, __ldg(pts + 3 * i), __ldg(pts + 3 * i + 1), __ldg(pts + 3 * i + 2));
         key = pixel_key(cam, h, X);
+        X_z = X.z;
     }
     const bool valid = in && key != kNoKey;
+    // the smallest depth of a tabled point, encoded so that atomicMax takes
+    // it (a depth <= 0, possible only with z_near < 0, counts as 0)
+    __shared__ uint32_t s_ze;
+    if (threadIdx.x == 0) s_ze = 0u;
+    __syncthreads();
+    const uint32_t ze = __reduce_max_sync(
+        0xffffffffu, valid ? (X_z > 0.0f ? 0x7f800000u - (uint32_t)__float_as_int(X_z) : 0x7f800000u) : 0u);
+    if (lane == 0 && ze != 0u) atomicMax(&s_ze, ze);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_ze != 0u) atomicMax(zmin_enc, s_ze);   // one global atomic per block
     const unsigned active = __ballot_sync(0xffffffffu, valid);
     uint32_t rank = 0;
     if (valid) {
@@ -143,10 +156,11 @@ cudaError_t launch_build(const BuildArgs &a, cudaStream_t st, Prof *prof)
     const int64_t n_scan = a.P + 1;
     const int64_t scan_tiles = div_up(n_scan, kScanTile);
     if ((e = cudaMemsetAsync(a.scan_flags, 0, sizeof(uint64_t) * (size_t)scan_tiles, st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(a.scan_ticket, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+    // the scan's ticket and the depth minimum (scan_ticket[1] == zmin_enc)
+    if ((e = cudaMemsetAsync(a.scan_ticket, 0, 2 * sizeof(uint32_t), st)) != cudaSuccess) return e;
     if (a.N > 0) {
         prof_begin(prof, st, KID_PROJECT);
-        k_project_count<<<(unsigned)div_up(a.N, 256), 256, 0, st>>>(a.pts, a.N, a.cam, a.h, a.cnt, a.keyrank);
+        k_project_count<<<(unsigned)div_up(a.N, 256), 256, 0, st>>>(a.pts, a.N, a.cam, a.h, a.cnt, a.keyrank, a.zmin_enc);
         prof_end(prof, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

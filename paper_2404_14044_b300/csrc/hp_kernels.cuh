@@ -49,6 +49,7 @@ struct BuildArgs {
     float4 *spts_tmp;       // [N] scattered in atomic order, before the in-bucket sort
     uint64_t *scan_flags;   // [ceil((P+1)/kScanTile)]
     uint32_t *scan_ticket;
+    uint32_t *zmin_enc;     // smallest depth of a tabled point, 0x7f800000 - bits (0: none), by atomicMax
     ErrWord *err;
     uint32_t spin_limit;
     int32_t skip_tile;
@@ -72,7 +73,8 @@ struct SearchArgs {
     const float2 *interval;  // per-ray [t0, t1] (proposal-restricted search), NULL: plain
     const uint16_t *prop_w;  // proposal weights (BF16): the search infers each ray's interval itself
     float2 *interval_buf;    // ... and leaves it here for the rays it hands to the warp-per-ray search
-    float win_fx, cos_max, sin_max;  // per-ray window bound of the restricted search (fixed radius)
+    float win_fx, cos_max, sin_max;  // window bound terms for a depth lower bound (fixed radius)
+    const uint32_t *zmin_enc;        // smallest depth of a tabled point (as BuildArgs::zmin_enc)
     int32_t *fallback;       // rays whose restricted search kept nothing (original indices)
     uint32_t *fallback_count;
     int32_t *wide;           // rays with more candidates than a lane holds (original indices)

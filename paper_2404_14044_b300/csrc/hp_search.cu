@@ -69,6 +69,28 @@ __device__ __forceinline__ bool accept_point(const SearchArgs &a, const Ray &ray
     return rho2 <= dmul(rad, rad);
 }
 
+// Window half-width of the plain search.  An accepted point P lies within
+// r(t) of the ray point X nearest to it; along the segment X-P the depth
+// falls by at most r sin(theta_max) below P's own, so the projection offset
+// of every accepted point obeys the window bound of the table (h, derived
+// from t_near) and the same bound taken at the smallest depth of any tabled
+// point minus r sin(theta_max): the smaller window finds the same points.
+// Fixed radius only (the cone modes keep h).
+__device__ __forceinline__ int plain_window(const SearchArgs &a)
+{
+    int h = a.h;
+    if (a.mode == HP_RADIUS_FIXED && a.zmin_enc) {
+        const uint32_t e = __ldg(a.zmin_enc);
+        if (e != 0u) {
+            const float zmin = __int_as_float((int)(0x7f800000u - e));
+            const float zlo = fmaxf(dsub(zmin, dmul(a.r, a.sin_max)), a.cam.z_near);
+            const float lim = dadd(dmul(ddiv(a.win_fx, zlo), 1.001f), 1e-3f);
+            if (lim < (float)h) h = min(h, (int)floorf(dadd(lim, 0.5f)));
+        }
+    }
+    return h;
+}
+
 // Keep the cand_cap smallest (t, id) of the accepted points: lanes whose
 // point passed append it at a ballot prefix; once the buffer is full each
 // further point replaces the current largest key if it is smaller.
@@ -187,7 +209,7 @@ __device__ __forceinline__ void wide_ray(const SearchArgs &a, const float2 *inte
     // [t_near, t_far] and h; the proposal-restricted search the ray's
     // interval and the (smaller) window bound that follows from its t0
     float tn = a.cam.t_near, tf = a.cam.t_far;
-    int hr = a.h;
+    int hr = plain_window(a);
     if (interval) {
         const float2 iv = __ldg(interval + ri);
         tn = fmaxf(tn, iv.x);
@@ -197,7 +219,7 @@ __device__ __forceinline__ void wide_ray(const SearchArgs &a, const float2 *inte
             // single roundings so the CPU reference walks the same window)
             const float zlo = fmaxf(dsub(dmul(tn, a.cos_max), dmul(a.r, a.sin_max)), a.cam.z_near);
             const float lim = dadd(dmul(ddiv(a.win_fx, zlo), 1.001f), 1e-3f);
-            if (lim < (float)a.h) hr = min(a.h, (int)floorf(dadd(lim, 0.5f)));
+            if (lim < (float)a.h) hr = min(hr, (int)floorf(dadd(lim, 0.5f)));
         }
     }
     const int span = 2 * hr + 1, off = a.h - hr;
@@ -491,7 +513,7 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
     const bool restricted = kLearned || a.interval;
     float tn = a.cam.t_near, tf = a.cam.t_far;
     float2 iv = make_float2(tn, tf);
-    int hr = a.h;
+    int hr = plain_window(a);
     bool full_window_empty = false;
     if (restricted) {
         if constexpr (kLearned) {
@@ -506,7 +528,7 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
         if (a.mode == HP_RADIUS_FIXED) {
             const float zlo = fmaxf(dsub(dmul(tn, a.cos_max), dmul(a.r, a.sin_max)), a.cam.z_near);
             const float lim = dadd(dmul(ddiv(a.win_fx, zlo), 1.001f), 1e-3f);
-            if (lim < (float)a.h) hr = min(a.h, (int)floorf(dadd(lim, 0.5f)));
+            if (lim < (float)a.h) hr = min(hr, (int)floorf(dadd(lim, 0.5f)));
         }
         const int fspan = 2 * a.h + 1;
         uint32_t flen = 0;
