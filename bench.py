@@ -151,13 +151,12 @@ def algorithmic(kernel, N, Nv, P, R, S, K, F, dims, U, tensor_decode=True):
 # kernel is compiled from when it was captured; once those change the figure
 # no longer describes the kernel and the roofline reports traffic = null.
 NCU_TRAFFIC = {
-    "k_search_select": {"bytes": 54825472 + 57423104,
+    "k_search_select": {"bytes": 45042176 + 48034304,
                         "sources": ("hp_search.cu", "hp_common.cuh", "hp_kernels.cuh"),
-                        "sha256": "c459b2948fec7d07ac810568a8d5dab2f4ee29d8f549758865a01a0a46099967"},
-    "k_aggregate_decode": {"bytes": 78131712 + 1125120,
+                        "sha256": "b6c1486f165035ca491f2ac4dc927009f99853203eb237f34a42a365ba1ccebd"},
+    "k_aggregate_decode": {"bytes": 78086656 + 1655552,
                            "sources": ("hp_decode_tc.cu", "hp_tc.cuh", "hp_common.cuh", "hp_kernels.cuh"),
-                           "sha256": "881e39d5b0b910b61db659eb7cf5888c8065c276933fff53694f4004cf35651c"},
-
+                           "sha256": "2c2b3c9304b503765998bb2cd5c7df5c7cf712cc84371c43813f4d27ab037289"},
 }
 
 
