@@ -494,7 +494,9 @@ __device__ __forceinline__ int point_id(const SearchArgs &a, uint32_t idx) { ret
 // One ray on one lane; lt / li point at this lane's column (depth lt[c * 32],
 // table index li[c * 32]).  Returns false when the ray must go to the
 // warp-per-ray search.
-template <int KB, bool kLearned>
+// kMode: 0 plain search, 1 restricted to given intervals, 2 restricted to
+// intervals the proposal network infers here.
+template <int KB, int kMode>
 __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pix, float *lt, uint32_t *li,
                                          const float *prop_w)
 {
@@ -510,12 +512,13 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
     // depth range and window of this ray (plain: [t_near, t_far] and h;
     // restricted: the ray's interval -- given, or inferred here by the
     // proposal network -- and the window bound of its t0, D12)
-    const bool restricted = kLearned || a.interval;
+    constexpr bool kLearned = kMode == 2;
+    constexpr bool restricted = kMode != 0;
     float tn = a.cam.t_near, tf = a.cam.t_far;
     float2 iv = make_float2(tn, tf);
     int hr = plain_window(a);
     bool full_window_empty = false;
-    if (restricted) {
+    if constexpr (restricted) {
         if constexpr (kLearned) {
             float x[prop::kIn];
             prop::histogram(a.cam, a.start, a.spts, a.h, a.Wp, a.cam.height + 2 * a.h, pu, pv, x);
@@ -580,7 +583,7 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
                 if (i0 + k >= hi) break;
                 float t = 0.0f;
                 bool acc;
-                if (!restricted) {
+                if constexpr (!restricted) {
                     acc = accept_point(a, ray, pb[k], tn, tf, t);
                 } else {
                     const bool plain = accept_point(a, ray, pb[k], a.cam.t_near, a.cam.t_far, t);
@@ -773,9 +776,10 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
 
 // Warps pull work units from a grid-wide counter: an 8 x 4 pixel tile (whole
 // frames; ray i is pixel i) or 32 consecutive listed rays.
-template <int KB, bool kLearned>
+template <int KB, int kMode>
 __global__ void __launch_bounds__(kLaneWarps * 32, lane_blocks_per_sm(KB)) k_search_select(const SearchArgs a)
 {
+    constexpr bool kLearned = kMode == 2;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // this lane's candidate list: depth lt[c * 32] and table index li[c * 32]
@@ -825,7 +829,7 @@ __global__ void __launch_bounds__(kLaneWarps * 32, lane_blocks_per_sm(KB)) k_sea
         }
         // a window too large for one lane, or more candidates than this lane
         // may answer for: the warp-per-ray search takes the ray
-        if (!lane_ray<KB, kLearned>(a, ri, pix, lt, li, pw)) a.wide[atomicAdd(a.wide_count, 1u)] = (int32_t)ri;
+        if (!lane_ray<KB, kMode>(a, ri, pix, lt, li, pw)) a.wide[atomicAdd(a.wide_count, 1u)] = (int32_t)ri;
     }
 
 }
@@ -908,10 +912,12 @@ namespace {
 cudaError_t search_pass(const SearchArgs &a, cudaStream_t st, Prof *prof, int kid)
 {
     cudaError_t e;
-    auto lane_k = a.prop_w ? (a.K <= 4 ? k_search_select<4, true> : a.K <= 8 ? k_search_select<8, true>
-                              : a.K <= 16 ? k_search_select<16, true> : k_search_select<32, true>)
-                           : (a.K <= 4 ? k_search_select<4, false> : a.K <= 8 ? k_search_select<8, false>
-                              : a.K <= 16 ? k_search_select<16, false> : k_search_select<32, false>);
+    auto lane_k = a.prop_w ? (a.K <= 4 ? k_search_select<4, 2> : a.K <= 8 ? k_search_select<8, 2>
+                              : a.K <= 16 ? k_search_select<16, 2> : k_search_select<32, 2>)
+                  : a.interval ? (a.K <= 4 ? k_search_select<4, 1> : a.K <= 8 ? k_search_select<8, 1>
+                                  : a.K <= 16 ? k_search_select<16, 1> : k_search_select<32, 1>)
+                               : (a.K <= 4 ? k_search_select<4, 0> : a.K <= 8 ? k_search_select<8, 0>
+                                  : a.K <= 16 ? k_search_select<16, 0> : k_search_select<32, 0>);
     auto wide_k = a.K <= 4 ? k_search_select_wide<4> : a.K <= 8 ? k_search_select_wide<8>
                 : a.K <= 16 ? k_search_select_wide<16> : k_search_select_wide<32>;
     const size_t lsm = lane_smem_bytes() + (a.prop_w ? (size_t)(prop::kNP + 4) * 4 : 0), wsm = search_smem_bytes();
