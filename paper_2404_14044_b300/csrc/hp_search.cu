@@ -891,14 +891,45 @@ __global__ void __launch_bounds__(kPackRays) k_pack_samples(const SearchArgs a)
         a.delta[base + p] = rec.z;
         a.ray[base + p] = (int)r;
     }
-    // neighbour ids and distances: lane (sample sub, element e) per warp step
-    const int K = a.K, per = 32 / K, sub = lane / K, e = lane - sub * K;
-    if (sub < per) {
-        for (int64_t p = (int64_t)warp * per + sub; p < total; p += 8 * per) {
-            const int v = s_slot[p];
-            const int64_t sl = (ray0 + (v >> 4)) * a.n_max + (v & 15);
-            a.nbr[(base + p) * K + e] = a.slot_nbr[sl * K + e];
-            a.nbr_dist[(base + p) * K + e] = a.slot_dist[sl * K + e];
+    // neighbour ids and distances
+    const int K = a.K;
+    auto slot_of = [&](int64_t p) {
+        const int v = s_slot[p];
+        return (ray0 + (v >> 4)) * a.n_max + (v & 15);
+    };
+    const bool vec = (K & 3) == 0 && (((uintptr_t)a.nbr | (uintptr_t)a.nbr_dist) & 15) == 0;
+    if (vec) {
+        // 16-byte chunks: lane (sample sub, chunk e), two samples per lane in
+        // flight (the slots are spread over the tile's rays)
+        const int q = K >> 2, spi = 32 / q, sub = lane / q, e = lane - sub * q;
+        const int4 *sn = reinterpret_cast<const int4 *>(a.slot_nbr);
+        const float4 *sd = reinterpret_cast<const float4 *>(a.slot_dist);
+        int4 *on = reinterpret_cast<int4 *>(a.nbr);
+        float4 *od = reinterpret_cast<float4 *>(a.nbr_dist);
+        if (sub < spi) {
+            for (int64_t p = (int64_t)warp * spi + sub; p < total; p += 16 * spi) {
+                const int64_t p2 = p + 8 * spi;
+                const bool two = p2 < total;
+                const int64_t s0 = slot_of(p), s1 = two ? slot_of(p2) : s0;
+                const int4 n0 = __ldg(sn + s0 * q + e), n1 = __ldg(sn + s1 * q + e);
+                const float4 d0 = __ldg(sd + s0 * q + e), d1 = __ldg(sd + s1 * q + e);
+                on[(base + p) * q + e] = n0;
+                od[(base + p) * q + e] = d0;
+                if (two) {
+                    on[(base + p2) * q + e] = n1;
+                    od[(base + p2) * q + e] = d1;
+                }
+            }
+        }
+    } else {
+        // lane (sample sub, element e) per warp step
+        const int per = 32 / K, sub = lane / K, e = lane - sub * K;
+        if (sub < per) {
+            for (int64_t p = (int64_t)warp * per + sub; p < total; p += 8 * per) {
+                const int64_t sl = slot_of(p);
+                a.nbr[(base + p) * K + e] = a.slot_nbr[sl * K + e];
+                a.nbr_dist[(base + p) * K + e] = a.slot_dist[sl * K + e];
+            }
         }
     }
 }
