@@ -11,8 +11,9 @@
 //                     (camera x, y, z, id bits)
 // K4 k_bucket_sort    each run ordered by (z, x, y, id), which makes the list
 //                     independent of the atomics' order and of the input order:
-//                     one thread per point counts the points of its bucket that
-//                     precede it and writes it to that rank
+//                     one thread per bucket sorts a small bucket in registers;
+//                     k_bucket_sort_big ranks the points of larger buckets,
+//                     one warp per bucket
 #include "hp_kernels.cuh"
 
 namespace hp {
@@ -132,21 +133,83 @@ __device__ __forceinline__ bool pt_less(const float4 &a, const float4 &b)
     return __float_as_int(a.w) < __float_as_int(b.w);
 }
 
-// One thread per point: its rank among the points of its bucket under
-// (z, x, y, id) -- a strict total order, ids being distinct -- is its place.
-__global__ void __launch_bounds__(256) k_bucket_sort(const uint2 *__restrict__ keyrank, int64_t N,
-                                                     const uint32_t *__restrict__ start,
-                                                     const float4 *__restrict__ tmp, float4 *__restrict__ spts)
+// Buckets are ordered by (z, x, y, id) -- a strict total order, ids being
+// distinct.  One thread per bucket sorts a bucket of up to kSmallBucket points
+// in registers (consecutive threads read and write consecutive ranges); a
+// larger bucket goes on a list that one warp per bucket ranks: each point's
+// place is the number of the bucket's points before it.
+constexpr int kSmallBucket = 8;
+constexpr unsigned kBigSortBlocks = 296;   // warps loop over the large-bucket list
+
+__global__ void __launch_bounds__(256) k_bucket_sort(int64_t P, const uint32_t *__restrict__ start,
+                                                     const float4 *__restrict__ tmp, float4 *__restrict__ spts,
+                                                     uint32_t *__restrict__ big, uint32_t *__restrict__ n_big)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const uint2 kr = keyrank[i];
-    if (kr.x == kNoKey) return;
-    const uint32_t a = start[kr.x], b = start[kr.x + 1];
-    const float4 x = tmp[a + kr.y];
-    uint32_t rank = 0;
-    for (uint32_t j = a; j < b; ++j) rank += pt_less(__ldg(tmp + j), x) ? 1u : 0u;
-    spts[a + rank] = x;
+    const int64_t bkt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (bkt >= P) return;
+    const uint32_t a = __ldg(start + bkt), n = __ldg(start + bkt + 1) - a;
+    if (n == 0) return;
+    if (n > (uint32_t)kSmallBucket) {
+        big[atomicAdd(n_big, 1u)] = (uint32_t)bkt;
+        return;
+    }
+    float4 v[kSmallBucket];
+#pragma unroll
+    for (int i = 0; i < kSmallBucket; ++i)
+        if (i < (int)n) v[i] = __ldg(tmp + a + i);
+    // insertion sort with fixed register indices: v[i] sinks into the sorted prefix
+#pragma unroll
+    for (int i = 1; i < kSmallBucket; ++i) {
+        if (i < (int)n) {
+#pragma unroll
+            for (int j = i; j > 0; --j) {
+                if (pt_less(v[j], v[j - 1])) {
+                    const float4 t = v[j];
+                    v[j] = v[j - 1];
+                    v[j - 1] = t;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < kSmallBucket; ++i)
+        if (i < (int)n) spts[a + i] = v[i];
+}
+
+constexpr int kBigStage = 256;   // points of a large bucket staged in shared memory per warp
+
+__global__ void __launch_bounds__(256) k_bucket_sort_big(const uint32_t *__restrict__ start,
+                                                         const float4 *__restrict__ tmp, float4 *__restrict__ spts,
+                                                         const uint32_t *__restrict__ big,
+                                                         const uint32_t *__restrict__ n_big)
+{
+    __shared__ float4 s_pts[8][kBigStage];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float4 *sp = s_pts[warp];
+    const uint32_t nb = *n_big;
+    for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nb; w += (gridDim.x * blockDim.x) >> 5) {
+        const uint32_t bkt = big[w];
+        const uint32_t a = __ldg(start + bkt), b = __ldg(start + bkt + 1), n = b - a;
+        if (n <= (uint32_t)kBigStage) {
+            // the bucket in shared memory (coalesced), then ranks from broadcast reads
+            for (uint32_t p = lane; p < n; p += 32) sp[p] = __ldg(tmp + a + p);
+            __syncwarp();
+            for (uint32_t p = lane; p < n; p += 32) {
+                const float4 x = sp[p];
+                uint32_t rank = 0;
+                for (uint32_t j = 0; j < n; ++j) rank += pt_less(sp[j], x) ? 1u : 0u;
+                spts[a + rank] = x;
+            }
+            __syncwarp();
+        } else {
+            for (uint32_t p = a + lane; p < b; p += 32) {
+                const float4 x = __ldg(tmp + p);
+                uint32_t rank = 0;
+                for (uint32_t j = a; j < b; ++j) rank += pt_less(__ldg(tmp + j), x) ? 1u : 0u;
+                spts[a + rank] = x;
+            }
+        }
+    }
 }
 
 cudaError_t launch_build(const BuildArgs &a, cudaStream_t st, Prof *prof)
@@ -156,8 +219,9 @@ cudaError_t launch_build(const BuildArgs &a, cudaStream_t st, Prof *prof)
     const int64_t n_scan = a.P + 1;
     const int64_t scan_tiles = div_up(n_scan, kScanTile);
     if ((e = cudaMemsetAsync(a.scan_flags, 0, sizeof(uint64_t) * (size_t)scan_tiles, st)) != cudaSuccess) return e;
-    // the scan's ticket and the depth minimum (scan_ticket[1] == zmin_enc)
-    if ((e = cudaMemsetAsync(a.scan_ticket, 0, 2 * sizeof(uint32_t), st)) != cudaSuccess) return e;
+    // the scan's ticket, the depth minimum (scan_ticket[1] == zmin_enc) and
+    // the large-bucket count of the sort (scan_ticket[2])
+    if ((e = cudaMemsetAsync(a.scan_ticket, 0, 3 * sizeof(uint32_t), st)) != cudaSuccess) return e;
     if (a.N > 0) {
         prof_begin(prof, st, KID_PROJECT);
         k_project_count<<<(unsigned)div_up(a.N, 256), 256, 0, st>>>(a.pts, a.N, a.cam, a.h, a.cnt, a.keyrank, a.zmin_enc);
@@ -175,7 +239,11 @@ cudaError_t launch_build(const BuildArgs &a, cudaStream_t st, Prof *prof)
         prof_end(prof, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         prof_begin(prof, st, KID_SORT);
-        k_bucket_sort<<<(unsigned)div_up(a.N, 256), 256, 0, st>>>(a.keyrank, a.N, a.start, a.spts_tmp, a.spts);
+        // the counts are spent after the scan: cnt holds the large-bucket list
+        k_bucket_sort<<<(unsigned)div_up(a.P, 256), 256, 0, st>>>(a.P, a.start, a.spts_tmp, a.spts, a.cnt,
+                                                                  a.scan_ticket + 2);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_bucket_sort_big<<<kBigSortBlocks, 256, 0, st>>>(a.start, a.spts_tmp, a.spts, a.cnt, a.scan_ticket + 2);
         prof_end(prof, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
