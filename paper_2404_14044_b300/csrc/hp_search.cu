@@ -91,6 +91,26 @@ __device__ __forceinline__ int plain_window(const SearchArgs &a)
     return h;
 }
 
+__device__ __forceinline__ uint64_t warp_min_u64(uint64_t v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t u = __shfl_xor_sync(kFull, v, o);
+        v = u < v ? u : v;
+    }
+    return v;
+}
+
+__device__ __forceinline__ uint64_t warp_max_u64(uint64_t v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t u = __shfl_xor_sync(kFull, v, o);
+        v = u > v ? u : v;
+    }
+    return v;
+}
+
 // Keep the cand_cap smallest (t, id) of the accepted points: lanes whose
 // point passed append it at a ballot prefix; once the buffer is full each
 // further point replaces the current largest key if it is smaller.
@@ -287,142 +307,138 @@ __device__ __forceinline__ void wide_ray(const SearchArgs &a, const float2 *inte
     }
     __syncwarp();
 
-    // ---- sort the candidates by (t, id): rank sort, keys being unique
-    // (ids); lane l ranks candidates l, l+32, l+64, l+96 against all C
-    // (broadcast reads), then every candidate moves to its rank
+    // ---- adaptive primary surface sampling, candidates taken lazily in
+    // (t, id) order.  Lane l holds candidates l, l+32, l+64, l+96 in
+    // registers; the next candidate is a warp minimum of the keys above the
+    // last one, and candidate j's K nearest (d2, id) keys come out of its
+    // neighbourhood (candidates within lim in depth) by K warp minima, in
+    // ascending order -- so only the candidates the selection reaches are
+    // ever ordered.
+    static_assert(kCandCap <= 128, "4 candidates per lane");
     const int C = kept;
-    {
-        static_assert(kCandCap <= 128, "rank sort holds 4 candidates per lane");
-        uint64_t key[4];
-        int rank[4];
+    uint64_t ckey[4];
+    float4 cpos[4];
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const int e = lane + 32 * m;
-            key[m] = e < C ? ck[e] : ~0ull;
-            rank[m] = 0;
-        }
-        for (int c = 0; c < C; ++c) {
-            const uint64_t kc = ck[c];
-#pragma unroll
-            for (int m = 0; m < 4; ++m) rank[m] += kc < key[m] ? 1 : 0;
-        }
-        __syncwarp();
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const int e = lane + 32 * m;
-            if (e < C) {
-                ck[rank[m]] = key[m];
-                ci[rank[m]] = (uint8_t)e;
-            }
-        }
-        __syncwarp();
+    for (int m = 0; m < 4; ++m) {
+        const int e = lane + 32 * m;
+        ckey[m] = e < C ? ck[e] : ~0ull;
+        cpos[m] = e < C ? cp[e] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-
-    // ---- adaptive primary surface sampling.  Lanes own candidates: lane
-    // j walks all candidates (shared-memory broadcast) keeping the K nearest
-    // within r(t_j) in registers, and forms d_j and alpha_j.  The product
-    // w_j = alpha_j T_j is then taken in depth order across the warp.
-    float T = 1.0f, t_prev = 0.0f;
+    float T = 1.0f, t_prev = 0.0f, t_sel = 0.0f;
     int jstar = -1, ns = 0, prim = -1;
     const int64_t slot0 = ri * n_max;
     bool done = false;
     early_hit = __any_sync(kFull, early_hit);
     late_hit = __any_sync(kFull, late_hit);
-    for (int c0 = 0; c0 < C && !done; c0 += 32) {
-        const int j = c0 + lane;
-        float tj = 0.0f, alpha = 0.0f;
-        int idj = -1;
-        uint64_t keys[KB];
+    uint64_t prev = 0;
+    for (int j = 0; j < C; ++j) {
+        uint64_t lm = ~0ull;
 #pragma unroll
-        for (int m = 0; m < KB; ++m) keys[m] = ~0ull;
-        if (j < C) {
-            const uint64_t kj = ck[j];
-            tj = __uint_as_float((uint32_t)(kj >> 32));
-            idj = (int)(uint32_t)kj;
-            const float rad = radius_at(a.mode, a.r, ray, tj);
-            const float rad2 = dmul(rad, rad);
-            // Only candidates whose depth is within lim of t_j can lie within
-            // r(t_j) of x_j: |x_j - P_i| >= |t_j - t_i| up to float32 rounding
-            // (~1e-6 (1 + t)), far inside the margin, so the set is unchanged.
-            const float lim = rad * 1.001f + 1e-5f * (1.0f + tj);
-            int i0 = j;
-            while (i0 > 0 && tj - __uint_as_float((uint32_t)(ck[i0 - 1] >> 32)) <= lim) --i0;
-            for (int i = i0; i < C; ++i) {
-                const uint64_t ki = ck[i];
-                if (__uint_as_float((uint32_t)(ki >> 32)) - tj > lim) break;
-                const float4 Pi = cp[ci[i]];
-                const float ax = dfma(tj, ray.dx, -Pi.x);
-                const float ay = dfma(tj, ray.dy, -Pi.y);
-                const float az = dfma(tj, ray.dz, -Pi.z);
-                const float d2 = dadd(dadd(dmul(ax, ax), dmul(ay, ay)), dmul(az, az));
-                if (d2 <= rad2) knn_insert<KB>(keys, ((uint64_t)__float_as_uint(d2) << 32) | (uint32_t)ki);
-            }
-            float s = 0.0f;
-            int kp = 0;
-#pragma unroll
-            for (int m = 0; m < KB; ++m) {
-                if (m < K && keys[m] != ~0ull) {
-                    s = dadd(s, dsqrt(__uint_as_float((uint32_t)(keys[m] >> 32))));
-                    ++kp;
-                }
-            }
-            const float dj = ddiv(s, (float)kp);
-            alpha = dmul(a.gamma, exp32(-ddiv(dmul(dj, dj), a.beta2)));
-        }
-        const int nj = min(32, C - c0);
-        const int ns0 = ns;
-        unsigned sel = 0;
-        for (int jj = 0; jj < nj; ++jj) {
-            const float aj = __shfl_sync(kFull, alpha, jj);
-            const float tjj = __shfl_sync(kFull, tj, jj);
-            if (jstar >= 0 && a.gap_k > 0.0f) {
-                const float gap = dsub(tjj, t_prev);
-                if (!(gap <= dmul(a.gap_k, radius_at(a.mode, a.r, ray, t_prev)))) {
-                    done = true;
-                    break;
-                }
-            }
-            const float w = dmul(aj, T);
-            T = dmul(T, dsub(1.0f, aj));
-            if (w > a.eps_w) {
-                if (jstar < 0) {
-                    jstar = c0 + jj;
-                    const float4 pj = cp[ci[jstar]];
-                    prim = (int)pixel_key(a.cam, a.h, make_float3(pj.x, pj.y, pj.z));
-                }
-                sel |= 1u << jj;
-                if (++ns == n_max) {
-                    done = true;
-                    break;
-                }
-            }
-            t_prev = tjj;
-            // w_k <= gamma T_k <= gamma T for every later k: nothing more can pass
-            if (!(dmul(a.gamma, T) > a.eps_w)) {
+        for (int m = 0; m < 4; ++m)
+            if (ckey[m] != ~0ull && (j == 0 || ckey[m] > prev) && ckey[m] < lm) lm = ckey[m];
+        const uint64_t mk = warp_min_u64(lm);
+        prev = mk;
+        const float tj = __uint_as_float((uint32_t)(mk >> 32));
+        const int idj = (int)(uint32_t)mk;
+        if (jstar >= 0 && a.gap_k > 0.0f) {
+            const float gap = dsub(tj, t_prev);
+            if (!(gap <= dmul(a.gap_k, radius_at(a.mode, a.r, ray, t_prev)))) {
                 done = true;
                 break;
             }
         }
-        if ((sel >> lane) & 1u) {
-            const int64_t slot = slot0 + ns0 + __popc(sel & lt_mask);
-            a.slot_rec[slot].x = tj;
-            a.slot_rec[slot].y = __int_as_float(idj);
+        const float rad = radius_at(a.mode, a.r, ray, tj);
+        const float rad2 = dmul(rad, rad);
+        // |x_j - P_i| >= |t_j - t_i| up to float32 rounding (~1e-6 (1 + t)),
+        // far inside the margin, so only candidates within lim in depth qualify
+        const float lim = rad * 1.001f + 1e-5f * (1.0f + tj);
+        uint64_t nk[4];
 #pragma unroll
-            for (int m = 0; m < KB; ++m) {
-                if (m < K) {
-                    const bool ok = keys[m] != ~0ull;
-                    a.slot_nbr[slot * K + m] = ok ? (int)(uint32_t)keys[m] : -1;
-                    a.slot_dist[slot * K + m] = ok ? dsqrt(__uint_as_float((uint32_t)(keys[m] >> 32))) : 0.0f;
-                }
+        for (int m = 0; m < 4; ++m) {
+            nk[m] = ~0ull;
+            if (ckey[m] != ~0ull && !(fabsf(__uint_as_float((uint32_t)(ckey[m] >> 32)) - tj) > lim)) {
+                const float4 Pi = cpos[m];
+                const float ax = dfma(tj, ray.dx, -Pi.x);
+                const float ay = dfma(tj, ray.dy, -Pi.y);
+                const float az = dfma(tj, ray.dz, -Pi.z);
+                const float d2 = dadd(dadd(dmul(ax, ax), dmul(ay, ay)), dmul(az, az));
+                if (d2 <= rad2) nk[m] = ((uint64_t)__float_as_uint(d2) << 32) | (uint32_t)ckey[m];
             }
         }
+        // the K nearest, ascending: lane k keeps the k-th
+        uint64_t mine = ~0ull;
+        float s = 0.0f;
+        int kp = 0;
+        for (int k = 0; k < K; ++k) {
+            uint64_t l2 = nk[0];
+#pragma unroll
+            for (int m = 1; m < 4; ++m) l2 = nk[m] < l2 ? nk[m] : l2;
+            const uint64_t g = warp_min_u64(l2);
+            if (g == ~0ull) break;
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+                if (nk[m] == g) nk[m] = ~0ull;
+            if (lane == k) mine = g;
+            s = dadd(s, dsqrt(__uint_as_float((uint32_t)(g >> 32))));
+            ++kp;
+        }
+        const float dj = ddiv(s, (float)kp);
+        const float alpha = dmul(a.gamma, exp32(-ddiv(dmul(dj, dj), a.beta2)));
+        const float w = dmul(alpha, T);
+        T = dmul(T, dsub(1.0f, alpha));
+        if (w > a.eps_w) {
+            if (jstar < 0) {
+                jstar = j;
+                // the candidate's position, from the lane that holds it
+                int src = -1, sm = 0;
+#pragma unroll
+                for (int m = 0; m < 4; ++m)
+                    if (ckey[m] == mk) {
+                        src = lane;
+                        sm = m;
+                    }
+                const unsigned hold = __ballot_sync(kFull, src >= 0);
+                const int sl = __ffs(hold) - 1;
+                float4 pj = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int m = 0; m < 4; ++m)
+                    if (m == sm) pj = cpos[m];
+                pj.x = __shfl_sync(kFull, pj.x, sl);
+                pj.y = __shfl_sync(kFull, pj.y, sl);
+                pj.z = __shfl_sync(kFull, pj.z, sl);
+                prim = (int)pixel_key(a.cam, a.h, make_float3(pj.x, pj.y, pj.z));
+            }
+            const int64_t slot = slot0 + ns;
+            if (lane == 0) {
+                a.slot_rec[slot].x = tj;
+                a.slot_rec[slot].y = __int_as_float(idj);
+                if (ns > 0) a.slot_rec[slot - 1].z = tj - t_sel;
+            }
+            t_sel = tj;
+            if (lane < K) {
+                const bool ok = mine != ~0ull;
+                a.slot_nbr[slot * K + lane] = ok ? (int)(uint32_t)mine : -1;
+                a.slot_dist[slot * K + lane] = ok ? dsqrt(__uint_as_float((uint32_t)(mine >> 32))) : 0.0f;
+            }
+            if (++ns == n_max) {
+                done = true;
+                break;
+            }
+        }
+        t_prev = tj;
+        // w_k <= gamma T_k <= gamma T for every later k: nothing more can pass
+        if (!(dmul(a.gamma, T) > a.eps_w)) {
+            done = true;
+            break;
+        }
     }
-    __syncwarp();
-    if (lane < ns) {
-        const int64_t slot = slot0 + lane;
-        const float tm = a.slot_rec[slot].x;
-        a.slot_rec[slot].z = (lane + 1 < ns) ? a.slot_rec[slot + 1].x - tm : 2.0f * radius_at(a.mode, a.r, ray, tm);
-    }
+    // the largest kept candidate depth (for the fallback rule)
+    uint64_t lmax = 0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+        if (ckey[m] != ~0ull && ckey[m] > lmax) lmax = ckey[m];
+    const uint64_t kmax = warp_max_u64(lmax);
+    if (lane == 0 && ns > 0) a.slot_rec[slot0 + ns - 1].z = 2.0f * radius_at(a.mode, a.r, ray, t_sel);
     if (lane == 0) {
         a.n_s[ri] = ns;
         a.primary[ri] = prim;
@@ -436,7 +452,7 @@ __device__ __forceinline__ void wide_ray(const SearchArgs &a, const float2 *inte
         // before t1: the gap rule stops the plain selection before it
         bool late_ok = false;
         if (interval && jstar >= 0 && a.gap_k > 0.0f && C > 0) {
-            const float tl = __uint_as_float((uint32_t)(ck[C - 1] >> 32));
+            const float tl = __uint_as_float((uint32_t)(kmax >> 32));
             late_ok = dsub(tf, tl) > dmul(fmaxf(a.gap_k, 1.0f), radius_at(a.mode, a.r, ray, tl));
         }
         const bool miss = (ns == 0 && !full_window_empty) || early_hit || (!done && late_hit && !late_ok);
