@@ -40,7 +40,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 
 struct SearchSmem {
-    size_t cp, ck, ci, total;
+    size_t cp, ck, total;
 };
 
 __host__ __device__ inline SearchSmem search_layout()
@@ -49,7 +49,6 @@ __host__ __device__ inline SearchSmem search_layout()
     size_t o = 0;
     L.cp = o; o += sizeof(float4) * kCandCap * kSearchWarps;
     L.ck = o; o += sizeof(uint64_t) * kCandCap * kSearchWarps;
-    L.ci = o; o += (size_t)kCandCap * kSearchWarps;
     L.total = o;
     return L;
 }
@@ -197,11 +196,11 @@ __global__ void __launch_bounds__(256) k_ray_table(Cam cam, int mode, float rdd,
     tab[i] = make_float4(r.dx, r.dy, r.dz, r.c);
 }
 
-// One ray on one warp (the warp-per-ray search); cp / ck / ci: the warp's
+// One ray on one warp (the warp-per-ray search); cp / ck: the warp's
 // candidate buffers (kCandCap entries each).
 template <int KB>
 __device__ __forceinline__ void wide_ray(const SearchArgs &a, const float2 *interval, int64_t ri, float4 *cp,
-                                         uint64_t *ck, uint8_t *ci)
+                                         uint64_t *ck)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -469,7 +468,6 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select_wide(const 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float4 *cp = reinterpret_cast<float4 *>(smem + L.cp) + warp * kCandCap;
     uint64_t *ck = reinterpret_cast<uint64_t *>(smem + L.ck) + warp * kCandCap;
-    uint8_t *ci = reinterpret_cast<uint8_t *>(smem + L.ci) + warp * kCandCap;
     const int64_t R_eff = a.count_ptr ? (int64_t)*a.count_ptr : a.R;
 
     // every warp pulls the next listed ray from a grid-wide counter, so heavy
@@ -482,7 +480,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select_wide(const 
         if ((int64_t)rl >= R_eff) break;
         // ri: the ray's index in the outputs (listed passes: from the list)
         const int64_t ri = a.ray_map ? (int64_t)__ldg(a.ray_map + (int64_t)rl) : (int64_t)rl;
-        wide_ray<KB>(a, a.interval, ri, cp, ck, ci);
+        wide_ray<KB>(a, a.interval, ri, cp, ck);
     }
 }
 
