@@ -228,7 +228,8 @@ __device__ __forceinline__ void wide_ray(const SearchArgs &a, const float2 *inte
     // [t_near, t_far] and h; the proposal-restricted search the ray's
     // interval and the (smaller) window bound that follows from its t0
     float tn = a.cam.t_near, tf = a.cam.t_far;
-    int hr = plain_window(a);
+    const int hw = plain_window(a);           // the plain search's window
+    int hr = hw;
     if (interval) {
         const float2 iv = __ldg(interval + ri);
         tn = fmaxf(tn, iv.x);
@@ -454,7 +455,11 @@ __device__ __forceinline__ void wide_ray(const SearchArgs &a, const float2 *inte
             const float tl = __uint_as_float((uint32_t)(kmax >> 32));
             late_ok = dsub(tf, tl) > dmul(fmaxf(a.gap_k, 1.0f), radius_at(a.mode, a.r, ray, tl));
         }
-        const bool miss = (ns == 0 && !full_window_empty) || early_hit || (!done && late_hit && !late_ok);
+        // nothing the plain test accepts in the plain search's own window:
+        // the plain search would come back empty as well, so an empty result
+        // needs no second search
+        const bool plain_empty = total == 0 && !early_hit && !late_hit && hr == hw;
+        const bool miss = (ns == 0 && !full_window_empty && !plain_empty) || early_hit || (!done && late_hit && !late_ok);
         if (interval && a.fallback && miss) a.fallback[atomicAdd(a.fallback_count, 1u)] = (int32_t)ri;
     }
     __syncwarp();
@@ -530,7 +535,8 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
     constexpr bool restricted = kMode != 0;
     float tn = a.cam.t_near, tf = a.cam.t_far;
     float2 iv = make_float2(tn, tf);
-    int hr = plain_window(a);
+    const int hw = plain_window(a);           // the plain search's window
+    int hr = hw;
     bool full_window_empty = false;
     if constexpr (restricted) {
         if constexpr (kLearned) {
@@ -782,7 +788,11 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
         bool late_ok = false;
         if (jstar >= 0 && a.gap_k > 0.0f && total > 0)
             late_ok = dsub(tf, t_max) > dmul(fmaxf(a.gap_k, 1.0f), radius_at(a.mode, a.r, ray, t_max));
-        const bool miss = (ns == 0 && !full_window_empty) || early_hit || (!done && late_hit && !late_ok);
+        // nothing the plain test accepts in the plain search's own window:
+        // the plain search would come back empty as well, so an empty result
+        // needs no second search
+        const bool plain_empty = total == 0 && !early_hit && !late_hit && hr == hw;
+        const bool miss = (ns == 0 && !full_window_empty && !plain_empty) || early_hit || (!done && late_hit && !late_ok);
         if (miss) a.fallback[atomicAdd(a.fallback_count, 1u)] = (int32_t)ri;
     }
     return true;
