@@ -273,8 +273,9 @@ __device__ __forceinline__ void wide_ray(const SearchArgs &a, const float2 *inte
         const int incl = warp_incl_scan(len);
         const int tot = __shfl_sync(kFull, incl, 31);
         const int excl = incl - len;
-        for (int v0 = 0; v0 < tot; v0 += 32) {
-            const int v = v0 + lane;
+        // point v of the concatenated runs (v < tot); the load for the next
+        // 32 points is issued before the current ones are tested
+        auto fetch = [&](int v) {
             // row of v: the last row whose exclusive offset is <= v (binary search)
             int row = 0;
             for (int step = 16; step > 0; step >>= 1) {
@@ -284,11 +285,16 @@ __device__ __forceinline__ void wide_ray(const SearchArgs &a, const float2 *inte
             }
             const uint32_t rlo = __shfl_sync(kFull, lo, row);
             const int rex = __shfl_sync(kFull, excl, row);
+            return v < tot ? __ldg(a.spts + rlo + (uint32_t)(v - rex)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        };
+        float4 pn = tot > 0 ? fetch(lane) : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int v0 = 0; v0 < tot; v0 += 32) {
+            const int v = v0 + lane;
+            const float4 p = pn;
+            if (v0 + 32 < tot) pn = fetch(v0 + 32 + lane);
             bool acc = false;
             float t = 0.0f;
-            float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
             if (v < tot) {
-                p = __ldg(a.spts + rlo + (uint32_t)(v - rex));
                 if (!interval) {
                     acc = accept_point(a, ray, p, tn, tf, t);
                 } else {
@@ -324,6 +330,7 @@ __device__ __forceinline__ void wide_ray(const SearchArgs &a, const float2 *inte
         ckey[m] = e < C ? ck[e] : ~0ull;
         cpos[m] = e < C ? cp[e] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    __syncwarp();                              // the buffers are scratch from here on
     float T = 1.0f, t_prev = 0.0f, t_sel = 0.0f;
     int jstar = -1, ns = 0, prim = -1;
     const int64_t slot0 = ri * n_max;
@@ -365,23 +372,32 @@ __device__ __forceinline__ void wide_ray(const SearchArgs &a, const float2 *inte
                 if (d2 <= rad2) nk[m] = ((uint64_t)__float_as_uint(d2) << 32) | (uint32_t)ckey[m];
             }
         }
-        // the K nearest, ascending: lane k keeps the k-th
-        uint64_t mine = ~0ull;
-        float s = 0.0f;
-        int kp = 0;
-        for (int k = 0; k < K; ++k) {
-            uint64_t l2 = nk[0];
+        // the K nearest, ascending: the neighbourhood's keys are compacted
+        // into shared memory (the candidate buffers are free once in
+        // registers), each ranked against all of them, the first K placed by
+        // rank; lane k keeps the k-th
+        uint64_t *nb_keys = ck;                                   // up to kCandCap
+        uint64_t *nb_sorted = reinterpret_cast<uint64_t *>(cp);   // the first K by rank
+        int n_nb = 0;
 #pragma unroll
-            for (int m = 1; m < 4; ++m) l2 = nk[m] < l2 ? nk[m] : l2;
-            const uint64_t g = warp_min_u64(l2);
-            if (g == ~0ull) break;
-#pragma unroll
-            for (int m = 0; m < 4; ++m)
-                if (nk[m] == g) nk[m] = ~0ull;
-            if (lane == k) mine = g;
-            s = dadd(s, dsqrt(__uint_as_float((uint32_t)(g >> 32))));
-            ++kp;
+        for (int m = 0; m < 4; ++m) {
+            const unsigned bm = __ballot_sync(kFull, nk[m] != ~0ull);
+            if (nk[m] != ~0ull) nb_keys[n_nb + __popc(bm & lt_mask)] = nk[m];
+            n_nb += __popc(bm);
         }
+        __syncwarp();
+        for (int i = lane; i < n_nb; i += 32) {
+            const uint64_t x = nb_keys[i];
+            int rank = 0;
+            for (int jn = 0; jn < n_nb; ++jn) rank += nb_keys[jn] < x ? 1 : 0;
+            if (rank < K) nb_sorted[rank] = x;
+        }
+        __syncwarp();
+        const int kp = n_nb < K ? n_nb : K;
+        const uint64_t mine = lane < kp ? nb_sorted[lane] : ~0ull;
+        float s = 0.0f;
+        for (int k = 0; k < kp; ++k) s = dadd(s, dsqrt(__uint_as_float((uint32_t)(nb_sorted[k] >> 32))));
+        __syncwarp();                                             // buffers reused next candidate
         const float dj = ddiv(s, (float)kp);
         const float alpha = dmul(a.gamma, exp32(-ddiv(dmul(dj, dj), a.beta2)));
         const float w = dmul(alpha, T);
