@@ -875,15 +875,16 @@ __global__ void __launch_bounds__(kLaneWarps * 32, lane_blocks_per_sm(KB)) k_sea
 }
 
 // Packing (K6): exclusive scan of n_s with a decoupled look-back over
-// uniform tiles of 256 rays; the tile's samples form one contiguous packed
+// uniform tiles of kPackRays rays; the tile's samples form one contiguous packed
 // range, which the whole block copies with coalesced stores (each packed
 // sample's slot is looked up in a shared-memory map).
-constexpr int kPackRays = 256;
+constexpr int kPackRays = 1024;
+constexpr int kPackWarps = kPackRays / 32;
 
 __global__ void __launch_bounds__(kPackRays) k_pack_samples(const SearchArgs a)
 {
     __shared__ int64_t s_tile, s_prefix;
-    __shared__ int s_warp[8];
+    __shared__ int s_warp[kPackWarps];
     __shared__ int s_total;
     __shared__ uint16_t s_slot[kPackRays * kMaxSamples];   // packed sample -> (ray in tile) << 4 | m
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -896,10 +897,10 @@ __global__ void __launch_bounds__(kPackRays) k_pack_samples(const SearchArgs a)
     if (lane == 31) s_warp[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-        const int w = lane < 8 ? s_warp[lane] : 0;
+        const int w = lane < kPackWarps ? s_warp[lane] : 0;
         const int wi = warp_incl_scan(w);
-        if (lane < 8) s_warp[lane] = wi - w;
-        const int tot = __shfl_sync(kFull, wi, 7);
+        if (lane < kPackWarps) s_warp[lane] = wi - w;
+        const int tot = __shfl_sync(kFull, wi, kPackWarps - 1);
         const int64_t pre = lookback_prefix_warp(a.flags, tile, tot, a.err, a.spin_limit, true);
         if (lane == 0) {
             s_total = tot;
@@ -947,8 +948,8 @@ __global__ void __launch_bounds__(kPackRays) k_pack_samples(const SearchArgs a)
         int4 *on = reinterpret_cast<int4 *>(a.nbr);
         float4 *od = reinterpret_cast<float4 *>(a.nbr_dist);
         if (sub < spi) {
-            for (int64_t p = (int64_t)warp * spi + sub; p < total; p += 16 * spi) {
-                const int64_t p2 = p + 8 * spi;
+            for (int64_t p = (int64_t)warp * spi + sub; p < total; p += 2 * kPackWarps * spi) {
+                const int64_t p2 = p + kPackWarps * spi;
                 const bool two = p2 < total;
                 const int64_t s0 = slot_of(p), s1 = two ? slot_of(p2) : s0;
                 const int4 n0 = __ldg(sn + s0 * q + e), n1 = __ldg(sn + s1 * q + e);
@@ -965,7 +966,7 @@ __global__ void __launch_bounds__(kPackRays) k_pack_samples(const SearchArgs a)
         // lane (sample sub, element e) per warp step
         const int per = 32 / K, sub = lane / K, e = lane - sub * K;
         if (sub < per) {
-            for (int64_t p = (int64_t)warp * per + sub; p < total; p += 8 * per) {
+            for (int64_t p = (int64_t)warp * per + sub; p < total; p += kPackWarps * per) {
                 const int64_t sl = slot_of(p);
                 a.nbr[(base + p) * K + e] = a.slot_nbr[sl * K + e];
                 a.nbr_dist[(base + p) * K + e] = a.slot_dist[sl * K + e];
@@ -1036,7 +1037,7 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof)
         k_ray_table<<<(unsigned)div_up(npix, 256), 256, 0, st>>>(a.cam, a.mode, a.rdd, a.raytab);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    const int64_t tiles = div_up(a.R, 256);
+    const int64_t tiles = div_up(a.R, kPackRays);
     if ((e = cudaMemsetAsync(a.flags, 0, sizeof(uint64_t) * (size_t)tiles, st)) != cudaSuccess) return e;
     // pack ticket, fallback count, wide-ray count
     if ((e = cudaMemsetAsync(a.ticket, 0, 3 * sizeof(uint32_t), st)) != cudaSuccess) return e;
