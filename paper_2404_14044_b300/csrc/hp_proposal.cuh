@@ -66,7 +66,7 @@ __device__ __forceinline__ float2 interval(const float *w, const float (&x)[kIn]
     for (int b = 0; b < kIn; ++b) any += x[b];
     if (any == 0.0f) return make_float2(cam.t_near, cam.t_far);   // no point around the pixel
     const float4 *w4 = reinterpret_cast<const float4 *>(w);
-    float h1[kHid], h2[kHid];
+    float h1[kHid];
 #pragma unroll
     for (int o = 0; o < kHid; ++o) {
         float z = w[oB0 + o];
@@ -80,6 +80,9 @@ __device__ __forceinline__ float2 interval(const float *w, const float (&x)[kIn]
         }
         h1[o] = fmaxf(z, 0.0f);
     }
+    // second hidden layer and output layer together: each h2 value is used
+    // as soon as it is formed (no h2 array)
+    float o0 = w[oB2], o1 = w[oB2 + 1];
 #pragma unroll 4
     for (int o = 0; o < kHid; ++o) {
         float z = w[oB1 + o];
@@ -91,14 +94,9 @@ __device__ __forceinline__ float2 interval(const float *w, const float (&x)[kIn]
             z = fmaf(q.z, h1[i + 2], z);
             z = fmaf(q.w, h1[i + 3], z);
         }
-        h2[o] = fmaxf(z, 0.0f);
-    }
-    float o0 = w[oB2], o1 = w[oB2 + 1];
-#pragma unroll
-    for (int i = 0; i < kHid; i += 4) {
-        const float4 q0 = w4[(oW2 + i) / 4], q1 = w4[(oW2 + kHid + i) / 4];
-        o0 = fmaf(q0.x, h2[i], fmaf(q0.y, h2[i + 1], fmaf(q0.z, h2[i + 2], fmaf(q0.w, h2[i + 3], o0))));
-        o1 = fmaf(q1.x, h2[i], fmaf(q1.y, h2[i + 1], fmaf(q1.z, h2[i + 2], fmaf(q1.w, h2[i + 3], o1))));
+        const float h2 = fmaxf(z, 0.0f);
+        o0 = fmaf(w[oW2 + o], h2, o0);
+        o1 = fmaf(w[oW2 + kHid + o], h2, o1);
     }
     const float u0 = sigm(o0), u1 = sigm(o1);
     const float span = cam.t_far - cam.t_near;
