@@ -601,6 +601,11 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
     int total = 0;
     float t_max = 0.0f;
     bool early_hit = false, late_hit = false;
+    // the smallest appended depth and its entry (candidate 0 unless another
+    // entry has the same depth: then the ids decide, by a scan below)
+    float t_lo = __int_as_float(0x7f800000);
+    uint32_t i_lo = 0;
+    bool lo_tie = false;
     uint32_t nlo = __ldg(a.start + kb0), nhi = __ldg(a.start + kb0 + span);
     for (int q = 0; q < span; ++q) {
         const uint32_t lo = nlo, hi = nhi;
@@ -638,6 +643,11 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
                 li[total * 32] = i0 + k;
                 ++total;
                 t_max = fmaxf(t_max, t);
+                lo_tie = t == t_lo ? true : (t < t_lo ? false : lo_tie);
+                if (t < t_lo) {
+                    t_lo = t;
+                    i_lo = i0 + k;
+                }
             }
         }
     }
@@ -658,10 +668,11 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
     const int64_t slot0 = ri * n_max;
     const float kInf = __int_as_float(0x7f800000);
     // candidate 0: the smallest (t, id)
-    float tq = kInf;
-    uint32_t iq = 0;
+    float tq = t_lo;
+    uint32_t iq = i_lo;
     int idq = -2;                              // -2: not looked up yet
-    for (int c = 0; c < C; ++c) {
+    if (lo_tie) tq = kInf;
+    for (int c = 0; lo_tie && c < C; ++c) {
         const float tc = lt[c * 32];
         if (tc > tq) continue;
         const uint32_t ic = li[c * 32];
