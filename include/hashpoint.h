@@ -243,9 +243,11 @@ hp_status hp_proposal_train_step(hp_ctx *ctx, const int32_t *d_ray_pixels, int64
  * candidates, and in the fixed-radius mode the window shrinks to the bound
  * that t0 allows.  Rays that keep no sample are searched again without the
  * restriction (plain-search fallback) unless their whole plain window holds
- * no point, so a ray is empty only if the plain search finds nothing either;
- * also when the plain search accepts a point in front of t0, or behind t1
- * while the selection ran out of candidates (decision contract D12).
+ * no point, or the restricted walk covered the plain window and the plain
+ * radius test accepted none of its points, so a ray is empty only if the
+ * plain search finds nothing either; also when the plain search accepts a
+ * point in front of t0, or behind t1 while the selection ran out of
+ * candidates (decision contract D12).
  * Outputs as hp_search_sample; d_fallback_count (device, optional) receives
  * the number of rays searched again. */
 hp_status hp_search_sample_proposal(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n_rays, int32_t K,
