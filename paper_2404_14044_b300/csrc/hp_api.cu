@@ -157,7 +157,9 @@ size_t search_region_bytes(int64_t R, int n_max, int K)
     return al(256) + al(8 * (size_t)div_up(R > 0 ? R : 1, 256)) + al(16 * slots) + 2 * al(4 * slots * K) +
            al(4 * (size_t)(R > 0 ? R : 1)) +         // fallback list of the proposal-restricted search
            al(4 * (size_t)(R > 0 ? R : 1)) +         // rays handed to the warp-per-ray search
-           al(8 * (size_t)(R > 0 ? R : 1));          // intervals the learned search inferred for them
+           al(8 * (size_t)(R > 0 ? R : 1)) +         // intervals the learned search inferred for them
+           al(4 * (size_t)(R > 0 ? R : 1)) +         // point-major pass: candidates per pixel
+           al(8 * (size_t)kLaneCap * (size_t)(R > 0 ? R : 1));   // ... and the candidates
 }
 
 // decoded samples, then the backward's per-sample scratch
@@ -435,6 +437,7 @@ hp_status hp_build_table(hp_ctx *ctx, const float *d_points, int64_t n_points, c
     a.spts_tmp = ctx->spts_tmp;
     a.scan_flags = ctx->scan_flags; a.scan_ticket = ctx->scan_ticket; a.err = ctx->d_err;
     a.zmin_enc = ctx->scan_ticket + 1;
+    a.pcell = reinterpret_cast<uint32_t *>(ctx->keyrank);   // the keys are spent once the scatter has run
     a.spin_limit = ctx->spin_limit; a.skip_tile = ctx->skip_tile;
     if (launch_build(a, static_cast<cudaStream_t>(stream), &ctx->prof) != cudaSuccess) {
         cudaGetLastError();
@@ -517,7 +520,11 @@ static hp_status search_impl(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n
         a.fallback = reinterpret_cast<int32_t *>(base + o);  o += al(4 * (size_t)n_rays);
         a.fallback_count = a.ticket + 1;
         a.wide = reinterpret_cast<int32_t *>(base + o);      o += al(4 * (size_t)n_rays);
-        a.interval_buf = reinterpret_cast<float2 *>(base + o);
+        a.interval_buf = reinterpret_cast<float2 *>(base + o); o += al(8 * (size_t)n_rays);
+        a.pm_cnt = reinterpret_cast<uint32_t *>(base + o);    o += al(4 * (size_t)n_rays);
+        a.pm_slot = reinterpret_cast<uint2 *>(base + o);
+        a.pcell = reinterpret_cast<const uint32_t *>(ctx->keyrank);
+        a.n_points = ctx->N;
         a.prop_w = d_prop_w;
         a.wide_count = a.ticket + 2;
         a.pull = reinterpret_cast<unsigned long long *>(a.ticket + 4);

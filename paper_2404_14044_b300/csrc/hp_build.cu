@@ -143,7 +143,8 @@ constexpr unsigned kBigSortBlocks = 296;   // warps loop over the large-bucket l
 
 __global__ void __launch_bounds__(256) k_bucket_sort(int64_t P, const uint32_t *__restrict__ start,
                                                      const float4 *__restrict__ tmp, float4 *__restrict__ spts,
-                                                     uint32_t *__restrict__ big, uint32_t *__restrict__ n_big)
+                                                     uint32_t *__restrict__ pcell, uint32_t *__restrict__ big,
+                                                     uint32_t *__restrict__ n_big)
 {
     const int64_t bkt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (bkt >= P) return;
@@ -173,13 +174,17 @@ __global__ void __launch_bounds__(256) k_bucket_sort(int64_t P, const uint32_t *
     }
 #pragma unroll
     for (int i = 0; i < kSmallBucket; ++i)
-        if (i < (int)n) spts[a + i] = v[i];
+        if (i < (int)n) {
+            spts[a + i] = v[i];
+            pcell[a + i] = (uint32_t)bkt;
+        }
 }
 
 constexpr int kBigStage = 256;   // points of a large bucket staged in shared memory per warp
 
 __global__ void __launch_bounds__(256) k_bucket_sort_big(const uint32_t *__restrict__ start,
                                                          const float4 *__restrict__ tmp, float4 *__restrict__ spts,
+                                                         uint32_t *__restrict__ pcell,
                                                          const uint32_t *__restrict__ big,
                                                          const uint32_t *__restrict__ n_big)
 {
@@ -199,6 +204,7 @@ __global__ void __launch_bounds__(256) k_bucket_sort_big(const uint32_t *__restr
                 uint32_t rank = 0;
                 for (uint32_t j = 0; j < n; ++j) rank += pt_less(sp[j], x) ? 1u : 0u;
                 spts[a + rank] = x;
+                pcell[a + rank] = bkt;
             }
             __syncwarp();
         } else {
@@ -207,6 +213,7 @@ __global__ void __launch_bounds__(256) k_bucket_sort_big(const uint32_t *__restr
                 uint32_t rank = 0;
                 for (uint32_t j = a; j < b; ++j) rank += pt_less(__ldg(tmp + j), x) ? 1u : 0u;
                 spts[a + rank] = x;
+                pcell[a + rank] = bkt;
             }
         }
     }
@@ -240,10 +247,11 @@ cudaError_t launch_build(const BuildArgs &a, cudaStream_t st, Prof *prof)
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         prof_begin(prof, st, KID_SORT);
         // the counts are spent after the scan: cnt holds the large-bucket list
-        k_bucket_sort<<<(unsigned)div_up(a.P, 256), 256, 0, st>>>(a.P, a.start, a.spts_tmp, a.spts, a.cnt,
-                                                                  a.scan_ticket + 2);
+        k_bucket_sort<<<(unsigned)div_up(a.P, 256), 256, 0, st>>>(a.P, a.start, a.spts_tmp, a.spts, a.pcell,
+                                                                  a.cnt, a.scan_ticket + 2);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        k_bucket_sort_big<<<kBigSortBlocks, 256, 0, st>>>(a.start, a.spts_tmp, a.spts, a.cnt, a.scan_ticket + 2);
+        k_bucket_sort_big<<<kBigSortBlocks, 256, 0, st>>>(a.start, a.spts_tmp, a.spts, a.pcell, a.cnt,
+                                                          a.scan_ticket + 2);
         prof_end(prof, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

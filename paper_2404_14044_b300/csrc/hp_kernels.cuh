@@ -47,6 +47,7 @@ struct BuildArgs {
     uint2 *keyrank;         // [N]
     float4 *spts;           // [N]
     float4 *spts_tmp;       // [N] scattered in atomic order, before the in-bucket sort
+    uint32_t *pcell;        // [N] bucket of each sorted point (written by the sort)
     uint64_t *scan_flags;   // [ceil((P+1)/kScanTile)]
     uint32_t *scan_ticket;
     uint32_t *zmin_enc;     // smallest depth of a tabled point, 0x7f800000 - bits (0: none), by atomicMax
@@ -54,6 +55,10 @@ struct BuildArgs {
     uint32_t spin_limit;
     int32_t skip_tile;
 };
+
+// Candidates per ray held by the lane-per-ray search (its shared-memory
+// column) and by the point-major pass's per-ray slots.
+constexpr int kLaneCap = 48;
 
 struct SearchArgs {
     Cam cam;                 // raytab is (re)computed from cam when raytab_stale
@@ -75,6 +80,10 @@ struct SearchArgs {
     float2 *interval_buf;    // ... and leaves it here for the rays it hands to the warp-per-ray search
     float win_fx, cos_max, sin_max;  // window bound terms for a depth lower bound (fixed radius)
     const uint32_t *zmin_enc;        // smallest depth of a tabled point (as BuildArgs::zmin_enc)
+    const uint32_t *pcell;   // bucket of each sorted point (whole frames: point-major candidate pass)
+    int64_t n_points;        // points given to the table build (bound of the tabled ones)
+    uint32_t *pm_cnt;        // [W*H] candidates each pixel's ray received from the point-major pass
+    uint2 *pm_slot;          // [W*H x kLaneCap] (t bits, table index) of those candidates
     int32_t *fallback;       // rays whose restricted search kept nothing (original indices)
     uint32_t *fallback_count;
     int32_t *wide;           // rays with more candidates than a lane holds (original indices)

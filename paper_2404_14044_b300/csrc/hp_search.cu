@@ -110,6 +110,43 @@ __device__ __forceinline__ uint64_t warp_max_u64(uint64_t v)
     return v;
 }
 
+// Point-major candidate pass (whole frames, plain search): one thread per
+// tabled point tests it against the ray of every pixel whose window holds its
+// bucket -- the (point, ray) pairs the ray-major walk tests, each once -- and
+// appends the accepted ones, (t, table index), to that pixel's slots.  The
+// points are read once, coalesced; the appends are in any order, and the
+// selection takes candidates in (t, id) order whatever their order.
+__global__ void __launch_bounds__(256) k_search_splat(const SearchArgs a)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int Hp = a.cam.height + 2 * a.h;
+    const int64_t nv = (int64_t)__ldg(a.start + (int64_t)a.Wp * Hp);
+    if (i >= nv || i >= a.n_points) return;
+    const float4 p = __ldg(a.spts + i);
+    const uint32_t key = __ldg(a.pcell + i);
+    const int kv = (int)(key / (uint32_t)a.Wp), ku = (int)(key - (uint32_t)kv * (uint32_t)a.Wp);
+    // pixel (pu, pv) walks buckets pu + o .. pu + o + 2 hw (padded), o = h - hw
+    const int hw = plain_window(a), o = a.h - hw;
+    const int W = a.cam.width, H = a.cam.height;
+    const int pu0 = max(ku - o - 2 * hw, 0), pu1 = min(ku - o, W - 1);
+    const int pv0 = max(kv - o - 2 * hw, 0), pv1 = min(kv - o, H - 1);
+    for (int pv = pv0; pv <= pv1; ++pv) {
+        for (int pu = pu0; pu <= pu1; ++pu) {
+            const int64_t pix = (int64_t)pv * W + pu;
+            const float4 rt = __ldg(a.raytab + pix);
+            Ray ray;
+            ray.dx = rt.x;
+            ray.dy = rt.y;
+            ray.dz = rt.z;
+            ray.c = rt.w;
+            float t;
+            if (!accept_point(a, ray, p, a.cam.t_near, a.cam.t_far, t)) continue;
+            const uint32_t pos = atomicAdd(a.pm_cnt + pix, 1u);
+            if (pos < (uint32_t)kLaneCap) a.pm_slot[pix * kLaneCap + pos] = make_uint2(__float_as_uint(t), (uint32_t)i);
+        }
+    }
+}
+
 // Keep the cand_cap smallest (t, id) of the accepted points: lanes whose
 // point passed append it at a ballot prefix; once the buffer is full each
 // further point replaces the current largest key if it is smaller.
@@ -514,7 +551,6 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select_wide(const 
 // than the column holds, is listed for the warp-per-ray search instead
 // (before walking, or as soon as the column overflows).
 constexpr int kLaneWarps = 4;
-constexpr int kLaneCap = 48;
 // most points a lane walks for one ray; windows holding more go to the
 // warp-per-ray search
 constexpr uint32_t kLaneWalkMax = 384;
@@ -548,7 +584,8 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
     // restricted: the ray's interval -- given, or inferred here by the
     // proposal network -- and the window bound of its t0, D12)
     constexpr bool kLearned = kMode == 2;
-    constexpr bool restricted = kMode != 0;
+    constexpr bool restricted = kMode == 1 || kMode == 2;
+    constexpr bool kPointMajor = kMode == 3;   // candidates from the point-major pass
     float tn = a.cam.t_near, tf = a.cam.t_far;
     float2 iv = make_float2(tn, tf);
     const int hw = plain_window(a);           // the plain search's window
@@ -580,21 +617,6 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
     const int span = 2 * hr + 1, off = a.h - hr;
     const int64_t kb0 = (int64_t)(pv + off) * a.Wp + pu + off;
 
-    // a window holding many points (rays along a surface near a silhouette)
-    // would keep one lane walking while the rest of its warp idles: the
-    // warp-per-ray search, which walks 32 points at a time, takes the ray
-    {
-        uint32_t n_win = 0;
-        for (int q = 0; q < span; ++q) {
-            const int64_t kb = kb0 + (int64_t)q * a.Wp;
-            n_win += __ldg(a.start + kb + span) - __ldg(a.start + kb);
-        }
-        if (n_win > kLaneWalkMax) {
-            if (kLearned) a.interval_buf[ri] = iv;
-            return false;
-        }
-    }
-
     // ---- window walk: s runs, the next row's bounds loaded one row ahead,
     // kPtBatch points of a run loaded before any of them is used
     constexpr int kPtBatch = 8;
@@ -606,47 +628,93 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
     float t_lo = __int_as_float(0x7f800000);
     uint32_t i_lo = 0;
     bool lo_tie = false;
-    uint32_t nlo = __ldg(a.start + kb0), nhi = __ldg(a.start + kb0 + span);
-    for (int q = 0; q < span; ++q) {
-        const uint32_t lo = nlo, hi = nhi;
-        if (q + 1 < span) {
-            const int64_t kb = kb0 + (int64_t)(q + 1) * a.Wp;
-            nlo = __ldg(a.start + kb);
-            nhi = __ldg(a.start + kb + span);
-        }
-        for (uint32_t i0 = lo; i0 < hi; i0 += kPtBatch) {
-            float4 pb[kPtBatch];
+    if constexpr (kPointMajor) {
+        // the pass left this ray's accepted points (any order) in its slots
+        const uint32_t cnt = __ldg(a.pm_cnt + pix);
+        if (cnt > (uint32_t)kLaneCap) return false;   // more than the column holds
+        // 16-byte loads, kPtBatch of them in flight (a ray's slots are 16-byte aligned)
+        const uint4 *sl = reinterpret_cast<const uint4 *>(a.pm_slot + (int64_t)pix * kLaneCap);
+        for (uint32_t c0 = 0; c0 < cnt; c0 += 2 * kPtBatch) {
+            uint4 e[kPtBatch];
 #pragma unroll
             for (int k = 0; k < kPtBatch; ++k)
-                if (i0 + k < hi) pb[k] = __ldg(a.spts + i0 + k);
+                if (c0 + 2 * k < cnt) e[k] = __ldg(sl + (c0 >> 1) + k);
 #pragma unroll
-            for (int k = 0; k < kPtBatch; ++k) {
-                if (i0 + k >= hi) break;
-                float t = 0.0f;
-                bool acc;
-                if constexpr (!restricted) {
-                    acc = accept_point(a, ray, pb[k], tn, tf, t);
-                } else {
-                    const bool plain = accept_point(a, ray, pb[k], a.cam.t_near, a.cam.t_far, t);
-                    acc = plain && t >= tn && t <= tf;
-                    early_hit |= plain && t < tn;
-                    late_hit |= plain && t > tf;
-                }
-                if (!acc) continue;
-                // more accepted points than the column holds: the warp-per-ray
-                // search takes the ray, so stop walking
-                if (total == kLaneCap) {
-                    if (kLearned) a.interval_buf[ri] = iv;
-                    return false;
-                }
-                lt[total * 32] = t;
-                li[total * 32] = i0 + k;
-                ++total;
+            for (int k = 0; k < 2 * kPtBatch; ++k) {
+                const uint32_t c = c0 + k;
+                if (c >= cnt) break;
+                const uint32_t tb = (k & 1) ? e[k >> 1].z : e[k >> 1].x;
+                const uint32_t ix = (k & 1) ? e[k >> 1].w : e[k >> 1].y;
+                const float t = __uint_as_float(tb);
+                lt[c * 32] = t;
+                li[c * 32] = ix;
                 t_max = fmaxf(t_max, t);
                 lo_tie = t == t_lo ? true : (t < t_lo ? false : lo_tie);
                 if (t < t_lo) {
                     t_lo = t;
-                    i_lo = i0 + k;
+                    i_lo = ix;
+                }
+            }
+        }
+        total = (int)cnt;
+    } else {
+        // a window holding many points (rays along a surface near a silhouette)
+        // would keep one lane walking while the rest of its warp idles: the
+        // warp-per-ray search, which walks 32 points at a time, takes the ray
+        {
+            uint32_t n_win = 0;
+            for (int q = 0; q < span; ++q) {
+                const int64_t kb = kb0 + (int64_t)q * a.Wp;
+                n_win += __ldg(a.start + kb + span) - __ldg(a.start + kb);
+            }
+            if (n_win > kLaneWalkMax) {
+                if (kLearned) a.interval_buf[ri] = iv;
+                return false;
+            }
+        }
+
+        uint32_t nlo = __ldg(a.start + kb0), nhi = __ldg(a.start + kb0 + span);
+        for (int q = 0; q < span; ++q) {
+            const uint32_t lo = nlo, hi = nhi;
+            if (q + 1 < span) {
+                const int64_t kb = kb0 + (int64_t)(q + 1) * a.Wp;
+                nlo = __ldg(a.start + kb);
+                nhi = __ldg(a.start + kb + span);
+            }
+            for (uint32_t i0 = lo; i0 < hi; i0 += kPtBatch) {
+                float4 pb[kPtBatch];
+#pragma unroll
+                for (int k = 0; k < kPtBatch; ++k)
+                    if (i0 + k < hi) pb[k] = __ldg(a.spts + i0 + k);
+#pragma unroll
+                for (int k = 0; k < kPtBatch; ++k) {
+                    if (i0 + k >= hi) break;
+                    float t = 0.0f;
+                    bool acc;
+                    if constexpr (!restricted) {
+                        acc = accept_point(a, ray, pb[k], tn, tf, t);
+                    } else {
+                        const bool plain = accept_point(a, ray, pb[k], a.cam.t_near, a.cam.t_far, t);
+                        acc = plain && t >= tn && t <= tf;
+                        early_hit |= plain && t < tn;
+                        late_hit |= plain && t > tf;
+                    }
+                    if (!acc) continue;
+                    // more accepted points than the column holds: the warp-per-ray
+                    // search takes the ray, so stop walking
+                    if (total == kLaneCap) {
+                        if (kLearned) a.interval_buf[ri] = iv;
+                        return false;
+                    }
+                    lt[total * 32] = t;
+                    li[total * 32] = i0 + k;
+                    ++total;
+                    t_max = fmaxf(t_max, t);
+                    lo_tie = t == t_lo ? true : (t < t_lo ? false : lo_tie);
+                    if (t < t_lo) {
+                        t_lo = t;
+                        i_lo = i0 + k;
+                    }
                 }
             }
         }
@@ -995,10 +1063,15 @@ namespace {
 cudaError_t search_pass(const SearchArgs &a, cudaStream_t st, Prof *prof, int kid)
 {
     cudaError_t e;
+    // whole frames, plain search: the point-major pass finds the candidates
+    const bool point_major = !a.prop_w && !a.interval && !a.rays && !a.ray_map && a.pm_slot && a.pcell &&
+                             a.R == (int64_t)a.cam.width * a.cam.height;
     auto lane_k = a.prop_w ? (a.K <= 4 ? k_search_select<4, 2> : a.K <= 8 ? k_search_select<8, 2>
                               : a.K <= 16 ? k_search_select<16, 2> : k_search_select<32, 2>)
                   : a.interval ? (a.K <= 4 ? k_search_select<4, 1> : a.K <= 8 ? k_search_select<8, 1>
                                   : a.K <= 16 ? k_search_select<16, 1> : k_search_select<32, 1>)
+                  : point_major ? (a.K <= 4 ? k_search_select<4, 3> : a.K <= 8 ? k_search_select<8, 3>
+                                   : a.K <= 16 ? k_search_select<16, 3> : k_search_select<32, 3>)
                                : (a.K <= 4 ? k_search_select<4, 0> : a.K <= 8 ? k_search_select<8, 0>
                                   : a.K <= 16 ? k_search_select<16, 0> : k_search_select<32, 0>);
     auto wide_k = a.K <= 4 ? k_search_select_wide<4> : a.K <= 8 ? k_search_select_wide<8>
@@ -1019,7 +1092,13 @@ cudaError_t search_pass(const SearchArgs &a, cudaStream_t st, Prof *prof, int ki
     // persistent warps: as many blocks as stay resident, fewer for small work
     const int KB = a.K <= 4 ? 4 : a.K <= 8 ? 8 : a.K <= 16 ? 16 : 32;
     const int64_t blocks = std::min<int64_t>(div_up(units, kLaneWarps), (int64_t)a.n_sm * lane_blocks_per_sm(KB));
+    if (point_major) {
+        const int64_t npix = (int64_t)a.cam.width * a.cam.height;
+        if ((e = cudaMemsetAsync(a.pm_cnt, 0, sizeof(uint32_t) * (size_t)npix, st)) != cudaSuccess) return e;
+    }
     prof_begin(prof, st, kid);
+    if (point_major && a.n_points > 0)
+        k_search_splat<<<(unsigned)div_up(a.n_points, 256), 256, 0, st>>>(a);
     lane_k<<<(unsigned)blocks, kLaneWarps * 32, lsm, st>>>(a);
     prof_end(prof, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
