@@ -850,16 +850,31 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
                 prim = (int)pixel_key(a.cam, a.h, make_float3(pj.x, pj.y, pj.z));
             }
             const int64_t slot = slot0 + ns;
-            a.slot_rec[slot].x = tj;
-            a.slot_rec[slot].y = __int_as_float(idj);
+            *reinterpret_cast<float2 *>(&a.slot_rec[slot]) = make_float2(tj, __int_as_float(idj));
             if (ns > 0) a.slot_rec[slot - 1].z = tj - t_sel;
             t_sel = tj;
+            if ((K & 3) == 0) {
+                // 16-byte stores (a slot's K entries start 16-byte aligned)
+                int4 *sn = reinterpret_cast<int4 *>(a.slot_nbr + slot * K);
+                float4 *sd = reinterpret_cast<float4 *>(a.slot_dist + slot * K);
 #pragma unroll
-            for (int m = 0; m < KB; ++m) {
-                if (m < K) {
-                    const bool ok = keys[m] != ~0ull;
-                    a.slot_nbr[slot * K + m] = ok ? (int)(uint32_t)keys[m] : -1;
-                    a.slot_dist[slot * K + m] = dist[m];
+                for (int m = 0; m < KB; m += 4) {
+                    if (m < K) {
+                        int v[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) v[q] = keys[m + q] != ~0ull ? (int)(uint32_t)keys[m + q] : -1;
+                        sn[m >> 2] = make_int4(v[0], v[1], v[2], v[3]);
+                        sd[m >> 2] = make_float4(dist[m], dist[m + 1], dist[m + 2], dist[m + 3]);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < KB; ++m) {
+                    if (m < K) {
+                        const bool ok = keys[m] != ~0ull;
+                        a.slot_nbr[slot * K + m] = ok ? (int)(uint32_t)keys[m] : -1;
+                        a.slot_dist[slot * K + m] = dist[m];
+                    }
                 }
             }
             if (++ns == n_max) {
