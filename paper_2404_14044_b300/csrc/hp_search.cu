@@ -731,6 +731,7 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
     // (ids are looked up only for equal depths).
     const int K = a.K, n_max = a.n_max;
     float T = 1.0f, t_prev = 0.0f, t_sel = 0.0f;
+    int id_sel = 0;
     int jstar = -1, ns = 0, prim = -1;
     bool done = false;
     const int64_t slot0 = ri * n_max;
@@ -850,9 +851,10 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
                 prim = (int)pixel_key(a.cam, a.h, make_float3(pj.x, pj.y, pj.z));
             }
             const int64_t slot = slot0 + ns;
-            *reinterpret_cast<float2 *>(&a.slot_rec[slot]) = make_float2(tj, __int_as_float(idj));
-            if (ns > 0) a.slot_rec[slot - 1].z = tj - t_sel;
+            // a record is written whole once its delta is known (next sample or the end)
+            if (ns > 0) a.slot_rec[slot - 1] = make_float4(t_sel, __int_as_float(id_sel), tj - t_sel, 0.0f);
             t_sel = tj;
+            id_sel = idj;
             if ((K & 3) == 0) {
                 // 16-byte stores (a slot's K entries start 16-byte aligned)
                 int4 *sn = reinterpret_cast<int4 *>(a.slot_nbr + slot * K);
@@ -888,7 +890,9 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
             break;
         }
     }
-    if (ns > 0) a.slot_rec[slot0 + ns - 1].z = 2.0f * radius_at(a.mode, a.r, ray, t_sel);
+    if (ns > 0)
+        a.slot_rec[slot0 + ns - 1] =
+            make_float4(t_sel, __int_as_float(id_sel), 2.0f * radius_at(a.mode, a.r, ray, t_sel), 0.0f);
     a.n_s[ri] = ns;
     a.primary[ri] = prim;
     a.cand_count[ri] = total;
