@@ -159,7 +159,7 @@ size_t search_region_bytes(int64_t R, int n_max, int K)
            al(4 * (size_t)(R > 0 ? R : 1)) +         // rays handed to the warp-per-ray search
            al(8 * (size_t)(R > 0 ? R : 1)) +         // intervals the learned search inferred for them
            al(4 * (size_t)(R > 0 ? R : 1)) +         // point-major pass: candidates per pixel
-           al(8 * (size_t)kLaneCap * (size_t)(R > 0 ? R : 1));   // ... and the candidates
+           al(8 * (size_t)kPmCap * (size_t)(R > 0 ? R : 1));   // ... and the candidates
 }
 
 // decoded samples, then the backward's per-sample scratch

@@ -57,8 +57,11 @@ struct BuildArgs {
 };
 
 // Candidates per ray held by the lane-per-ray search (its shared-memory
-// column) and by the point-major pass's per-ray slots.
+// column); rays with more go to the warp-per-ray search.
 constexpr int kLaneCap = 48;
+// Slots per ray of the point-major pass: the lane search reads rays of up to
+// kLaneCap candidates from them, the warp-per-ray search rays of up to kPmCap.
+constexpr int kPmCap = 128;
 
 struct SearchArgs {
     Cam cam;                 // raytab is (re)computed from cam when raytab_stale
@@ -83,7 +86,7 @@ struct SearchArgs {
     const uint32_t *pcell;   // bucket of each sorted point (whole frames: point-major candidate pass)
     int64_t n_points;        // points given to the table build (bound of the tabled ones)
     uint32_t *pm_cnt;        // [W*H] candidates each pixel's ray received from the point-major pass
-    uint2 *pm_slot;          // [W*H x kLaneCap] (t bits, table index) of those candidates
+    uint2 *pm_slot;          // [W*H x kPmCap] (t bits, table index) of those candidates
     int32_t *fallback;       // rays whose restricted search kept nothing (original indices)
     uint32_t *fallback_count;
     int32_t *wide;           // rays with more candidates than a lane holds (original indices)

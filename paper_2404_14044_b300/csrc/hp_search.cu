@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(256) k_search_splat(const SearchArgs a)
             float t;
             if (!accept_point(a, ray, p, a.cam.t_near, a.cam.t_far, t)) continue;
             const uint32_t pos = atomicAdd(a.pm_cnt + pix, 1u);
-            if (pos < (uint32_t)kLaneCap) a.pm_slot[pix * kLaneCap + pos] = make_uint2(__float_as_uint(t), (uint32_t)i);
+            if (pos < (uint32_t)kPmCap) a.pm_slot[pix * kPmCap + pos] = make_uint2(__float_as_uint(t), (uint32_t)i);
         }
     }
 }
@@ -293,12 +293,22 @@ __device__ __forceinline__ void wide_ray(const SearchArgs &a, const float2 *inte
         full_window_empty = __ballot_sync(kFull, flen != 0) == 0;
     }
 
+    // whole frames, plain search: the point-major pass left the ray's
+    // accepted points in its slots; the walk is needed only when they
+    // overflowed the slots or exceed the candidate cap
+    int kept = 0, total = 0;
+    bool early_hit = false, late_hit = false;
+    uint32_t n_slot = 0;
+    bool from_slots = false;
+    if (a.pm_cnt && !interval) {
+        n_slot = __ldg(a.pm_cnt + pix);
+        from_slots = n_slot <= (uint32_t)kPmCap && (int)n_slot <= a.cand_cap;
+    }
+
     // ---- window walk.  The s rows' runs are concatenated into one index
     // space (lane q holds row q's [lo, lo+len) and its exclusive offset),
     // so every load instruction serves 32 points whatever the row lengths.
-    int kept = 0, total = 0;
-    bool early_hit = false, late_hit = false;
-    for (int r0 = 0; r0 < span; r0 += 32) {
+    for (int r0 = 0; r0 < span && !from_slots; r0 += 32) {
         const int nrows = min(32, span - r0);
         uint32_t lo = 0;
         int len = 0;
@@ -357,15 +367,33 @@ __device__ __forceinline__ void wide_ray(const SearchArgs &a, const float2 *inte
     // neighbourhood (candidates within lim in depth) by K warp minima, in
     // ascending order -- so only the candidates the selection reaches are
     // ever ordered.
-    static_assert(kCandCap <= 128, "4 candidates per lane");
-    const int C = kept;
+    static_assert(kCandCap <= 128 && kPmCap <= 128, "4 candidates per lane");
+    const int C = from_slots ? (int)n_slot : kept;
     uint64_t ckey[4];
     float4 cpos[4];
+    if (from_slots) {
+        // (t bits, table index) from the slots, the positions from the table
+        const uint2 *sl = a.pm_slot + (int64_t)pix * kPmCap;
+        uint2 e2[4];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-        const int e = lane + 32 * m;
-        ckey[m] = e < C ? ck[e] : ~0ull;
-        cpos[m] = e < C ? cp[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int m = 0; m < 4; ++m) {
+            const int e = lane + 32 * m;
+            e2[m] = e < C ? __ldg(sl + e) : make_uint2(0u, 0u);
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int e = lane + 32 * m;
+            cpos[m] = e < C ? __ldg(a.spts + e2[m].y) : make_float4(0.f, 0.f, 0.f, 0.f);
+            ckey[m] = e < C ? ((uint64_t)e2[m].x << 32) | (uint32_t)__float_as_int(cpos[m].w) : ~0ull;
+        }
+        total = C;
+    } else {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int e = lane + 32 * m;
+            ckey[m] = e < C ? ck[e] : ~0ull;
+            cpos[m] = e < C ? cp[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
     }
     __syncwarp();                              // the buffers are scratch from here on
     float T = 1.0f, t_prev = 0.0f, t_sel = 0.0f;
@@ -633,7 +661,7 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
         const uint32_t cnt = __ldg(a.pm_cnt + pix);
         if (cnt > (uint32_t)kLaneCap) return false;   // more than the column holds
         // 16-byte loads, kPtBatch of them in flight (a ray's slots are 16-byte aligned)
-        const uint4 *sl = reinterpret_cast<const uint4 *>(a.pm_slot + (int64_t)pix * kLaneCap);
+        const uint4 *sl = reinterpret_cast<const uint4 *>(a.pm_slot + (int64_t)pix * kPmCap);
         for (uint32_t c0 = 0; c0 < cnt; c0 += 2 * kPtBatch) {
             uint4 e[kPtBatch];
 #pragma unroll
@@ -1124,6 +1152,7 @@ cudaError_t search_pass(const SearchArgs &a, cudaStream_t st, Prof *prof, int ki
     SearchArgs b = a;
     b.ray_map = a.wide;
     b.count_ptr = a.wide_count;
+    if (!point_major) b.pm_cnt = nullptr;   // no slots to read the candidates from
     if (a.prop_w) {
         // the lanes left the inferred intervals of the rays they handed over
         b.interval = a.interval_buf;
@@ -1160,6 +1189,7 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof)
         b.ray_map = a.fallback;
         b.count_ptr = a.fallback_count;
         b.raytab_stale = 0;
+        b.pm_cnt = nullptr;
         if ((e = cudaMemsetAsync(a.pull, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
         auto wide_k = a.K <= 4 ? k_search_select_wide<4> : a.K <= 8 ? k_search_select_wide<8>
                     : a.K <= 16 ? k_search_select_wide<16> : k_search_select_wide<32>;

@@ -189,6 +189,19 @@ def test_objects_reduced_full_frame():
     assert_table(g, sc)
 
 
+def test_crowded_rays_full_frame():
+    # dense clouds: rays with more candidates than a lane's column (48) and
+    # than the point-major pass's slots (128), so the warp-per-ray search runs
+    # both from the slots and with its own walk
+    sc = scenes.sphere_plane_64(seed=3, n_sphere=125_000, n_plane=125_000, res=64)
+    g = gpu_render(sc)
+    o = oracle_render(sc)
+    c = np.asarray(o["cand_count"])
+    assert (c > 48).sum() > 500 and (c > 128).sum() > 100
+    assert_parity(g, o, sc.params.K)
+    assert_table(g, sc)
+
+
 # ------------------------------------------- full-size workloads, sampled rays
 
 def _sampled(sc, n=3000, seed=11):
