@@ -153,12 +153,12 @@ def algorithmic(kernel, N, Nv, P, R, S, K, F, dims, U, tensor_decode=True):
 NCU_TRAFFIC = {
     # the search stage's time (k_search_select) covers the point-major pass
     # (k_search_splat) and the selection launch: their bytes are summed
-    "k_search_select": {"bytes": 34691584 + 15346432 + 94497280 + 42607360,
+    "k_search_select": {"bytes": 35452160 + 17165056 + 94461440 + 42873344,
                         "sources": ("hp_search.cu", "hp_common.cuh", "hp_kernels.cuh"),
-                        "sha256": "7ef68d86a784bb4195481bdaade0191bc4b98eb41ac9fe90abf68045d3094241"},
-    "k_aggregate_decode": {"bytes": 78086912 + 1017344,
+                        "sha256": "e6c1238d67f8bf56bd0bb212ff5441650a2a10885cf701a0ef1c93651ea10a14"},
+    "k_aggregate_decode": {"bytes": 78249472 + 941312,
                            "sources": ("hp_decode_tc.cu", "hp_tc.cuh", "hp_common.cuh", "hp_kernels.cuh"),
-                           "sha256": "fc0d62ce8049b9a8bc7ecf10f896e4fe5dd1b1e8e201932880afb7aa4bdc8f5d"},
+                           "sha256": "ff5638bc5e379bb2e5c4916ce9c604b6ff679af047e1fbedc8a4ef5630dcd526"},
 }
 
 
