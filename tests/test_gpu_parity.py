@@ -189,15 +189,18 @@ def test_objects_reduced_full_frame():
     assert_table(g, sc)
 
 
-def test_crowded_rays_full_frame():
+@pytest.mark.parametrize("mode,K,n", [(scenes.RADIUS_FIXED, 8, 250_000), (scenes.RADIUS_FIXED, 16, 250_000),
+                                      (scenes.RADIUS_CONE_EXACT, 16, 120_000)])
+def test_crowded_rays_full_frame(mode, K, n):
     # dense clouds: rays with more candidates than a lane's column (48) and
     # than the point-major pass's slots (128), so the warp-per-ray search runs
     # both from the slots and with its own walk
-    sc = scenes.sphere_plane_64(seed=3, n_sphere=125_000, n_plane=125_000, res=64)
+    sc = scenes.sphere_plane_64(seed=3, n_sphere=n // 2, n_plane=n // 2, res=64)
+    sc.params = scenes.Params(**{**sc.params.__dict__, "radius_mode": mode, "rho": 2.5 if mode else 0.0, "K": K})
     g = gpu_render(sc)
     o = oracle_render(sc)
     c = np.asarray(o["cand_count"])
-    assert (c > 48).sum() > 500 and (c > 128).sum() > 100
+    assert (c > 48).sum() > 500 and (c > 128).sum() > 100 and ((c > 48) & (c <= 128)).sum() > 500
     assert_parity(g, o, sc.params.K)
     assert_table(g, sc)
 
