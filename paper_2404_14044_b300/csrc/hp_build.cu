@@ -139,7 +139,7 @@ __device__ __forceinline__ bool pt_less(const float4 &a, const float4 &b)
 // larger bucket goes on a list that one warp per bucket ranks: each point's
 // place is the number of the bucket's points before it.
 constexpr int kSmallBucket = 8;
-constexpr unsigned kBigSortBlocks = 296;   // warps loop over the large-bucket list
+constexpr unsigned kBigSortBlocks = 888;   // warps loop over the large-bucket list (6 blocks per SM of 148)
 
 __global__ void __launch_bounds__(256) k_bucket_sort(int64_t P, const uint32_t *__restrict__ start,
                                                      const float4 *__restrict__ tmp, float4 *__restrict__ spts,
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(256) k_bucket_sort(int64_t P, const uint32_t *
         }
 }
 
-constexpr int kBigStage = 256;   // points of a large bucket staged in shared memory per warp
+constexpr int kBigStage = 128;   // points of a large bucket staged in shared memory per warp (larger ones: from global memory)
 
 __global__ void __launch_bounds__(256) k_bucket_sort_big(const uint32_t *__restrict__ start,
                                                          const float4 *__restrict__ tmp, float4 *__restrict__ spts,
