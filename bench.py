@@ -153,12 +153,12 @@ def algorithmic(kernel, N, Nv, P, R, S, K, F, dims, U, tensor_decode=True):
 NCU_TRAFFIC = {
     # the search stage's time (k_search_select) covers the point-major pass
     # (k_search_splat) and the selection launch: their bytes are summed
-    "k_search_select": {"bytes": 35452160 + 17165056 + 94461440 + 42873344,
+    "k_search_select": {"bytes": 35423744 + 15392000 + 87702016 + 31165184,
                         "sources": ("hp_search.cu", "hp_common.cuh", "hp_kernels.cuh"),
-                        "sha256": "e6c1238d67f8bf56bd0bb212ff5441650a2a10885cf701a0ef1c93651ea10a14"},
-    "k_aggregate_decode": {"bytes": 78249472 + 941312,
+                        "sha256": "a138349f42a70ce04a0271a654cd293e1d90b80f3ed7b41df62b169b94c2cdbf"},
+    "k_aggregate_decode": {"bytes": 78093824 + 944640,
                            "sources": ("hp_decode_tc.cu", "hp_tc.cuh", "hp_common.cuh", "hp_kernels.cuh"),
-                           "sha256": "ff5638bc5e379bb2e5c4916ce9c604b6ff679af047e1fbedc8a4ef5630dcd526"},
+                           "sha256": "ae722d4449cebe06f078fb62b4d4e6be9ce46af2a65dfc68967d103068c86b4c"},
 }
 
 

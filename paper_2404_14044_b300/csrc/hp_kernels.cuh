@@ -109,9 +109,9 @@ struct SearchArgs {
     int32_t *nbr;
     float *nbr_dist;
     int64_t capacity;
-    float4 *slot_rec;        // [R * n_max] per-ray sample slots (scratch): t, source id bits, delta
-    int32_t *slot_nbr;       // [R * n_max * K]
-    float *slot_dist;
+    float4 *slot_rec;        // [n_max x R] sample slots (scratch), slot m of ray i at m R + i: t, source id bits, delta
+    int32_t *slot_nbr;       // [n_max x R x K]
+    float *slot_dist;        // [n_max x R x K]
     uint64_t *flags;         // [ceil(R / 256)] look-back words of the packing scan
     uint32_t *ticket;
     ErrWord *err;

@@ -398,7 +398,9 @@ __device__ __forceinline__ void wide_ray(const SearchArgs &a, const float2 *inte
     __syncwarp();                              // the buffers are scratch from here on
     float T = 1.0f, t_prev = 0.0f, t_sel = 0.0f;
     int jstar = -1, ns = 0, prim = -1;
-    const int64_t slot0 = ri * n_max;
+    // slot m of ray ri at m R + ri: sample-major planes, so the rays of a
+    // tile write (and the pack reads) their first samples side by side
+    auto slot_at = [&](int m) { return (int64_t)m * a.R + ri; };
     bool done = false;
     early_hit = __any_sync(kFull, early_hit);
     late_hit = __any_sync(kFull, late_hit);
@@ -489,11 +491,11 @@ __device__ __forceinline__ void wide_ray(const SearchArgs &a, const float2 *inte
                 pj.z = __shfl_sync(kFull, pj.z, sl);
                 prim = (int)pixel_key(a.cam, a.h, make_float3(pj.x, pj.y, pj.z));
             }
-            const int64_t slot = slot0 + ns;
+            const int64_t slot = slot_at(ns);
             if (lane == 0) {
                 a.slot_rec[slot].x = tj;
                 a.slot_rec[slot].y = __int_as_float(idj);
-                if (ns > 0) a.slot_rec[slot - 1].z = tj - t_sel;
+                if (ns > 0) a.slot_rec[slot_at(ns - 1)].z = tj - t_sel;
             }
             t_sel = tj;
             if (lane < K) {
@@ -519,7 +521,7 @@ __device__ __forceinline__ void wide_ray(const SearchArgs &a, const float2 *inte
     for (int m = 0; m < 4; ++m)
         if (ckey[m] != ~0ull && ckey[m] > lmax) lmax = ckey[m];
     const uint64_t kmax = warp_max_u64(lmax);
-    if (lane == 0 && ns > 0) a.slot_rec[slot0 + ns - 1].z = 2.0f * radius_at(a.mode, a.r, ray, t_sel);
+    if (lane == 0 && ns > 0) a.slot_rec[slot_at(ns - 1)].z = 2.0f * radius_at(a.mode, a.r, ray, t_sel);
     if (lane == 0) {
         a.n_s[ri] = ns;
         a.primary[ri] = prim;
@@ -762,7 +764,9 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
     int id_sel = 0;
     int jstar = -1, ns = 0, prim = -1;
     bool done = false;
-    const int64_t slot0 = ri * n_max;
+    // slot m of ray ri at m R + ri: sample-major planes, so the rays of a
+    // tile write (and the pack reads) their first samples side by side
+    auto slot_at = [&](int m) { return (int64_t)m * a.R + ri; };
     const float kInf = __int_as_float(0x7f800000);
     // candidate 0: the smallest (t, id)
     float tq = t_lo;
@@ -878,9 +882,9 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
                 jstar = j;
                 prim = (int)pixel_key(a.cam, a.h, make_float3(pj.x, pj.y, pj.z));
             }
-            const int64_t slot = slot0 + ns;
+            const int64_t slot = slot_at(ns);
             // a record is written whole once its delta is known (next sample or the end)
-            if (ns > 0) a.slot_rec[slot - 1] = make_float4(t_sel, __int_as_float(id_sel), tj - t_sel, 0.0f);
+            if (ns > 0) a.slot_rec[slot_at(ns - 1)] = make_float4(t_sel, __int_as_float(id_sel), tj - t_sel, 0.0f);
             t_sel = tj;
             id_sel = idj;
             if ((K & 3) == 0) {
@@ -919,7 +923,7 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
         }
     }
     if (ns > 0)
-        a.slot_rec[slot0 + ns - 1] =
+        a.slot_rec[slot_at(ns - 1)] =
             make_float4(t_sel, __int_as_float(id_sel), 2.0f * radius_at(a.mode, a.r, ray, t_sel), 0.0f);
     a.n_s[ri] = ns;
     a.primary[ri] = prim;
@@ -1051,7 +1055,7 @@ __global__ void __launch_bounds__(kPackRays) k_pack_samples(const SearchArgs a)
     for (int p = tid; p < total; p += kPackRays) {
         const int v = s_slot[p];
         const int64_t r = ray0 + (v >> 4);
-        const int64_t sl = r * a.n_max + (v & 15);
+        const int64_t sl = (int64_t)(v & 15) * a.R + r;
         const float4 rec = a.slot_rec[sl];
         a.t[base + p] = rec.x;
         a.src[base + p] = __float_as_int(rec.y);
@@ -1062,7 +1066,7 @@ __global__ void __launch_bounds__(kPackRays) k_pack_samples(const SearchArgs a)
     const int K = a.K;
     auto slot_of = [&](int64_t p) {
         const int v = s_slot[p];
-        return (ray0 + (v >> 4)) * a.n_max + (v & 15);
+        return (int64_t)(v & 15) * a.R + ray0 + (v >> 4);
     };
     const bool vec = (K & 3) == 0 && (((uintptr_t)a.nbr | (uintptr_t)a.nbr_dist) & 15) == 0;
     if (vec) {
