@@ -179,7 +179,7 @@ hp_status hp_set_workspace(hp_ctx *ctx, void *d_ptr, size_t bytes);
 /* Sec. 3.2 table build for d_points (n_points x 3, world xyz) seen by `cam`.
  * Fixed mode: r is the search radius.  Cone modes: r is used only when
  * cfg.rho <= 0 (r_min at t_near).  n_points may be 0.  Kernels: projection +
- * warp-aggregated bucket counts, decoupled-lookback scan, scatter, per-bucket
+ * atomic bucket counts, decoupled-lookback scan, scatter, per-bucket
  * depth sort. */
 hp_status hp_build_table(hp_ctx *ctx, const float *d_points, int64_t n_points, const hp_camera *cam,
                          float r, void *stream);

@@ -4,7 +4,7 @@
 // contiguous, and the table holds, per pixel key, the start of its run (the
 // count is the difference of consecutive starts).
 //
-// K1 k_project_count  camera transform + key, warp-aggregated atomic count;
+// K1 k_project_count  camera transform + key, one atomic count per point;
 //                     the atomic's return value is the point's slot in its run
 // K2 k_scan           exclusive prefix sum of the counts (decoupled look-back)
 // K3 k_scatter        each point written to start[key] + slot as float4
@@ -43,17 +43,9 @@ __global__ void __launch_bounds__(256) k_project_count(const float *__restrict__
     if (lane == 0 && ze != 0u) atomicMax(&s_ze, ze);
     __syncthreads();
     if (threadIdx.x == 0 && s_ze != 0u) atomicMax(zmin_enc, s_ze);   // one global atomic per block
-    const unsigned active = __ballot_sync(0xffffffffu, valid);
     uint32_t rank = 0;
-    if (valid) {
-        // lanes that hit the same bucket share one atomic
-        const unsigned grp = __match_any_sync(active, key);
-        const int leader = __ffs(grp) - 1;
-        uint32_t base = 0;
-        if (lane == leader) base = atomicAdd(cnt + key, (uint32_t)__popc(grp));
-        base = __shfl_sync(grp, base, leader);
-        rank = base + (uint32_t)__popc(grp & ((1u << lane) - 1u));
-    }
+    // one atomic per point; its return value is the point's slot in its run
+    if (valid) rank = atomicAdd(cnt + key, 1u);
     if (in) keyrank[i] = make_uint2(key, rank);
 }
 
