@@ -141,12 +141,12 @@ size_t table_region_bytes(int64_t N, int64_t P, int64_t npix)
     size_t o = 0;
     o += al(16 * (size_t)npix);                              // ray table (first: depends on W*H only)
     o += al(256);                                            // tickets
+    o += al(8 * (size_t)div_up(P + 1, kScanTile));           // scan flags
     o += al(4 * (size_t)(P + 1));                            // cnt
     o += al(4 * (size_t)(P + 1));                            // start
     o += al(8 * (size_t)N);                                  // keyrank
     o += al(16 * (size_t)N);                                 // spts
     o += al(16 * (size_t)N);                                 // spts before the in-bucket order
-    o += al(8 * (size_t)div_up(P + 1, kScanTile));           // scan flags
     return o;
 }
 
@@ -413,13 +413,15 @@ hp_status hp_build_table(hp_ctx *ctx, const float *d_points, int64_t n_points, c
         ctx->raytab = rt;
         o += al(16 * (size_t)npix);
     }
+    // tickets, look-back words and counts back to back: the build clears
+    // them with one memset
     ctx->scan_ticket = reinterpret_cast<uint32_t *>(base + o); o += al(256);
+    ctx->scan_flags = reinterpret_cast<uint64_t *>(base + o);  o += al(8 * (size_t)div_up(P + 1, kScanTile));
     ctx->cnt = reinterpret_cast<uint32_t *>(base + o);         o += al(4 * (size_t)(P + 1));
     ctx->start = reinterpret_cast<uint32_t *>(base + o);       o += al(4 * (size_t)(P + 1));
     ctx->keyrank = reinterpret_cast<uint2 *>(base + o);        o += al(8 * (size_t)n_points);
     ctx->spts = reinterpret_cast<float4 *>(base + o);          o += al(16 * (size_t)n_points);
-    ctx->spts_tmp = reinterpret_cast<float4 *>(base + o);      o += al(16 * (size_t)n_points);
-    ctx->scan_flags = reinterpret_cast<uint64_t *>(base + o);
+    ctx->spts_tmp = reinterpret_cast<float4 *>(base + o);
 
     Cam c{};
     std::memcpy(c.R, cam->R, sizeof(c.R));

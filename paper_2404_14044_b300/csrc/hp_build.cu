@@ -214,13 +214,19 @@ __global__ void __launch_bounds__(256) k_bucket_sort_big(const uint32_t *__restr
 cudaError_t launch_build(const BuildArgs &a, cudaStream_t st, Prof *prof)
 {
     cudaError_t e;
-    if ((e = cudaMemsetAsync(a.cnt, 0, sizeof(uint32_t) * (size_t)(a.P + 1), st)) != cudaSuccess) return e;
     const int64_t n_scan = a.P + 1;
     const int64_t scan_tiles = div_up(n_scan, kScanTile);
-    if ((e = cudaMemsetAsync(a.scan_flags, 0, sizeof(uint64_t) * (size_t)scan_tiles, st)) != cudaSuccess) return e;
-    // the scan's ticket, the depth minimum (scan_ticket[1] == zmin_enc) and
-    // the large-bucket count of the sort (scan_ticket[2])
-    if ((e = cudaMemsetAsync(a.scan_ticket, 0, 3 * sizeof(uint32_t), st)) != cudaSuccess) return e;
+    // the scan's ticket, the depth minimum (scan_ticket[1] == zmin_enc), the
+    // large-bucket count of the sort (scan_ticket[2]), the look-back words and
+    // the counts lie in this order, back to back: one memset clears them
+    const char *z0 = reinterpret_cast<const char *>(a.scan_ticket);
+    const char *zf = reinterpret_cast<const char *>(a.scan_flags);
+    const char *zc = reinterpret_cast<const char *>(a.cnt);
+    if (!(zf >= z0 + 3 * sizeof(uint32_t) && zc >= zf + sizeof(uint64_t) * (size_t)scan_tiles))
+        return cudaErrorInvalidValue;
+    if ((e = cudaMemsetAsync(a.scan_ticket, 0, (size_t)(zc - z0) + sizeof(uint32_t) * (size_t)n_scan, st)) !=
+        cudaSuccess)
+        return e;
     if (a.N > 0) {
         prof_begin(prof, st, KID_PROJECT);
         k_project_count<<<(unsigned)div_up(a.N, 256), 256, 0, st>>>(a.pts, a.N, a.cam, a.h, a.cnt, a.keyrank, a.zmin_enc);

@@ -1132,9 +1132,7 @@ cudaError_t search_pass(const SearchArgs &a, cudaStream_t st, Prof *prof, int ki
         return e;
     if ((e = cudaFuncSetAttribute(wide_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm)) != cudaSuccess)
         return e;
-    if ((e = cudaMemsetAsync(a.wide_count, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(a.pull, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(a.lane_units, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+    // wide_count, pull and lane_units: cleared with the tickets by launch_search
     int64_t units;
     if (!a.rays && !a.ray_map)
         units = div_up((int64_t)a.cam.width, 8) * div_up((int64_t)a.cam.height, 4);
@@ -1180,9 +1178,18 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof)
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const int64_t tiles = div_up(a.R, kPackRays);
-    if ((e = cudaMemsetAsync(a.flags, 0, sizeof(uint64_t) * (size_t)tiles, st)) != cudaSuccess) return e;
-    // pack ticket, fallback count, wide-ray count
-    if ((e = cudaMemsetAsync(a.ticket, 0, 3 * sizeof(uint32_t), st)) != cudaSuccess) return e;
+    // the ticket words (pack ticket, fallback count, wide-ray count, lane
+    // units, the 64-bit pull counter: words 0-5) and the pack's look-back
+    // words after them: one memset
+    const char *z0 = reinterpret_cast<const char *>(a.ticket);
+    const char *zf = reinterpret_cast<const char *>(a.flags);
+    const char *ze = reinterpret_cast<const char *>(a.flags + tiles);
+    if (!(zf >= z0 + 6 * sizeof(uint32_t) && reinterpret_cast<const char *>(a.wide_count) < zf &&
+          reinterpret_cast<const char *>(a.lane_units) < zf && reinterpret_cast<const char *>(a.pull + 1) <= zf &&
+          reinterpret_cast<const char *>(a.wide_count) >= z0 && reinterpret_cast<const char *>(a.lane_units) >= z0 &&
+          reinterpret_cast<const char *>(a.pull) >= z0))
+        return cudaErrorInvalidValue;
+    if ((e = cudaMemsetAsync(a.ticket, 0, (size_t)(ze - z0), st)) != cudaSuccess) return e;
     if ((e = search_pass(a, st, prof, KID_SEARCH)) != cudaSuccess) return e;
     if ((a.interval || a.prop_w) && a.fallback) {
         // plain search for the rays the restricted search flagged: few and
