@@ -155,7 +155,7 @@ NCU_TRAFFIC = {
     # (k_search_splat) and the selection launch: their bytes are summed
     "k_search_select": {"bytes": 35423744 + 15392000 + 87702016 + 31165184,
                         "sources": ("hp_search.cu", "hp_common.cuh", "hp_kernels.cuh"),
-                        "sha256": "703b78f66a96e127d395b6931334f99fd941e7cc85d03b600d3cebe02c7b3e2d"},
+                        "sha256": "1f3948291eb2237725659b9b2930f2988538c28def01a4f1cd3d0a12a00df4c3"},
     "k_aggregate_decode": {"bytes": 78093824 + 944640,
                            "sources": ("hp_decode_tc.cu", "hp_tc.cuh", "hp_common.cuh", "hp_kernels.cuh"),
                            "sha256": "ae722d4449cebe06f078fb62b4d4e6be9ce46af2a65dfc68967d103068c86b4c"},

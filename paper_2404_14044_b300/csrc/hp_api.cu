@@ -516,6 +516,9 @@ static hp_status search_impl(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n
         size_t o = 0;
         a.ticket = reinterpret_cast<uint32_t *>(base + o);   o += al(256);
         a.flags = reinterpret_cast<uint64_t *>(base + o);    o += al(8 * (size_t)div_up(n_rays, 256));
+        // right after the look-back words: the search clears the tickets,
+        // those words and the per-pixel candidate counts with one memset
+        a.pm_cnt = reinterpret_cast<uint32_t *>(base + o);    o += al(4 * (size_t)n_rays);
         a.slot_rec = reinterpret_cast<float4 *>(base + o);   o += al(16 * slots);
         a.slot_nbr = reinterpret_cast<int32_t *>(base + o);  o += al(4 * slots * K);
         a.slot_dist = reinterpret_cast<float *>(base + o);   o += al(4 * slots * K);
@@ -523,7 +526,6 @@ static hp_status search_impl(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n
         a.fallback_count = a.ticket + 1;
         a.wide = reinterpret_cast<int32_t *>(base + o);      o += al(4 * (size_t)n_rays);
         a.interval_buf = reinterpret_cast<float2 *>(base + o); o += al(8 * (size_t)n_rays);
-        a.pm_cnt = reinterpret_cast<uint32_t *>(base + o);    o += al(4 * (size_t)n_rays);
         a.pm_slot = reinterpret_cast<uint2 *>(base + o);
         a.pcell = reinterpret_cast<const uint32_t *>(ctx->keyrank);
         a.n_points = ctx->N;

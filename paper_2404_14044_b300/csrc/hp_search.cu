@@ -1111,12 +1111,17 @@ namespace {
 
 // One search pass over the rays `a` describes: the lane-per-ray kernel, then
 // the warp-per-ray kernel over the rays the lanes listed as too wide.
+// Whole frames, plain search: the point-major pass finds the candidates.
+bool point_major_pass(const SearchArgs &a)
+{
+    return !a.prop_w && !a.interval && !a.rays && !a.ray_map && a.pm_slot && a.pm_cnt && a.pcell &&
+           a.R == (int64_t)a.cam.width * a.cam.height;
+}
+
 cudaError_t search_pass(const SearchArgs &a, cudaStream_t st, Prof *prof, int kid)
 {
     cudaError_t e;
-    // whole frames, plain search: the point-major pass finds the candidates
-    const bool point_major = !a.prop_w && !a.interval && !a.rays && !a.ray_map && a.pm_slot && a.pcell &&
-                             a.R == (int64_t)a.cam.width * a.cam.height;
+    const bool point_major = point_major_pass(a);
     auto lane_k = a.prop_w ? (a.K <= 4 ? k_search_select<4, 2> : a.K <= 8 ? k_search_select<8, 2>
                               : a.K <= 16 ? k_search_select<16, 2> : k_search_select<32, 2>)
                   : a.interval ? (a.K <= 4 ? k_search_select<4, 1> : a.K <= 8 ? k_search_select<8, 1>
@@ -1141,10 +1146,7 @@ cudaError_t search_pass(const SearchArgs &a, cudaStream_t st, Prof *prof, int ki
     // persistent warps: as many blocks as stay resident, fewer for small work
     const int KB = a.K <= 4 ? 4 : a.K <= 8 ? 8 : a.K <= 16 ? 16 : 32;
     const int64_t blocks = std::min<int64_t>(div_up(units, kLaneWarps), (int64_t)a.n_sm * lane_blocks_per_sm(KB));
-    if (point_major) {
-        const int64_t npix = (int64_t)a.cam.width * a.cam.height;
-        if ((e = cudaMemsetAsync(a.pm_cnt, 0, sizeof(uint32_t) * (size_t)npix, st)) != cudaSuccess) return e;
-    }
+    // pm_cnt: cleared with the tickets by launch_search
     prof_begin(prof, st, kid);
     if (point_major && a.n_points > 0)
         k_search_splat<<<(unsigned)div_up(a.n_points, 256), 256, 0, st>>>(a);
@@ -1184,6 +1186,11 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof)
     const char *z0 = reinterpret_cast<const char *>(a.ticket);
     const char *zf = reinterpret_cast<const char *>(a.flags);
     const char *ze = reinterpret_cast<const char *>(a.flags + tiles);
+    if (point_major_pass(a)) {
+        // ... and the point-major pass's per-pixel counts, which follow
+        if (reinterpret_cast<const char *>(a.pm_cnt) < ze) return cudaErrorInvalidValue;
+        ze = reinterpret_cast<const char *>(a.pm_cnt + a.R);
+    }
     if (!(zf >= z0 + 6 * sizeof(uint32_t) && reinterpret_cast<const char *>(a.wide_count) < zf &&
           reinterpret_cast<const char *>(a.lane_units) < zf && reinterpret_cast<const char *>(a.pull + 1) <= zf &&
           reinterpret_cast<const char *>(a.wide_count) >= z0 && reinterpret_cast<const char *>(a.lane_units) >= z0 &&
