@@ -155,10 +155,10 @@ NCU_TRAFFIC = {
     # (k_search_splat) and the selection launch: their bytes are summed
     "k_search_select": {"bytes": 35423744 + 15392000 + 87702016 + 31165184,
                         "sources": ("hp_search.cu", "hp_common.cuh", "hp_kernels.cuh"),
-                        "sha256": "1f3948291eb2237725659b9b2930f2988538c28def01a4f1cd3d0a12a00df4c3"},
+                        "sha256": "41835b4f320036211d61a1648223f30ad5e32a442799dcf5b7052659ad6a282d"},
     "k_aggregate_decode": {"bytes": 78093824 + 944640,
                            "sources": ("hp_decode_tc.cu", "hp_tc.cuh", "hp_common.cuh", "hp_kernels.cuh"),
-                           "sha256": "ae722d4449cebe06f078fb62b4d4e6be9ce46af2a65dfc68967d103068c86b4c"},
+                           "sha256": "a05dc4083a2001561310a067dd6d2188049d46121d7ff9bd2b6e797aca461de8"},
 }
 
 

@@ -1,5 +1,12 @@
 // Radiance-MLP decode on the 5th-generation tensor cores (tcgen05 + TMEM).
 //
+// Two kernels.  k_decode_ws (further down; the one that runs whenever every
+// layer is at most 128 wide and its weights fit shared memory) is
+// warp-specialized: producer warps gather and blend while two groups of
+// consumer warps take alternate tiles, keep the hidden activations in tensor
+// memory and accumulate the FP32-accurate split in one accumulator.
+// k_decode_tc, described here, serves the MLPs that do not fit that layout.
+//
 // k_decode_tc (persistent, one 512-thread block per SM, 128 samples per
 // tile): the block stages the hidden layers' weights once in shared memory as
 // K-major FP16 (or BF16) operands.  The neighbour lists (ids and distances)

@@ -1,33 +1,37 @@
 // Window search (Sec. 3.2 "Searching") and adaptive primary surface sampling
 // (Sec. 3.3), fused.
 //
+// k_search_splat (whole frames, plain search): one thread per tabled point
+// tests it against the ray of every pixel whose window holds its bucket and
+// appends the accepted (t, table index) pairs to that pixel's slots (an
+// atomic count per pixel; kPmCap slots).  Rays then only select.
+//
 // k_search_select: one thread per ray.  A warp owns an 8 x 4 tile of pixels
-// (whole frames) or 32 consecutive listed rays, so its lanes' windows overlap
-// and their point loads hit the same cache lines.  For a ray through pixel
-// (u, v) the s x s window of buckets is s rows of the padded table; the
-// buckets of one row are adjacent keys, so each row's points are one
-// contiguous run of the reordered list [start[k], start[k+s]).  The lane
-// tests every point of its s runs and inserts the accepted ones into its own
-// (t, id)-sorted list in shared memory (column `lane` of a [capacity][32]
-// array: conflict-free whatever the list lengths).  It then walks its
-// candidates in depth order: for candidate j it collects the K nearest
+// (whole frames) or 32 consecutive listed rays.  The lane gathers its ray's
+// accepted points into its own column of a [kLaneCap][32] shared-memory
+// array (conflict-free whatever the counts): from the point-major slots, or
+// by walking the s x s window itself (listed rays, restricted searches; a
+// window row of s buckets is s adjacent keys, so one contiguous run of the
+// reordered list).  The column stays unsorted: candidate j+1 is the smallest
+// (t, id) above candidate j, found by a scan, and the selection visits only
+// ~1.4 candidates a ray.  For candidate j the lane collects the K nearest
 // candidates within r(t_j) of the sample (only those within that distance in
 // t can qualify), forms d_j and alpha_j, applies the weight and the primary-
 // cluster rule, and stops when the cluster ends, when n samples are kept or
 // when gamma * T_j <= eps_w (no later weight can pass).  Rays with more
-// accepted points than a lane holds are listed and searched again by
-// k_search_select_wide.
+// candidates than a column holds are listed for k_search_select_wide.
 //
-// k_search_select_wide: one warp per ray, for those listed rays.  The warp
-// reads the concatenated runs 32 points at a time, appends the accepted ones
-// with a ballot prefix into its shared-memory buffer (keeping the cand_cap
-// smallest (t, id)), sorts them, and lanes take one candidate each for the
-// neighbour search.
+// k_search_select_wide: one warp per listed ray.  The candidates come from
+// the point-major slots, or from a walk that reads the concatenated runs 32
+// points at a time and appends the accepted ones with a ballot prefix
+// (keeping the cand_cap smallest (t, id)).  Lane l holds candidates l, l+32,
+// l+64, l+96; candidates are taken in (t, id) order by warp minima and each
+// one's K nearest are ranked in shared memory.
 //
-// Each ray writes its samples into its own n_samples slots of a scratch
-// area; K6 packs them ray by ray (scan + copy), so the output order is
-// independent of scheduling and blocks never wait on one another while they
-// search.
+// Each ray writes its samples into n_samples slots of a scratch area (slot m
+// of ray i at m R + i); K6 packs them ray by ray (scan + copy), so the output
+// order is independent of scheduling and blocks never wait on one another
+// while they search.
 #include <algorithm>
 
 #include "hp_kernels.cuh"
