@@ -598,24 +598,38 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
     uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + L.tslot);
     float *comb = reinterpret_cast<float *>(smem + L.comb);
 
-    // ---- stage weights (global W is [out][in] FP32) and FP32 biases
+    // ---- stage weights (global W is [out][in] FP32) and FP32 biases; each
+    // thread has kStageBatch weight loads in flight before it converts any
+    // (one load at a time made the staging ~35k cycles per CTA)
     {
+        constexpr int kStageBatch = 8;
         int g = 0;
         for (int l = 0; l < a.n_layers; ++l) {
             const int fi = a.dims[l], fo = a.dims[l + 1];
             const int nw = fi * fo;
             if (l < L.nh) {
-                for (int e = tid; e < nw; e += blockDim.x) {
-                    const int o = e / fi, i = e - o * fi;
-                    const float w = __ldg(a.mlp + g + e);
-                    const uint32_t off = tc::kmajor_off(o, i, fi);
-                    if constexpr (kBF16) {
-                        *reinterpret_cast<__nv_bfloat16 *>(smem + L.w_hi[l] + off) = __float2bfloat16_rn(w);
-                    } else {
-                        __half h, lo;
-                        tc::split_f16_same_scale(w, h, lo);
-                        *reinterpret_cast<__half *>(smem + L.w_hi[l] + off) = h;
-                        *reinterpret_cast<__half *>(smem + L.w_lo[l] + off) = lo;
+                for (int e0 = tid; e0 < nw; e0 += kStageBatch * blockDim.x) {
+                    float wv[kStageBatch];
+#pragma unroll
+                    for (int u = 0; u < kStageBatch; ++u) {
+                        const int e = e0 + u * (int)blockDim.x;
+                        wv[u] = e < nw ? __ldg(a.mlp + g + e) : 0.0f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kStageBatch; ++u) {
+                        const int e = e0 + u * (int)blockDim.x;
+                        if (e >= nw) break;
+                        const int o = e / fi, i = e - o * fi;
+                        const float w = wv[u];
+                        const uint32_t off = tc::kmajor_off(o, i, fi);
+                        if constexpr (kBF16) {
+                            *reinterpret_cast<__nv_bfloat16 *>(smem + L.w_hi[l] + off) = __float2bfloat16_rn(w);
+                        } else {
+                            __half h, lo;
+                            tc::split_f16_same_scale(w, h, lo);
+                            *reinterpret_cast<__half *>(smem + L.w_hi[l] + off) = h;
+                            *reinterpret_cast<__half *>(smem + L.w_lo[l] + off) = lo;
+                        }
                     }
                 }
             } else {
