@@ -153,12 +153,12 @@ def algorithmic(kernel, N, Nv, P, R, S, K, F, dims, U, tensor_decode=True):
 NCU_TRAFFIC = {
     # the search stage's time (k_search_select) covers the point-major pass
     # (k_search_splat) and the selection launch: their bytes are summed
-    "k_search_select": {"bytes": 35423744 + 15392000 + 87702016 + 31165184,
+    "k_search_select": {"bytes": 35589888 + 15760640 + 87729664 + 31665408,
                         "sources": ("hp_search.cu", "hp_common.cuh", "hp_kernels.cuh"),
                         "sha256": "41835b4f320036211d61a1648223f30ad5e32a442799dcf5b7052659ad6a282d"},
-    "k_aggregate_decode": {"bytes": 78093824 + 944640,
+    "k_aggregate_decode": {"bytes": 78091264 + 930560,
                            "sources": ("hp_decode_tc.cu", "hp_tc.cuh", "hp_common.cuh", "hp_kernels.cuh"),
-                           "sha256": "a05dc4083a2001561310a067dd6d2188049d46121d7ff9bd2b6e797aca461de8"},
+                           "sha256": "b413f90ba60cfcdf12eb20391b2fb8810394782f3c47547542f56badc7a182bf"},
 }
 
 
