@@ -190,7 +190,8 @@ def test_objects_reduced_full_frame():
 
 
 @pytest.mark.parametrize("mode,K,n", [(scenes.RADIUS_FIXED, 8, 250_000), (scenes.RADIUS_FIXED, 16, 250_000),
-                                      (scenes.RADIUS_CONE_EXACT, 16, 120_000)])
+                                      (scenes.RADIUS_CONE_EXACT, 16, 120_000), (scenes.RADIUS_FIXED, 32, 250_000),
+                                      (scenes.RADIUS_FIXED, 3, 250_000)])
 def test_crowded_rays_full_frame(mode, K, n):
     # dense clouds: rays with more candidates than a lane's column (48) and
     # than the point-major pass's slots (128), so the warp-per-ray search runs
