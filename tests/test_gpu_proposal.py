@@ -165,10 +165,17 @@ def _oracle_intervals(fr, cam, n_cells, theta, rng):
     return iv.astype(np.float32)
 
 
-def test_restricted_search_against_oracle():
+def _crowded():
+    # rays with more candidates than a lane's column: the restricted search
+    # hands them to the warp-per-ray pass, and its fallback walks the window
+    return scenes.sphere_plane_64(seed=3, n_sphere=125_000, n_plane=125_000, res=64)
+
+
+@pytest.mark.parametrize("crowded", [False, True])
+def test_restricted_search_against_oracle(crowded):
     H = _H()
     dev = torch.device("cuda", 0)
-    sc = _scene()
+    sc = _crowded() if crowded else _scene()
     cam, p = sc.camera, sc.params
     rng = np.random.default_rng(11)
     fr = oracle.render(sc.points, sc.feats, cam, p, sc.mlp_dims, sc.mlp_params, nthreads=8)
@@ -192,6 +199,8 @@ def test_restricted_search_against_oracle():
     # and some rays fell back to the plain search
     assert np.any(o["cand_count"] < fr["cand_count"])
     assert int(fb.item()) > 0
+    if crowded:
+        assert (np.asarray(o["cand_count"]) > 48).sum() > 100
     hp.close()
 
 
