@@ -246,13 +246,13 @@ def test_training_loop_and_miss_rate():
     hp.close()
 
 
-@pytest.mark.parametrize("subset", [False, True])
-def test_learned_search_equals_infer_then_restricted(subset):
+@pytest.mark.parametrize("subset,crowded", [(False, False), (True, False), (False, True)])
+def test_learned_search_equals_infer_then_restricted(subset, crowded):
     # the fused search infers each ray's interval with the inference
     # kernel's arithmetic: identical results, bit for bit
     H = _H()
     dev = torch.device("cuda", 0)
-    sc = _scene()
+    sc = _crowded() if crowded else _scene()
     cam, p = sc.camera, sc.params
     R = cam.width * cam.height
     rays = None
