@@ -521,7 +521,7 @@ constexpr int kWsConsumerWarps = 16;      // two groups, each 4 TMEM lane quarte
 constexpr int kWsProducerWarps = 16;
 constexpr int kWsGroupWarps = kWsConsumerWarps / 2;
 constexpr int kWsGroups = kWsGroupWarps / 4;
-constexpr int kWsBatch = 2;               // 8-column chunks a consumer thread reads from TMEM at once
+constexpr int kWsBatch = 1;               // 8-column chunks a consumer thread reads from TMEM at once (2 and 4: register spills)
 constexpr int kWsThreads = (kWsConsumerWarps + kWsProducerWarps) * 32;
 constexpr uint32_t kWsCols = 512, kColAH = 128, kColAL = 192;   // per consumer group, group g at 256 g
 
