@@ -161,9 +161,9 @@ NCU_TRAFFIC = {
     "k_search_select": {"bytes": 35589888 + 15760640 + 87729664 + 31665408,
                         "sources": ("hp_search.cu", "hp_common.cuh", "hp_kernels.cuh"),
                         "sha256": "41835b4f320036211d61a1648223f30ad5e32a442799dcf5b7052659ad6a282d"},
-    "k_aggregate_decode": {"bytes": 78088704 + 3128320,
+    "k_aggregate_decode": {"bytes": 78089984 + 3145216,
                            "sources": ("hp_decode_tc.cu", "hp_tc.cuh", "hp_common.cuh", "hp_kernels.cuh"),
-                           "sha256": "9871d4310afc76a9cedcf710c7b7581f971583f459a569ab1f50ce0d96571ed8"},
+                           "sha256": "aaa267858a72c30cfcb4365d993ed741f938feb57b4ced6a55e42a5ee326841d"},
 }
 
 

@@ -836,6 +836,17 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
                 const int nch = fo / 8;
                 for (int ch0 = cg; ch0 < nch; ch0 += kWsGroups * kWsBatch) {
                     float v1[kWsBatch][8];
+                    // the biases (16-byte aligned rows: widths are multiples
+                    // of 16) are loaded before the TMEM loads, so the two overlap
+                    float4 bq[kWsBatch][2];
+#pragma unroll
+                    for (int j = 0; j < kWsBatch; ++j) {
+                        const int ch = ch0 + kWsGroups * j;
+                        if (ch < nch) {
+                            bq[j][0] = *reinterpret_cast<const float4 *>(bias + 8 * ch);
+                            bq[j][1] = *reinterpret_cast<const float4 *>(bias + 8 * ch + 4);
+                        }
+                    }
 #pragma unroll
                     for (int j = 0; j < kWsBatch; ++j) {
                         const int ch = ch0 + kWsGroups * j;
@@ -843,15 +854,17 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
                             tc::ld8(d1 + lane_off + (uint32_t)(8 * ch), v1[j]);
                         }
                     }
-                    tc::wait_ld();
+                    // the first wait completes the loads; the others only tie
+                    // each array to the wait
+#pragma unroll
+                    for (int j = 0; j < kWsBatch; ++j) tc::wait_ld_regs(v1[j]);
 #pragma unroll
                     for (int j = 0; j < kWsBatch; ++j) {
                         const int ch = ch0 + kWsGroups * j;
                         if (ch >= nch) break;
                         const int c = 8 * ch;
-                        // biases and output weights: 16-byte aligned rows (widths are multiples of 16)
-                        const float4 b0 = *reinterpret_cast<const float4 *>(bias + c);
-                        const float4 b1 = *reinterpret_cast<const float4 *>(bias + c + 4);
+                        const float4 b0 = bq[j][0];
+                        const float4 b1 = bq[j][1];
                         const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
                         float h[8];
 #pragma unroll

@@ -163,6 +163,16 @@ __device__ __forceinline__ void ld8(uint32_t taddr, float (&v)[8])
 
 __device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// wait for this thread's TMEM loads, with v tied to the wait so that no use
+// of the loaded registers is scheduled before it
+__device__ __forceinline__ void wait_ld_regs(float (&v)[8])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7])
+                 :
+                 : "memory");
+}
+
 // 32 lanes x 32 bit, 8 consecutive columns: thread i of the warp writes lane
 // (base lane + i), columns col .. col+7.
 __device__ __forceinline__ void st8(uint32_t taddr, const uint32_t (&r)[8])
