@@ -336,7 +336,9 @@ hp_status hp_selftest_mma(hp_ctx *ctx, const uint16_t *d_a, const uint16_t *d_b,
  * frees nothing; it only clears the part of the array it uses.  The first
  * call on a device looks the array's device address up (cudaGetSymbolAddress,
  * with that device current) and caches it; make that first call before any
- * stream capture.  All calls share the one array: calls whose GPU work
+ * stream capture.  The cached address belongs to the device's primary
+ * context: after cudaDeviceReset on that device it is stale, and the process
+ * must not call hp_scan_noalloc on that device again.  All calls share the one array: calls whose GPU work
  * overlaps (different streams, or several host threads without ordering)
  * race and give wrong sums -- order them on one stream. */
 #define HP_SCAN_NOALLOC_MAX_N 67108864

@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t *__restric
 {
     __shared__ int64_t s_tile;
     __shared__ int64_t s_prefix;
-    __shared__ int s_warp[kScanThreads / 32];
+    __shared__ uint32_t s_warp[kScanThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_tile = atomicAdd(ticket, 1u);
     __syncthreads();
@@ -72,22 +72,25 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t *__restric
 #pragma unroll
         for (int k = 0; k < kScanItems; ++k) v[k] = (base + k < n) ? in[base + k] : 0u;
     }
-    int tsum = 0;
+    // tile arithmetic modulo 2^32 (the sums wrap like the uint32 result); the
+    // tile aggregate is published zero-extended, so the look-back's 62-bit
+    // sums of up to 2^26 / kScanTile aggregates never reach the state bits
+    uint32_t tsum = 0;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) tsum += (int)v[k];
-    const int incl = warp_incl_scan(tsum);
+    for (int k = 0; k < kScanItems; ++k) tsum += v[k];
+    const uint32_t incl = warp_incl_scan_u32(tsum);
     if (lane == 31) s_warp[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-        int w = lane < kScanThreads / 32 ? s_warp[lane] : 0;
-        int wi = warp_incl_scan(w);
+        const uint32_t w = lane < kScanThreads / 32 ? s_warp[lane] : 0u;
+        const uint32_t wi = warp_incl_scan_u32(w);
         if (lane < kScanThreads / 32) s_warp[lane] = wi - w;      // exclusive warp offsets
-        const int64_t agg = __shfl_sync(0xffffffffu, wi, kScanThreads / 32 - 1);
+        const int64_t agg = (int64_t)__shfl_sync(0xffffffffu, wi, kScanThreads / 32 - 1);
         const int64_t pre = lookback_prefix_warp(flags, tile, agg, err, spin_limit, tile != skip_tile);
         if (lane == 0) s_prefix = pre;
     }
     __syncthreads();
-    uint32_t run = (uint32_t)(s_prefix + s_warp[warp] + (incl - tsum));
+    uint32_t run = (uint32_t)s_prefix + s_warp[warp] + (incl - tsum);
     uint32_t o[kScanItems];
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {

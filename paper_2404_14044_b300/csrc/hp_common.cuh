@@ -218,6 +218,18 @@ __device__ __forceinline__ int warp_incl_scan(int v)
     return v;
 }
 
+// Inclusive warp scan of a uint32 (sums modulo 2^32).
+__device__ __forceinline__ uint32_t warp_incl_scan_u32(uint32_t v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
 inline int64_t div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 }  // namespace hp

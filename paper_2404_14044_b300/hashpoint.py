@@ -145,6 +145,8 @@ def scan_noalloc(d_in: torch.Tensor, d_out: torch.Tensor, d_status: Optional[tor
     allocate device memory; its scratch is a fixed static device array."""
     assert d_in.is_cuda and d_out.is_cuda and d_in.dtype == torch.int32 and d_out.dtype == torch.int32
     assert d_in.is_contiguous() and d_out.is_contiguous() and d_out.numel() >= d_in.numel()
+    assert d_in.data_ptr() % 16 == 0 and d_out.data_ptr() % 16 == 0, \
+        "hp_scan_noalloc reads and writes 16-byte vectors: both buffers must start 16-byte aligned"
     _check(lib().hp_scan_noalloc(_ptr(d_in), _ptr(d_out), d_in.numel(), _ptr(d_status), _stream(stream)),
            "hp_scan_noalloc")
 

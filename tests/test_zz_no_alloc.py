@@ -53,3 +53,35 @@ def test_scan_noalloc_rejects_too_large():
     x = torch.zeros(16, dtype=torch.int32, device=dev)
     rc = H.lib().hp_scan_noalloc(H._ptr(x), H._ptr(x), H.SCAN_NOALLOC_MAX_N + 1, None, H._stream(None))
     assert rc == H.HP_ERR_TOO_LARGE
+
+
+def _wrapping_exclusive_scan(x: np.ndarray) -> np.ndarray:
+    inc = np.cumsum(x.astype(np.uint64)) & np.uint64(0xFFFFFFFF)
+    out = np.zeros_like(x, dtype=np.uint32)
+    out[1:] = inc[:-1].astype(np.uint32)
+    return out
+
+
+@pytest.mark.parametrize("kind", ["all_ones", "near_2_31", "full_range"])
+def test_scan_noalloc_wrapping_uint32(kind):
+    """Sums past 2^31 and 2^32 inside and across 2048-entry tiles, on a ragged
+    length: the result must equal the uint32 exclusive prefix sum modulo 2^32."""
+    from paper_2404_14044_b300 import hashpoint as H
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(7)
+    n = 5 * 2048 + 777
+    if kind == "all_ones":
+        x = np.full(n, 0xFFFFFFFF, dtype=np.uint32)
+    elif kind == "near_2_31":
+        x = (np.uint32(1 << 31) - rng.integers(0, 1000, n).astype(np.uint32)).astype(np.uint32)
+    else:
+        x = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32)
+    d_in = torch.from_numpy(x.view(np.int32).copy()).to(dev)
+    status = torch.full((1,), -1, dtype=torch.int32, device=dev)
+    for _ in range(2):                                    # the shared array is reused by the second call
+        d_out = torch.full((n,), -7, dtype=torch.int32, device=dev)
+        H.scan_noalloc(d_in, d_out, status)
+        torch.cuda.synchronize()
+        assert int(status.item()) == H.HP_OK
+        got = d_out.cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, _wrapping_exclusive_scan(x))
