@@ -68,6 +68,9 @@ def lib():
         L.or_ray_candidates.argtypes = [fp, C.c_int64, C.POINTER(Camera), C.POINTER(Params), C.c_int32,
                                         C.c_int32, C.c_int32, i32p, fp]
         L.or_ray_candidates.restype = C.c_int64
+        L.or_ray_candidates_interval.argtypes = [fp, C.c_int64, C.POINTER(Camera), C.POINTER(Params), C.c_int32,
+                                                 C.c_int32, C.c_float, C.c_float, C.c_int32, i32p, fp, i32p]
+        L.or_ray_candidates_interval.restype = C.c_int64
         L.or_shade.argtypes = [fp, fp, C.c_int32, C.POINTER(Camera), C.POINTER(Params), i32p, C.c_int32, fp,
                                C.c_int32, C.c_int32, fp, i32p, dp, dp, dp, dp]
         L.or_mlp.argtypes = [i32p, C.c_int32, fp, dp, dp]
@@ -189,6 +192,24 @@ def render(pts, feats, cam, params, mlp_dims, mlp_params, rays=None, brute=False
         res["feat"] = feat_o[: S * F].reshape(S, F)
         res["out4"] = out4[: S * 4].reshape(S, 4)
     return res
+
+
+def ray_candidates_interval(pts, cam, params, pixel: int, mode: str, tn: float, tf: float, cap: int = 4096):
+    """Accepted points of one ray with t in [tn, tf]: ``mode`` "brute" (all
+    points), "full" (the hashed walk of the whole window h) or "d12" (the
+    hashed walk of the window the restricted search derives from tn).
+    Returns (ids, ts, count, window half-width walked)."""
+    pts = np.ascontiguousarray(pts, np.float32)
+    cid = np.zeros(cap, np.int32)
+    ct = np.zeros(cap, np.float32)
+    hw = np.zeros(1, np.int32)
+    m = {"brute": 0, "full": 1, "d12": 2}[mode]
+    n = lib().or_ray_candidates_interval(_p(pts, C.c_float), len(pts), C.byref(camera_struct(cam)),
+                                         C.byref(params_struct(params)), int(pixel), m, float(tn), float(tf), cap,
+                                         _p(cid, C.c_int32), _p(ct, C.c_float), _p(hw, C.c_int32))
+    if n < 0:
+        raise ValueError(f"or_ray_candidates_interval failed ({n})")
+    return cid[: min(n, cap)].copy(), ct[: min(n, cap)].copy(), int(n), int(hw[0])
 
 
 def shade(pts, feats, cam, params, mlp_dims, mlp_params, pixel, ts, nbr):

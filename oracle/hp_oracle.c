@@ -420,6 +420,36 @@ static int64_t ray_candidates_w(const frame_t *f, const ray_t *ray, int pu, int 
     return n;
 }
 
+/* D12: image-corner terms of the restricted window -- cos and sin of the
+ * largest angle between a pixel-centre ray and the optical axis, and the
+ * window's projected radius scale (float of double). */
+static void d12_terms(const or_camera *cam, const or_params *prm, float *rcos, float *rsin, float *rwin)
+{
+    double fx = cam->fx, fy = cam->fy, cx = cam->cx, cy = cam->cy;
+    double ax = fmax(fabs(0.5 - cx), fabs(((double)cam->width - 0.5) - cx)) / fx;
+    double ay = fmax(fabs(0.5 - cy), fabs(((double)cam->height - 0.5) - cy)) / fy;
+    double q = ax * ax + ay * ay;
+    double rr = prm->r;
+    *rcos = (float)(1.0 / sqrt(1.0 + q));
+    *rsin = (float)sqrt(q / (1.0 + q));
+    *rwin = (float)fmax(fx * rr * sqrt(1.0 + ax * ax), fy * rr * sqrt(1.0 + ay * ay));
+}
+
+/* D12: half-width of the window a ray restricted to depths t >= tn walks
+ * (fixed radius; the cone modes keep h): zlo = max(tn cos - r sin, z_near),
+ * lim = (win / zlo) 1.001 + 0.001, hr = min(h, floor(lim + 0.5)) when lim < h. */
+static int d12_window(const or_camera *cam, const or_params *prm, int h, float tn, float rcos, float rsin, float rwin)
+{
+    int hr = h;
+    if (prm->radius_mode == 0) {
+        float zlo = tn * rcos - prm->r * rsin;
+        if (!(zlo >= cam->z_near)) zlo = cam->z_near;
+        float lim = (rwin / zlo) * 1.001f + 1e-3f;
+        if (lim < (float)h) { int q = (int)floorf(lim + 0.5f); hr = q < h ? q : h; }
+    }
+    return hr;
+}
+
 /* ------------------------------------------------------------- selection */
 
 typedef struct {
@@ -656,16 +686,7 @@ int64_t or_render(const float *pts, int64_t N, const float *feats, int32_t F, co
     frame_t fr = {pts, N, cam, prm, h, rdd, start, ids, pos};
     /* D12 image-corner terms of the restricted window (float of double) */
     float rcos, rsin, rwin;
-    {
-        double fx = cam->fx, fy = cam->fy, cx = cam->cx, cy = cam->cy;
-        double ax = fmax(fabs(0.5 - cx), fabs(((double)cam->width - 0.5) - cx)) / fx;
-        double ay = fmax(fabs(0.5 - cy), fabs(((double)cam->height - 0.5) - cy)) / fy;
-        double q = ax * ax + ay * ay;
-        double rr = prm->r;
-        rcos = (float)(1.0 / sqrt(1.0 + q));
-        rsin = (float)sqrt(q / (1.0 + q));
-        rwin = (float)fmax(fx * rr * sqrt(1.0 + ax * ax), fy * rr * sqrt(1.0 + ay * ay));
-    }
+    d12_terms(cam, prm, &rcos, &rsin, &rwin);
     int bad = 0;
 #pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads > 0 ? nthreads : 1) reduction(| : bad)
     for (int64_t i = 0; i < R; ++i) {
@@ -684,13 +705,7 @@ int64_t or_render(const float *pts, int64_t N, const float *feats, int32_t F, co
             /* restricted to the ray's interval (D12); fall back to the plain search on a miss */
             float tn = intervals[2 * i] > cam->t_near ? intervals[2 * i] : cam->t_near;
             float tf = intervals[2 * i + 1] < cam->t_far ? intervals[2 * i + 1] : cam->t_far;
-            int hr = h;
-            if (prm->radius_mode == 0) {
-                float zlo = tn * rcos - prm->r * rsin;
-                if (!(zlo >= cam->z_near)) zlo = cam->z_near;
-                float lim = (rwin / zlo) * 1.001f + 1e-3f;
-                if (lim < (float)h) { int q = (int)floorf(lim + 0.5f); hr = q < h ? q : h; }
-            }
+            int hr = d12_window(cam, prm, h, tn, rcos, rsin, rwin);
             int early = 0, late = 0, stopped = 0;
             C = ray_candidates_w(&fr, &ray, pu, pv, brute, tn, tf, hr, &early, &late, &cs);
             int64_t Ck = C < prm->cand_cap ? C : prm->cand_cap;
@@ -782,6 +797,48 @@ int64_t or_ray_candidates(const float *pts, int64_t N, const or_camera *cam, con
     make_ray(cam, prm, rdd, (int)(pixel % W), (int)(pixel / W), &ray);
     cand_t *cs;
     int64_t C = ray_candidates(&fr, &ray, (int)(pixel % W), (int)(pixel / W), brute, cam->t_near, cam->t_far, &cs);
+    for (int64_t i = 0; i < C && i < cap; ++i) { cid[i] = cs[i].id; ct[i] = cs[i].t; }
+    free(cs); free(start); free(ids); free(pos);
+    return C;
+}
+
+/* Accepted points of one ray with t in [tn, tf] (D5 restricted to the
+ * interval), in (t, id) order.  mode 0: brute force over all points; 1: the
+ * hashed walk of the full window h; 2: the hashed walk of the D12 window hr
+ * that t >= tn allows.  Returns the count (cid / ct get the first cap) and
+ * the window half-width walked in *h_out. */
+int64_t or_ray_candidates_interval(const float *pts, int64_t N, const or_camera *cam, const or_params *prm,
+                                   int32_t pixel, int32_t mode, float tn, float tf, int32_t cap, int32_t *cid,
+                                   float *ct, int32_t *h_out)
+{
+    int32_t h;
+    float rdd;
+    if (or_window(cam, prm, &h, &rdd) != 0) return -1;
+    int64_t W = cam->width, H = cam->height;
+    if (pixel < 0 || pixel >= W * H || mode < 0 || mode > 2) return -3;
+    int64_t P = (W + 2 * h) * (H + 2 * h);
+    uint32_t *start = NULL;
+    int32_t *ids = NULL;
+    float *pos = NULL;
+    if (mode != 0) {
+        start = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(P + 1));
+        ids = (int32_t *)malloc(sizeof(int32_t) * (size_t)(N > 0 ? N : 1));
+        pos = (float *)malloc(sizeof(float) * 3 * (size_t)(N > 0 ? N : 1));
+        or_build_table(pts, N, cam, h, start, ids, pos);
+    }
+    frame_t fr = {pts, N, cam, prm, h, rdd, start, ids, pos};
+    ray_t ray;
+    int pu = (int)(pixel % W), pv = (int)(pixel / W);
+    make_ray(cam, prm, rdd, pu, pv, &ray);
+    int hr = h;
+    if (mode == 2) {
+        float rcos, rsin, rwin;
+        d12_terms(cam, prm, &rcos, &rsin, &rwin);
+        hr = d12_window(cam, prm, h, tn, rcos, rsin, rwin);
+    }
+    if (h_out) *h_out = hr;
+    cand_t *cs;
+    int64_t C = ray_candidates_w(&fr, &ray, pu, pv, mode == 0, tn, tf, hr, NULL, NULL, &cs);
     for (int64_t i = 0; i < C && i < cap; ++i) { cid[i] = cs[i].id; ct[i] = cs[i].t; }
     free(cs); free(start); free(ids); free(pos);
     return C;

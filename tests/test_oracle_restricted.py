@@ -88,3 +88,85 @@ def test_two_planes_restriction_and_fallback():
     rc = _render(sc, empty)
     assert np.array_equal(rc["cand_count"][hit], plain["cand_count"][hit])
     assert np.array_equal(rc["n_s"], plain["n_s"])
+
+
+def _halo_scene(tn, r, res=120, n_dir=48):
+    """Points just inside the radius r of pixel-centre rays at depth tn, in
+    n_dir directions perpendicular to each ray, for rays at the image corners,
+    edges and centre: the accepted points whose projections lie farthest from
+    the ray's pixel, where the D12 window bound is tightest."""
+    cam = scenes.make_camera(res, res, 40.0, (0.0, -6.0, 0.0), t_near=1.0, t_far=8.0)
+    R = cam.R.astype(np.float64)
+    eye = cam.eye()
+    pts = []
+    rays = []
+    for pu in (0, 1, res // 2, res - 2, res - 1):
+        for pv in (0, 1, res // 2, res - 2, res - 1):
+            d = np.array([(pu + 0.5 - cam.cx) / cam.fx, (pv + 0.5 - cam.cy) / cam.fy, 1.0])
+            d /= np.linalg.norm(d)
+            a = np.cross(d, [0.0, 0.0, 1.0])
+            a /= np.linalg.norm(a)
+            b = np.cross(d, a)
+            for k in range(n_dir):
+                phi = 2 * np.pi * k / n_dir
+                for t in (tn * 1.0005, tn * 1.002):
+                    pc = t * d + 0.998 * r * (np.cos(phi) * a + np.sin(phi) * b)
+                    pts.append(R.T @ pc + eye)
+            rays.append(pv * res + pu)
+    return cam, np.asarray(pts, np.float32), rays
+
+
+def test_d12_window_bound_at_its_worst_case():
+    # Pinned against brute force where the bound is tightest: points just
+    # inside the radius at the interval's start depth, in every direction
+    # around corner, edge and centre rays, over a sweep of start depths (so
+    # the window's half-width takes several values)
+    r = 0.03
+    widths = set()
+    for tn in np.linspace(1.05, 3.0, 14):
+        cam, pts, rays = _halo_scene(float(tn), r)
+        p = scenes.Params(r=r, K=4, n_max=4)
+        for px in rays:
+            b = oracle.ray_candidates_interval(pts, cam, p, px, "brute", np.float32(tn), cam.t_far)
+            d = oracle.ray_candidates_interval(pts, cam, p, px, "d12", np.float32(tn), cam.t_far)
+            assert b[2] > 0
+            assert b[2] == d[2] and np.array_equal(b[0], d[0]), (tn, px, b[2], d[2])
+            widths.add(d[3])
+    assert len(widths) >= 3, widths
+
+
+def test_d12_window_holds_every_interval_candidate():
+    # The restricted search walks the smaller window D12 derives from the
+    # interval's start tn.  Pinned against brute force over all points: for
+    # intervals that start just before a ray's first accepted point (the
+    # tightest window that point allows) and at random depths, the D12 walk,
+    # the full-window walk and brute force return the same candidates.
+    rng = np.random.default_rng(12)
+    checked = shrunk = 0
+    for seed, res in ((0, 96), (1, 120)):
+        sc = scenes.objects_800(seed=seed, n_points=60_000, res=res)
+        # a radius of several pixels at this resolution, so that h > 1 and the
+        # D12 window can shrink
+        cam, p = sc.camera, scenes.Params(**{**sc.params.__dict__, "r": 0.03})
+        pix = rng.choice(res * res, 400, replace=False)
+        for px in pix:
+            ids, ts, n, h = oracle.ray_candidates_interval(sc.points, cam, p, int(px), "brute", cam.t_near, cam.t_far)
+            if n == 0:
+                continue
+            t0 = float(ts[0])
+            for tn, tf in ((t0 - rng.uniform(0.0, 2.0 * p.r), cam.t_far),
+                           (rng.uniform(cam.t_near, t0), t0 + rng.uniform(0.0, 0.2)),
+                           (t0 + rng.uniform(0.0, 0.05), cam.t_far)):
+                tn, tf = np.float32(max(tn, cam.t_near)), np.float32(min(tf, cam.t_far))
+                b = oracle.ray_candidates_interval(sc.points, cam, p, int(px), "brute", tn, tf)
+                f = oracle.ray_candidates_interval(sc.points, cam, p, int(px), "full", tn, tf)
+                d = oracle.ray_candidates_interval(sc.points, cam, p, int(px), "d12", tn, tf)
+                assert b[2] == f[2] == d[2], (px, tn, tf, b[2], f[2], d[2])
+                assert np.array_equal(b[0], f[0]) and np.array_equal(b[0], d[0])
+                assert np.array_equal(b[1].view(np.int32), d[1].view(np.int32))
+                checked += 1
+                shrunk += d[3] < f[3]
+            if checked >= 150:
+                break
+    print("checked", checked, "shrunk", shrunk)
+    assert checked >= 150 and shrunk >= 50, (checked, shrunk)
