@@ -397,6 +397,31 @@ def forward_1008(seed: int = 0, n_field: int = 1_200_000, n_occ: int = 300_000, 
                  random_mlp(dims, seed, sigma_bias=1.5 / 0.004))
 
 
+def forward_cameras(n: int, seed: int, width: int = 1008, height: int = 756, max_shift: float = 0.15,
+                    max_angle_deg: float = 3.0) -> List[Camera]:
+    """Forward-facing views of the ``forward_1008`` scene: the reference
+    camera (at the origin, looking +z) moved by up to ``max_shift`` along each
+    axis and turned by up to ``max_angle_deg`` about x and y, as in a
+    hand-held forward-facing capture.  View 0 is the reference camera."""
+    rng = np.random.default_rng(seed)
+    f = 0.8 * width
+    cams = []
+    for i in range(n):
+        if i == 0:
+            R = np.eye(3)
+            eye = np.zeros(3)
+        else:
+            ax, ay = np.radians(rng.uniform(-max_angle_deg, max_angle_deg, 2))
+            Rx = np.array([[1, 0, 0], [0, math.cos(ax), -math.sin(ax)], [0, math.sin(ax), math.cos(ax)]])
+            Ry = np.array([[math.cos(ay), 0, math.sin(ay)], [0, 1, 0], [-math.sin(ay), 0, math.cos(ay)]])
+            R = Rx @ Ry                       # world -> camera rotation
+            eye = rng.uniform(-max_shift, max_shift, 3)
+        t = -R @ eye
+        cams.append(Camera(width, height, f, f, width / 2.0, height / 2.0, R.astype(np.float32),
+                           t.astype(np.float32), 0.5, 10.0, 0.05))
+    return cams
+
+
 WORKLOADS = {
     "sphere_plane_64": sphere_plane_64,
     "objects_800": objects_800,

@@ -275,3 +275,112 @@ def test_learned_search_equals_infer_then_restricted(subset, crowded):
                               y.view(np.int32) if y.dtype == np.float32 else y), k
     assert int(fa.item()) == int(fb.item()) > 0
     hp.close()
+
+
+# ------------------------------------------- forward-facing scene, full size
+
+def test_forward_1008_restricted_search_sampled():
+    # the proposal path on the 1008 x 756 forward-facing scene (cone radius,
+    # K = 16): GPU inference over the whole frame against the oracle's
+    # network, and the restricted search + fallback of the whole frame, given
+    # oracle-made intervals, bit-exact on sampled rays
+    H = _H()
+    dev = torch.device("cuda", 0)
+    sc = scenes.forward_1008()
+    cam, p = sc.camera, sc.params
+    R = cam.width * cam.height
+    rng = np.random.default_rng(21)
+    rays = np.sort(rng.choice(R, 2500, replace=False)).astype(np.int32)
+    theta = scenes.proposal_params(9, out_bias=(-1.0, 1.5))
+    tab = oracle.build_table(sc.points, cam, p)
+    n_all = OP.counts(tab, cam, np.arange(R))
+    iv_net = OP.intervals(OP.bf16_round(theta)[0], n_all, cam)
+    # sampled rays: intervals cut from the oracle's own plain samples
+    fr = oracle.render(sc.points, sc.feats, cam, p, sc.mlp_dims, sc.mlp_params, rays=rays, nthreads=8)
+    iv = iv_net.astype(np.float32)
+    tn, tf = cam.t_near, cam.t_far
+    kind = rng.integers(0, 5, len(rays))
+    for q, i in enumerate(rays):
+        ns, off = fr["n_s"][q], fr["sample_offset"][q]
+        if kind[q] == 0 or ns == 0:
+            continue                                   # network output
+        s0, s1 = float(fr["t"][off]), float(fr["t"][off + ns - 1])
+        rr = 0.01
+        cut = {1: (s0 - rr, s1 + 10 * rr), 2: (s0 + 1e-4, s1 + 10 * rr), 3: (s0 - rr, s0 + 1e-4),
+               4: (max(tn, s0 - 0.5), min(tf, s1 + 0.5))}[int(kind[q])]
+        lo = min(max(cut[0], tn), tf)
+        iv[i] = (lo, min(max(cut[1], lo), tf))
+    o = oracle.render(sc.points, sc.feats, cam, p, sc.mlp_dims, sc.mlp_params, rays=rays, nthreads=8,
+                      intervals=iv[rays])
+    hp = H.HashPoint(p, dev)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    hp.build_table(t(sc.points), cam, p.r)
+    state = H.ProposalState(dev, init=torch.from_numpy(theta))
+    giv = hp.proposal_infer(None, state.bf16).cpu().numpy().astype(np.float64)
+    assert hp.status() == (0, 0)
+    span = cam.t_far - cam.t_near
+    assert np.abs(giv - iv_net).max() <= 2e-5 * span
+    fb = torch.zeros(1, dtype=torch.int32, device=dev)
+    smp = hp.search_sample_proposal(None, p.K, p.n_max, t(iv), fallback_count=fb)
+    rgb, wsum = hp.aggregate_render(smp, t(sc.feats), sc.mlp_dims, t(sc.mlp_params))
+    g = smp.packed(R)
+    g = {k: (v.numpy() if isinstance(v, torch.Tensor) else v) for k, v in g.items()}
+    st = hp.status()
+    hp.close()
+    gs = {}
+    off = g["sample_offset"]
+    sel = np.concatenate([np.arange(off[i], off[i + 1]) for i in rays]).astype(np.int64)
+    for k in ("n_s", "primary", "cand_count"):
+        gs[k] = g[k][rays]
+    gs["sample_offset"] = np.concatenate([[0], np.cumsum(gs["n_s"])]).astype(np.int64)
+    for k in ("t", "src", "nbr", "nbr_dist", "delta"):
+        gs[k] = g[k][sel]
+    gs["ray"] = np.repeat(np.arange(len(rays)), gs["n_s"]).astype(np.int32)
+    gs["S"] = int(gs["sample_offset"][-1])
+    gs["rgb"] = rgb.cpu().numpy().astype(np.float64)[rays]
+    gs["wsum"] = wsum.cpu().numpy().astype(np.float64)[rays]
+    gs["status"] = st
+    assert_parity(gs, o, p.K)
+    assert np.any(o["cand_count"] < fr["cand_count"]) and int(fb.item()) > 0
+
+
+def test_forward_1008_training_loop_and_miss_rate():
+    # trained on 16 forward-facing views of the 1008 x 756 scene, inferred on
+    # a held-out view at full size with the plain search as the fallback
+    H = _H()
+    dev = torch.device("cuda", 0)
+    sc = scenes.forward_1008()
+    p = sc.params
+    cams = scenes.forward_cameras(17, 4)
+    t = lambda a: torch.from_numpy(a).to(dev)
+    pts_t, feats_t, mlp_t = t(sc.points), t(sc.feats), t(sc.mlp_params)
+    hp = H.HashPoint(p, dev)
+    state = H.ProposalState(dev, seed=0)
+    losses = []
+    for step in range(160):
+        cam = cams[1 + step % 16]
+        hp.build_table(pts_t, cam, p.r)
+        plain = hp.search_sample(None, p.K, p.n_max)
+        hp.proposal_train_step(None, plain, state, lr=3e-3)
+        if step % 16 == 15:
+            l = state.loss.cpu().numpy()
+            losses.append(l[0] / max(l[1], 1))
+    assert hp.status() == (0, 0)
+    # the layered scene's intervals start closer to their targets than the
+    # object scene's: the loss falls by about a third over these steps
+    assert losses[-1] < 0.8 * losses[0], losses
+    cam = cams[0]                                     # held-out: the reference view
+    hp.build_table(pts_t, cam, p.r)
+    iv = hp.proposal_infer(None, state.bf16)
+    g = _frame(hp, pts_t, feats_t, cam, sc.mlp_dims, mlp_t, interval=iv)
+    assert g["status"] == (0, 0)
+    plain = _frame(hp, pts_t, feats_t, cam, sc.mlp_dims, mlp_t)
+    assert np.all((g["n_s"] == 0) <= (plain["n_s"] == 0))
+    hit = np.nonzero(plain["n_s"] > 0)[0]
+    go, po = g["sample_offset"], plain["sample_offset"]
+    same = np.array([np.array_equal(g["src"][go[i]:go[i + 1]], plain["src"][po[i]:po[i + 1]]) for i in hit])
+    miss = 1.0 - same.mean()
+    print(f"forward_1008 proposal miss rate {miss:.4f} on {len(hit)} hit rays; "
+          f"losses {losses[0]:.4f} -> {losses[-1]:.4f}")
+    assert miss < 0.10
+    hp.close()

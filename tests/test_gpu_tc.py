@@ -48,6 +48,13 @@ def _render(sc, decode):
     return st, rgb.cpu().numpy().astype(np.float64), wsum.cpu().numpy().astype(np.float64), out
 
 
+# BF16 decode: (max, mean) absolute colour error bounds against the FP64
+# oracle, about 3x the measured error of each scene (measured: sphere_plane_64
+# 6.1e-4 / 6.5e-5, objects_200 8.3e-4 / 4.5e-5, forward_1008 sampled rays
+# 7.1e-4 / 8.2e-5)
+BF16_BOUND = {"sphere_plane_64": (1.8e-3, 2.0e-4), "objects_200": (2.5e-3, 1.4e-4), "forward_1008": (2.1e-3, 2.5e-4)}
+
+
 @pytest.mark.parametrize("which", ["sphere_plane_64", "objects_200"])
 def test_decode_modes_against_oracle(which):
     H = _H()
@@ -60,11 +67,45 @@ def test_decode_modes_against_oracle(which):
         assert st == (0, 0)
         assert np.array_equal(smp["n_s"].numpy(), o["n_s"])
         err = np.abs(rgb - ref)
-        res[mode] = (err.max(), err.mean())
+        res[mode] = (err.max(), err.mean(), _psnr(rgb, ref))
         if mode != H.DECODE_BF16:
             assert np.all(err <= 1e-4 * np.abs(ref) + 1e-6), (mode, err.max())
             assert np.all(np.abs(ws - o["wsum"]) <= 1e-4 * np.abs(o["wsum"]) + 1e-6)
         else:
-            # BF16 operands (8-bit mantissa): stated error, bounded loosely
-            assert err.max() < 5e-2 and err.mean() < 5e-3, res[mode]
-    print(which, {k: (float(a), float(b)) for k, (a, b) in res.items()})
+            # BF16 operands (8-bit mantissa, FP32 accumulation): about 3x the
+            # measured error of this scene
+            lim_max, lim_mean = BF16_BOUND[which]
+            assert err.max() < lim_max and err.mean() < lim_mean, res[mode]
+    print(which, {k: (float(a), float(b), p) for k, (a, b, p) in res.items()})
+
+
+def _psnr(x, ref):
+    mse = float(np.mean((np.asarray(x, np.float64) - ref) ** 2))
+    return float("inf") if mse == 0 else 10.0 * np.log10(1.0 / mse)
+
+
+def test_forward_1008_decode_modes_sampled():
+    # the forward-facing scene at full size (cone radius, K = 16, 1.5M points):
+    # FP32 and BF16 decodes of the whole frame, checked on sampled rays
+    # against the FP64 oracle
+    H = _H()
+    sc = scenes.forward_1008()
+    R = sc.camera.width * sc.camera.height
+    rays = np.sort(np.random.default_rng(5).choice(R, 3000, replace=False)).astype(np.int32)
+    o = oracle.render(sc.points, sc.feats, sc.camera, sc.params, sc.mlp_dims, sc.mlp_params, rays=rays,
+                      nthreads=8)
+    ref = o["rgb"]
+    assert o["S"] > 1000
+    stats = {}
+    for mode in (H.DECODE_FP32, H.DECODE_BF16):
+        st, rgb, ws, smp = _render(sc, mode)
+        assert st == (0, 0)
+        assert np.array_equal(smp["n_s"].numpy()[rays], o["n_s"])
+        err = np.abs(rgb[rays] - ref)
+        stats[mode] = (float(err.max()), float(err.mean()), _psnr(rgb[rays], ref))
+        if mode == H.DECODE_FP32:
+            assert np.all(err <= 1e-4 * np.abs(ref) + 1e-6), err.max()
+        else:
+            lim_max, lim_mean = BF16_BOUND["forward_1008"]
+            assert err.max() < lim_max and err.mean() < lim_mean, stats[mode]
+    print("forward_1008 (max, mean, PSNR dB vs oracle):", stats)
