@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-proposal", action="store_true")
+    ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--points", type=int, default=1_000_000)
     ap.add_argument("--res", type=int, default=800)
     return ap.parse_args()
@@ -201,50 +202,56 @@ def fp32_peak_tflops(sm_count=148, clock_mhz=2032.0):
 
 # ------------------------------------------------------------------ CPU side
 
-def oracle_frame_rate(pts, feats, params, dims, mlp, cam, stride, offset=0, nthreads=None):
-    """Oracle rays/s for a full frame from one oracle call on every
-    ``stride``-th ray (stride 1 = the whole frame): the call builds the whole
-    table (timed again on its own) and renders R/stride rays, and the frame
-    time is t_build + stride * (t_call - t_build)."""
+def oracle_frame_seconds(pts, feats, params, dims, mlp, cam, nthreads=None):
+    """Seconds the oracle takes for one whole frame (its own table build and
+    every ray of the view, OpenMP over rays on ``nthreads`` host threads)."""
     import oracle
     nthreads = nthreads or os.cpu_count() or 1
-    R = cam.width * cam.height
-    rays = None if stride == 1 else np.arange(offset % stride, R, stride, dtype=np.int32)
-    n = R if rays is None else len(rays)
     t0 = time.perf_counter()
-    oracle.build_table(pts, cam, params)
-    t_build = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    oracle.render(pts, feats, cam, params, dims, mlp, rays=rays, nthreads=nthreads)
-    t_call = time.perf_counter() - t0
-    t_frame = t_call if stride == 1 else t_build + (R / n) * max(t_call - t_build, 1e-9)
-    return R / t_frame, t_build, t_frame, nthreads, t_call
+    oracle.render(pts, feats, cam, params, dims, mlp, nthreads=nthreads)
+    return time.perf_counter() - t0, nthreads
+
+
+def oracle_views_rate(pts, feats, params, dims, mlp, cams):
+    """Oracle rays/s over whole frames of the given views (one frame each)."""
+    secs = []
+    cores = 1
+    for cam in cams:
+        t, cores = oracle_frame_seconds(pts, feats, params, dims, mlp, cam)
+        secs.append(t)
+    R = cams[0].width * cams[0].height
+    return R * len(cams) / sum(secs), secs, cores
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, on the host cores,
+    rendering the same whole frames (views cycled in the same order) that the
+    GPU arm times; rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     pts, feats, params, dims, mlp, cams = workload(args.points, args.res)
     R = args.res * args.res
-    stride = 16
-    for w in range(min(args.warmup, 1)):
-        oracle_frame_rate(pts, feats, params, dims, mlp, cams[w % N_VIEWS], 64)
+    for w in range(args.warmup):
+        oracle_frame_seconds(pts, feats, params, dims, mlp, cams[w % N_VIEWS])
     frames = []
+    cores = 1
+    t_run = time.perf_counter()
     for k in range(args.steps):
-        v, t_build, t_frame, cores, _ = oracle_frame_rate(pts, feats, params, dims, mlp, cams[k % N_VIEWS], stride,
-                                                          offset=k)
-        frames.append(t_frame)
+        t, cores = oracle_frame_seconds(pts, feats, params, dims, mlp, cams[k % N_VIEWS])
+        frames.append(t)
+    t_run = time.perf_counter() - t_run
     t_frame = float(np.mean(frames))
     value = R / t_frame
-    sample = (f"per step: the oracle builds the whole table ({args.points} points) and renders every "
-              f"{stride}th ray of the {R}-ray frame (OpenMP over rays); frame time = build + {stride} x rays")
+    sample = (f"per step: one whole frame -- the oracle builds the table of {args.points} points and renders all "
+              f"{R} rays (OpenMP over rays); views cycled as in the GPU arm")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_frame, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(args.points, args.res, {"parallelism": "cpu oracle, rank 0 only"}),
             "cpu_baseline": {"value": value, "unit": "rays/s", "cores": cores, "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s_timed_region": t_run}
     print(json.dumps(line), flush=True)
 
 
@@ -256,7 +263,7 @@ def psnr(a, b):
     return float("inf") if mse == 0 else 10.0 * math.log10(1.0 / mse)
 
 
-def proposal_section(hp, H, pts_np, feats_np, params, dims, mlp_np, cams, steps, dev, flush):
+def proposal_section(hp, H, pts_np, feats_np, params, dims, mlp_np, cam, train_cams, steps, dev, flush):
     """Learned depth-interval proposal + BF16 decode against the plain FP32
     path: train the proposal on the plain search's intervals of 64 views;
     fit features for 200 steps to a target image (plain FP32 render of view 0
@@ -264,23 +271,22 @@ def proposal_section(hp, H, pts_np, feats_np, params, dims, mlp_np, cams, steps,
     with the library's render + backward; then compare speed and PSNR against
     that target, and judge the proposal's misses with the plain search."""
     import torch
-    R = cams[0].width * cams[0].height
+    R = cam.width * cam.height
     t = lambda a: torch.from_numpy(a).to(dev)
     pts, mlp = t(pts_np), t(mlp_np)
-    # 1) proposal training on 64 views
-    train_cams = scenes.random_sphere_cameras(64, 4.0, 100, width=cams[0].width, height=cams[0].height)
+    # 1) proposal training on the training views (8 passes)
+    n_train = len(train_cams)
     state = H.ProposalState(dev, seed=0)
     t0 = time.perf_counter()
-    for it in range(8 * 64):
-        cam = train_cams[it % 64]
-        hp.build_table(pts, cam, params.r)
+    for it in range(8 * n_train):
+        tc = train_cams[it % n_train]
+        hp.build_table(pts, tc, params.r)
         plain = hp.search_sample(None, params.K, params.n_max)
         hp.proposal_train_step(None, plain, state, lr=3e-3)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     l = state.loss.cpu().numpy()
-    # 2) target and fitted features (view 0)
-    cam = cams[0]
+    # 2) target and fitted features (the evaluation view)
     tgt, _, _ = hp.render(pts, t(scenes.random_features(len(pts_np), 32, 7)), cam, dims, mlp)
     tgt = tgt.clone()
     feats = t(feats_np).clone()
@@ -338,13 +344,89 @@ def proposal_section(hp, H, pts_np, feats_np, params, dims, mlp_np, cams, steps,
             "ms_plain_fp32": ms_plain, "ms_plain_bf16": ms_bf16, "ms_proposal_fp32": ms_prop,
             "psnr_plain_fp32_db": p_plain, "psnr_proposal_bf16_db": p_both, "psnr_drop_db": p_plain - p_both,
             "psnr_bf16_vs_plain_db": psnr(rgb_bf16, rgb_plain), "psnr_proposal_vs_plain_db": psnr(rgb_prop32, rgb_plain),
-            "miss_rate": miss, "fallback_rays": int(fb.item()), "per_kernel_ms": kernels, "train": {"views": 64, "steps": 8 * 64, "seconds": t_train,
+            "miss_rate": miss, "fallback_rays": int(fb.item()), "per_kernel_ms": kernels, "train": {"views": n_train, "steps": 8 * n_train, "seconds": t_train,
                                          "final_loss": float(l[0] / max(l[1], 1))},
             "protocol": "target = plain FP32 render of view 0 with a second feature draw (matches the FP64 "
                         "oracle to 1e-4); features fitted 200 Adam steps (8192 rays/step) with "
                         "hp_aggregate_render_backward; proposal frames: hp_proposal_infer then "
                         "hp_search_sample_proposal; misses = hit rays whose sample sources differ from the "
                         "plain search"}
+
+
+# ------------------------------------------------------ training step (f2)
+
+def train_section(hp, H, pts_np, feats_np, params, dims, mlp_np, cams, steps, dev, flush):
+    """Training step with differentiation: 4 views of the object scene x 4096
+    random pixels per view; per view the forward (table build, search on the
+    listed rays, aggregate + render) and hp_aggregate_render_backward with
+    respect to the point features and positions, for the MSE loss against a
+    target image (the forward with a second feature draw).  Rays/s = 16,384
+    rays per step over the step's device time."""
+    import torch
+    t = lambda a: torch.from_numpy(a).to(dev)
+    pts, feats, mlp = t(pts_np), t(feats_np), t(mlp_np)
+    W, Hh = cams[0].width, cams[0].height
+    n_rays = 4096
+    views = cams[:4]
+    rays = [t(np.sort(scenes.random_rays(W, Hh, n_rays, v)).astype(np.int32)) for v in range(len(views))]
+    feats2 = t(scenes.random_features(len(pts_np), 32, 7))
+    tgt = []
+    for v, cam in enumerate(views):
+        rgb, _, _ = hp.render(pts, feats2, cam, dims, mlp, rays=rays[v])
+        tgt.append(rgb.clone())
+    gf = torch.zeros_like(feats)
+    gp = torch.zeros_like(pts)
+    smp = H.SampleBuffers.allocate(n_rays, params.K, params.n_max, dev)
+
+    def step():
+        gf.zero_()
+        gp.zero_()
+        loss = []
+        for v, cam in enumerate(views):
+            hp.build_table(pts, cam, params.r)
+            hp.search_sample(rays[v], params.K, params.n_max, out=smp)
+            rgb, wsum = hp.aggregate_render(smp, feats, dims, mlp)
+            d = rgb - tgt[v]
+            loss.append((d * d).mean())
+            hp.aggregate_render_backward(smp, pts, feats, dims, mlp, (2.0 / d.numel()) * d, grad_feats=gf,
+                                         grad_points=gp)
+        return loss
+
+    for _ in range(3):
+        step()
+    n = max(5, min(steps, 20))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    for k in range(n):
+        flush.zero_()
+        ev[k][0].record()
+        loss = step()
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / n
+    hp.profile_start(256)
+    step()
+    prof = hp.profile_stop()
+    code, detail = hp.status()
+    if code != 0:
+        raise SystemExit(f"device status after training pass: {H.status_string(code)} ({detail})")
+    per_kernel = {k: round(v[0] / max(v[1], 1), 5) for k, v in prof.items() if v[1]}
+    launches = {k: v[1] for k, v in prof.items() if v[1]}
+    # the last view's samples: the backward's work per launch
+    S = int(smp.sample_offset[n_rays].item())
+    sigma_io = sum(dims[l] * dims[l + 1] for l in range(len(dims) - 1))
+    flops = 4 * S * sigma_io              # forward recompute + back-propagation through the MLP (FP32 SIMT)
+    ms_dec = prof["k_decode_bwd"][0] / max(prof["k_decode_bwd"][1], 1)
+    peak = fp32_peak_tflops(148, 2032.0)
+    achieved = flops / (ms_dec / 1e3) / 1e12
+    return {"value": len(views) * n_rays / (ms / 1e3), "unit": "rays/s", "ms_per_step": ms,
+            "rays_per_step": len(views) * n_rays, "views": len(views), "loss": float(sum(x.item() for x in loss)),
+            "per_kernel_ms": per_kernel, "launches_per_step": launches,
+            "roofline_decode_bwd": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                                    "frac": achieved / peak, "flops_per_launch": flops, "samples_per_launch": S,
+                                    "peak_source": "derived: 148 SMs x 128 FP32 FMA lanes x 2 FLOP x 2032 MHz"},
+            "protocol": "per view: hp_build_table, hp_search_sample on 4096 random pixels, hp_aggregate_render, "
+                        "MSE loss against the forward with a second feature draw, "
+                        "hp_aggregate_render_backward (features and positions); L2 flushed before each step"}
 
 
 # ------------------------------------------------------------------ GPU side
@@ -552,16 +634,43 @@ def run_gpu(args):
     if code != 0:
         raise SystemExit(f"device status after e2e pass: {H.status_string(code)} ({detail})")
 
+    # per-frame statistics of the last timed view (outside the timed region)
+    ns_last = smp.n_s[:R]
+    cc_last = smp.cand_count[:R]
+    stats = {"n_s_histogram": [int(x) for x in torch.bincount(ns_last.long(), minlength=params.n_max + 1).tolist()],
+             "rays_over_candidate_cap": int((cc_last > params.cand_cap).sum().item()),
+             "rays_over_lane_column_48": int((cc_last > 48).sum().item()),
+             "sample_capacity_overflow": bool(S > smp.capacity),
+             "candidates_per_ray_mean": float(cc_last.float().mean().item())}
+
+    train = None
+    if rank == 0 and world == 1 and not args.no_train:
+        train = train_section(hp, H, pts_np, feats_np, params, dims, mlp_np, views, args.steps, dev, flush)
+
     prop = None
     if rank == 0 and world == 1 and not args.no_proposal:
-        prop = proposal_section(hp, H, pts_np, feats_np, params, dims, mlp_np, views, args.steps, dev, flush)
+        train_cams = scenes.random_sphere_cameras(64, 4.0, 100, width=args.res, height=args.res)
+        prop = proposal_section(hp, H, pts_np, feats_np, params, dims, mlp_np, views[0], train_cams, args.steps,
+                                dev, flush)
+        prop["workload"] = f"objects_{args.res} (view 0, held out of the 64 training views)"
+        # the forward-facing scene at 1008 x 756 (cone radius, K = 16): trained on
+        # 64 jittered forward views, evaluated on the reference view
+        fw = scenes.forward_1008()
+        hpf = H.HashPoint(fw.params, dev)
+        fcams = scenes.forward_cameras(65, 4)
+        prop_fw = proposal_section(hpf, H, fw.points, fw.feats, fw.params, fw.mlp_dims, fw.mlp_params, fcams[0],
+                                   fcams[1:], args.steps, dev, flush)
+        prop_fw["workload"] = ("forward_1008: 1.5M points, 1008x756, cone radius (rho 2), K=16, n=8, reference view "
+                               "held out of 64 jittered forward views")
+        hpf.close()
+        prop = {"objects": prop, "forward_1008": prop_fw}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, t_build, t_frame, cores, t_call = oracle_frame_rate(pts_np, feats_np, params, dims, mlp_np, cams[0], 1)
+        v, secs, cores = oracle_views_rate(pts_np, feats_np, params, dims, mlp_np, cams)
         cpu = {"value": v, "unit": "rays/s", "cores": cores, "kind": "oracle",
-               "sample": f"one whole frame (view 0: table of {N} points + all {R} rays, OpenMP over rays), "
-                         f"{t_frame:.2f} s"}
+               "sample": f"one whole frame of each of the {len(cams)} views (table of {N} points + all {R} rays, "
+                         f"OpenMP over rays), {sum(secs):.2f} s in total"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
@@ -572,7 +681,7 @@ def run_gpu(args):
                                        "samples_last_frame": S, "visible_points_last_frame": Nv,
                                        "buckets": P, "unique_points_gathered": U}),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "proposal_bf16": prop,
+                "proposal_bf16": prop, "train_step": train, "frame_stats": stats,
                 "clocks": clk, "per_kernel_ms": {k: round(v["ms_avg"], 5) for k, v in per_kernel.items()},
                 "wall_s_timed_region": t_wall}
         print(json.dumps(line), flush=True)
