@@ -477,6 +477,27 @@ hp_status hp_table_copy(const hp_ctx *ctx, uint32_t *d_start, float *d_points, v
     return HP_OK;
 }
 
+// Most candidates the selection (Sec. 3.3) can process on a ray: every
+// processed candidate multiplies T by 1 - alpha_j <= 1 - alpha_min, alpha_min
+// = gamma exp(-d_max^2 / beta^2) with d_max the largest radius a neighbour can
+// lie within (the pseudo-UDF d_j is a mean of such distances), and the
+// selection stops once gamma T <= eps_w.  The margins cover float32 rounding
+// and exp32's error.  0 when the bound exceeds kPruneMax (or does not exist).
+static int selection_bound(const hp_config &cfg, int mode, float r, float rdd, float t_far)
+{
+    const double g = cfg.gamma, b2 = cfg.beta2, eps = cfg.eps_w;
+    if (!(g > 0.0) || !(b2 > 0.0) || !(eps > 0.0)) return 0;
+    const double dmax = (mode == HP_RADIUS_FIXED ? (double)r : (double)t_far * (double)rdd) * 1.001;
+    const double amin = g * std::exp(-dmax * dmax / b2) * (1.0 - 1e-4);
+    if (!(amin > 0.0) || !(amin < 1.0)) return 0;
+    double T = 1.0;
+    for (int m = 1; m <= kPruneMax; ++m) {
+        T *= (1.0 - amin) * (1.0 + 1e-5);
+        if (g * T <= eps * (1.0 - 1e-5)) return m;
+    }
+    return 0;
+}
+
 static hp_status search_impl(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n_rays, int32_t K, int32_t n_samples,
                              const hp_samples *out, const float *d_interval, const uint16_t *d_prop_w,
                              uint32_t *d_fallback_count, void *stream)
@@ -507,6 +528,7 @@ static hp_status search_impl(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n
         a.cam = ctx->cam; a.mode = ctx->cfg.radius_mode; a.r = ctx->r; a.rdd = ctx->rdd; a.h = ctx->h;
         a.Wp = ctx->Wp; a.gamma = ctx->cfg.gamma; a.beta2 = ctx->cfg.beta2; a.eps_w = ctx->cfg.eps_w;
         a.gap_k = ctx->cfg.gap_k; a.cand_cap = ctx->cfg.cand_cap; a.K = K; a.n_max = n_samples;
+        a.prune_m = selection_bound(ctx->cfg, ctx->cfg.radius_mode, ctx->r, ctx->rdd, ctx->cam.t_far);
         a.start = ctx->start; a.spts = ctx->spts; a.rays = d_ray_pixels; a.R = n_rays;
         a.raytab = ctx->raytab; a.raytab_stale = ctx->raytab_valid ? 0 : 1;
         a.n_s = out->n_s; a.primary = out->primary; a.cand_count = out->cand_count;

@@ -62,6 +62,9 @@ constexpr int kLaneCap = 48;
 // Slots per ray of the point-major pass: the lane search reads rays of up to
 // kLaneCap candidates from them, the warp-per-ray search rays of up to kPmCap.
 constexpr int kPmCap = 128;
+// Most candidates the selection can process for which the lane search prunes
+// its column (prune_m; larger bounds switch the pruning off).
+constexpr int kPruneMax = 4;
 
 struct SearchArgs {
     Cam cam;                 // raytab is (re)computed from cam when raytab_stale
@@ -74,6 +77,7 @@ struct SearchArgs {
     int cand_cap;
     int K;
     int n_max;
+    int prune_m;             // at most this many candidates are processed per ray (0: no bound used)
     const uint32_t *start;
     const float4 *spts;
     float4 *raytab;          // [W*H] per-pixel (dx, dy, dz, cone c)

@@ -594,8 +594,6 @@ __host__ __device__ constexpr int lane_blocks_per_sm(int KB) { return KB <= 8 ? 
 
 __host__ __device__ constexpr size_t lane_smem_bytes() { return (size_t)kLaneWarps * kLaneCap * 32 * 8; }
 
-__device__ __forceinline__ int point_id(const SearchArgs &a, uint32_t idx) { return __float_as_int(__ldg(&a.spts[idx].w)); }
-
 // One ray on one lane; lt / li point at this lane's column (depth lt[c * 32],
 // table index li[c * 32]).  Returns false when the ray must go to the
 // warp-per-ray search.
@@ -660,33 +658,112 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
     // the smallest appended depth and its entry (candidate 0 unless another
     // entry has the same depth: then the ids decide, by a scan below)
     float t_lo = __int_as_float(0x7f800000);
-    uint32_t i_lo = 0;
+    int c_lo = 0;                              // its column entry
     bool lo_tie = false;
+    int n_col = 0;                             // entries in the column (the walk: every accepted point)
     if constexpr (kPointMajor) {
-        // the pass left this ray's accepted points (any order) in its slots
+        // the pass left this ray's accepted points (any order) in its slots;
+        // slots that overflowed hold an arbitrary subset: the warp search walks
         const uint32_t cnt = __ldg(a.pm_cnt + pix);
-        if (cnt > (uint32_t)kLaneCap) return false;   // more than the column holds
-        // 16-byte loads, kPtBatch of them in flight (a ray's slots are 16-byte aligned)
+        if (cnt > (uint32_t)kPmCap) return false;
+        // Candidates the selection can reach: it processes at most prune_m
+        // candidates (every one multiplies T by at most 1 - alpha_min, and it
+        // stops once gamma T <= eps_w), and a processed candidate's
+        // neighbourhood lies within lim of its depth; so only the depths up
+        // to the prune_m-th smallest plus that candidate's lim matter, a
+        // prefix of the (t, id) order.  The column keeps that prefix.
+        auto threshold = [&](float tl) {
+            const float rl = radius_at(a.mode, a.r, ray, tl);
+            return tl + (rl * 1.001f + 1e-5f * (1.0f + tl)) * 1.01f;
+        };
+        auto top_m = [&](float (&tm)[kPruneMax], float x) {
+#pragma unroll
+            for (int q = 0; q < kPruneMax; ++q) {
+                const float lo = fminf(tm[q], x);
+                x = fmaxf(tm[q], x);
+                tm[q] = lo;
+            }
+        };
+        auto mth = [&](const float (&tm)[kPruneMax]) {
+            float tl = tm[0];
+#pragma unroll
+            for (int q = 1; q < kPruneMax; ++q)
+                if (q < a.prune_m) tl = tm[q];
+            return tl;
+        };
+        const bool prune = a.prune_m > 0 && cnt > (uint32_t)a.prune_m;
+        float thr = __int_as_float(0x7f800000);
+        auto keep = [&](float t, uint32_t ix) {
+            lt[n_col * 32] = t;
+            li[n_col * 32] = ix;
+            t_max = fmaxf(t_max, t);
+            lo_tie = t == t_lo ? true : (t < t_lo ? false : lo_tie);
+            if (t < t_lo) {
+                t_lo = t;
+                c_lo = n_col;
+            }
+            ++n_col;
+        };
         const uint4 *sl = reinterpret_cast<const uint4 *>(a.pm_slot + (int64_t)pix * kPmCap);
-        for (uint32_t c0 = 0; c0 < cnt; c0 += 2 * kPtBatch) {
-            uint4 e[kPtBatch];
+        constexpr int kSlotBatch = 4;        // 16-byte loads in flight (a ray's slots are 16-byte aligned)
+        if (cnt <= (uint32_t)kLaneCap) {
+            // one pass: every slot into the column (the threshold on the way),
+            // then the column compacted to the reachable prefix in place
+            float tm[kPruneMax];
 #pragma unroll
-            for (int k = 0; k < kPtBatch; ++k)
-                if (c0 + 2 * k < cnt) e[k] = __ldg(sl + (c0 >> 1) + k);
+            for (int q = 0; q < kPruneMax; ++q) tm[q] = thr;
+            for (uint32_t c0 = 0; c0 < cnt; c0 += 2 * kSlotBatch) {
+                uint4 e[kSlotBatch];
 #pragma unroll
-            for (int k = 0; k < 2 * kPtBatch; ++k) {
-                const uint32_t c = c0 + k;
-                if (c >= cnt) break;
-                const uint32_t tb = (k & 1) ? e[k >> 1].z : e[k >> 1].x;
-                const uint32_t ix = (k & 1) ? e[k >> 1].w : e[k >> 1].y;
-                const float t = __uint_as_float(tb);
-                lt[c * 32] = t;
-                li[c * 32] = ix;
-                t_max = fmaxf(t_max, t);
-                lo_tie = t == t_lo ? true : (t < t_lo ? false : lo_tie);
-                if (t < t_lo) {
-                    t_lo = t;
-                    i_lo = ix;
+                for (int k = 0; k < kSlotBatch; ++k)
+                    if (c0 + 2 * k < cnt) e[k] = __ldg(sl + (c0 >> 1) + k);
+#pragma unroll
+                for (int k = 0; k < 2 * kSlotBatch; ++k) {
+                    const uint32_t c = c0 + k;
+                    if (c >= cnt) break;
+                    const float t = __uint_as_float((k & 1) ? e[k >> 1].z : e[k >> 1].x);
+                    lt[c * 32] = t;
+                    li[c * 32] = (k & 1) ? e[k >> 1].w : e[k >> 1].y;
+                    if (prune) top_m(tm, t);
+                }
+            }
+            if (prune) thr = threshold(mth(tm));
+            for (uint32_t c = 0; c < cnt; ++c) {
+                const float t = lt[c * 32];
+                if (!(t <= thr)) continue;
+                keep(t, li[c * 32]);                 // n_col <= c: in place
+            }
+        } else {
+            // more than a column holds: the slots twice (the threshold first)
+            if (prune) {
+                float tm[kPruneMax];
+#pragma unroll
+                for (int q = 0; q < kPruneMax; ++q) tm[q] = thr;
+                for (uint32_t c0 = 0; c0 < cnt; c0 += 2 * kSlotBatch) {
+                    uint4 e[kSlotBatch];
+#pragma unroll
+                    for (int k = 0; k < kSlotBatch; ++k)
+                        if (c0 + 2 * k < cnt) e[k] = __ldg(sl + (c0 >> 1) + k);
+#pragma unroll
+                    for (int k = 0; k < 2 * kSlotBatch; ++k) {
+                        if (c0 + k >= cnt) break;
+                        top_m(tm, __uint_as_float((k & 1) ? e[k >> 1].z : e[k >> 1].x));
+                    }
+                }
+                thr = threshold(mth(tm));
+            }
+            for (uint32_t c0 = 0; c0 < cnt; c0 += 2 * kSlotBatch) {
+                uint4 e[kSlotBatch];
+#pragma unroll
+                for (int k = 0; k < kSlotBatch; ++k)
+                    if (c0 + 2 * k < cnt) e[k] = __ldg(sl + (c0 >> 1) + k);
+#pragma unroll
+                for (int k = 0; k < 2 * kSlotBatch; ++k) {
+                    if (c0 + k >= cnt) break;
+                    const float t = __uint_as_float((k & 1) ? e[k >> 1].z : e[k >> 1].x);
+                    if (!(t <= thr)) continue;
+                    if (n_col == kLaneCap) return false;   // more than the column holds
+                    keep(t, (k & 1) ? e[k >> 1].w : e[k >> 1].y);
                 }
             }
         }
@@ -742,22 +819,27 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
                     }
                     lt[total * 32] = t;
                     li[total * 32] = i0 + k;
-                    ++total;
                     t_max = fmaxf(t_max, t);
                     lo_tie = t == t_lo ? true : (t < t_lo ? false : lo_tie);
                     if (t < t_lo) {
                         t_lo = t;
-                        i_lo = i0 + k;
+                        c_lo = total;
                     }
+                    ++total;
                 }
             }
         }
     }
-    if (total > a.cand_cap) {                  // the cap rule is the warp search's
+    if constexpr (!kPointMajor) n_col = total;
+    // the cap rule is the warp search's (a pruned column is a prefix of the
+    // (t, id) order: within the cap when it fits)
+    if (n_col > a.cand_cap) {
         if (kLearned) a.interval_buf[ri] = iv;
         return false;
     }
-    const int C = total;
+    const int C = n_col;
+    // the position (and id) of column entry c
+    auto pos_of = [&](int c) -> float4 { return __ldg(a.spts + li[c * 32]); };
 
     // ---- adaptive primary surface sampling, candidates in (t, id) order.
     // Each pass over the column forms candidate j's neighbourhood and, in the
@@ -774,27 +856,26 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
     const float kInf = __int_as_float(0x7f800000);
     // candidate 0: the smallest (t, id)
     float tq = t_lo;
-    uint32_t iq = i_lo;
+    int cq = c_lo;                             // column entry of the next candidate
     int idq = -2;                              // -2: not looked up yet
     if (lo_tie) tq = kInf;
     for (int c = 0; lo_tie && c < C; ++c) {
         const float tc = lt[c * 32];
         if (tc > tq) continue;
-        const uint32_t ic = li[c * 32];
         if (tc == tq) {
-            if (idq == -2) idq = point_id(a, iq);
-            const int idc = point_id(a, ic);
+            if (idq == -2) idq = __float_as_int(pos_of(cq).w);
+            const int idc = __float_as_int(pos_of(c).w);
             if (idc >= idq) continue;
             idq = idc;
         } else {
             idq = -2;
         }
         tq = tc;
-        iq = ic;
+        cq = c;
     }
     for (int j = 0; j < C; ++j) {
         const float tj = tq;
-        const float4 pj = __ldg(a.spts + iq);
+        const float4 pj = pos_of(cq);
         const int idj = __float_as_int(pj.w);
         if (jstar >= 0 && a.gap_k > 0.0f) {
             const float gap = dsub(tj, t_prev);
@@ -818,40 +899,31 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
         constexpr int kNb = 4;
         for (int c0 = 0; c0 < C; c0 += kNb) {
             float tcs[kNb];
-            uint32_t ics[kNb];
             float4 P[kNb];
 #pragma unroll
-            for (int k = 0; k < kNb; ++k) {
-                tcs[k] = kInf;
-                ics[k] = 0;
-                if (c0 + k < C) {
-                    tcs[k] = lt[(c0 + k) * 32];
-                    ics[k] = li[(c0 + k) * 32];
-                }
-            }
+            for (int k = 0; k < kNb; ++k) tcs[k] = c0 + k < C ? lt[(c0 + k) * 32] : kInf;
 #pragma unroll
             for (int k = 0; k < kNb; ++k)
-                if (c0 + k < C && fabsf(tcs[k] - tj) <= lim) P[k] = __ldg(a.spts + ics[k]);
+                if (c0 + k < C && fabsf(tcs[k] - tj) <= lim) P[k] = pos_of(c0 + k);
 #pragma unroll
             for (int k = 0; k < kNb; ++k) {
                 if (c0 + k >= C) break;
                 const float tc = tcs[k];
-                const uint32_t ic = ics[k];
                 // next candidate
                 if (tc >= tj && tc <= tq) {
                     bool take = true;
                     int idc = -2;
                     if (tc == tj || tc == tq) {
-                        idc = point_id(a, ic);
+                        idc = __float_as_int(pos_of(c0 + k).w);
                         if (tc == tj && idc <= idj) take = false;
                         if (take && tc == tq) {
-                            if (idq == -2) idq = point_id(a, iq);
+                            if (idq == -2) idq = __float_as_int(pos_of(cq).w);
                             if (idc >= idq) take = false;
                         }
                     }
                     if (take) {
                         tq = tc;
-                        iq = ic;
+                        cq = c0 + k;
                         idq = idc;
                     }
                 }
@@ -959,6 +1031,7 @@ __global__ void __launch_bounds__(kLaneWarps * 32, lane_blocks_per_sm(KB)) k_sea
     // this lane's candidate list: depth lt[c * 32] and table index li[c * 32]
     float *lt = reinterpret_cast<float *>(smem) + warp * (kLaneCap * 32) + lane;
     uint32_t *li = reinterpret_cast<uint32_t *>(smem) + kLaneWarps * kLaneCap * 32 + warp * (kLaneCap * 32) + lane;
+
     // proposal weights (FP32 copy of the BF16 ones) behind the columns
     float *pw = nullptr;
     if constexpr (kLearned) {
