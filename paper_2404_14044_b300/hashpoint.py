@@ -10,7 +10,9 @@ from __future__ import annotations
 
 import ctypes as C
 import dataclasses
+import json
 import os
+import struct
 from typing import Dict, Optional, Sequence
 
 import torch
@@ -478,9 +480,57 @@ class ProposalState:
         self.m = torch.zeros_like(self.params)
         self.v = torch.zeros_like(self.params)
         self.grad = torch.zeros_like(self.params)
-        self.bf16 = self.params.to(torch.bfloat16).view(torch.int16).contiguous()
+        self.refresh_bf16()
         self.loss = torch.zeros(2, device=device)
         self.step = 0
+
+    def refresh_bf16(self):
+        """The inference copy: the FP32 weights rounded to bfloat16 (nearest even)."""
+        self.bf16 = self.params.to(torch.bfloat16).view(torch.int16).contiguous()
+
+    # Checkpoint file: 8-byte magic, little-endian uint64 header length, a JSON
+    # header, then the FP32 arrays it lists (parameters, Adam's m and v), raw
+    # little-endian, in that order.  Enough to resume training (Adam's step
+    # count is in the header) or to serve the network (its BF16 copy is
+    # re-derived from the parameters on load).
+    MAGIC = b"HPPROP\x00\x01"
+
+    def save(self, path: str) -> None:
+        header = {"format": "hashpoint-proposal", "version": 1, "layers": [PROP_BINS, 32, 32, 2],
+                  "n_params": PROP_PARAMS, "dtype": "float32", "byteorder": "little", "step": int(self.step),
+                  "arrays": ["params", "m", "v"]}
+        raw = json.dumps(header, sort_keys=True).encode()
+        tmp = path + ".tmp"
+        with open(tmp, "wb") as f:
+            f.write(self.MAGIC)
+            f.write(struct.pack("<Q", len(raw)))
+            f.write(raw)
+            for t in (self.params, self.m, self.v):
+                f.write(t.detach().to("cpu", torch.float32).contiguous().numpy().astype("<f4").tobytes())
+        os.replace(tmp, path)
+
+    @classmethod
+    def load(cls, path: str, device) -> "ProposalState":
+        with open(path, "rb") as f:
+            blob = f.read()
+        if blob[:8] != cls.MAGIC or len(blob) < 16:
+            raise ValueError(f"{path}: not a proposal checkpoint")
+        (n,) = struct.unpack("<Q", blob[8:16])
+        header = json.loads(blob[16:16 + n].decode())
+        if header.get("format") != "hashpoint-proposal" or header.get("version") != 1 or \
+                header.get("n_params") != PROP_PARAMS or header.get("dtype") != "float32":
+            raise ValueError(f"{path}: unsupported proposal checkpoint header {header}")
+        body = blob[16 + n:]
+        if len(body) != 3 * 4 * PROP_PARAMS:
+            raise ValueError(f"{path}: expected {3 * 4 * PROP_PARAMS} bytes of arrays, found {len(body)}")
+        import numpy as np
+        arr = np.frombuffer(body, dtype="<f4").reshape(3, PROP_PARAMS)
+        st = cls.__new__(cls)
+        st._set(device, torch.from_numpy(arr[0].copy()))
+        st.m = torch.from_numpy(arr[1].copy()).to(device).contiguous()
+        st.v = torch.from_numpy(arr[2].copy()).to(device).contiguous()
+        st.step = int(header["step"])
+        return st
 
 
 class RenderFunction(torch.autograd.Function):
