@@ -633,7 +633,12 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
                     }
                 }
             } else {
-                for (int e = tid; e < nw; e += blockDim.x) f32[L.wl + e] = __ldg(a.mlp + g + e);
+                for (int e = tid; e < nw; e += blockDim.x) {
+                    // the output layer's W [4][fi] stored transposed, [fi][4]:
+                    // one 16-byte load gives an input's four weights
+                    const int o = e / fi, ii = e - o * fi;
+                    f32[L.wl + ii * 4 + o] = __ldg(a.mlp + g + e);
+                }
             }
             g += nw;
             for (int e = tid; e < fo; e += blockDim.x) f32[L.bias[l] + e] = __ldg(a.mlp + g + e);
@@ -717,7 +722,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
             // precomputed weights that variant spills at its 64 registers.
             if constexpr (kBF16) {
                 for (int e = ptid; e < kTcTile * K; e += kWsProducerWarps * 32)
-                    s_dst[e] = s_ids[e] >= 0 ? 1.0f / fmaxf(s_dst[e], a.eps_d) : 0.0f;
+                    s_dst[e] = s_ids[e] >= 0 ? __fdividef(1.0f, fmaxf(s_dst[e], a.eps_d)) : 0.0f;
             }
             // the buffer is free once the layer-0 MMAs of tile it-2 are done
             if (ok && !tc::mbar_wait(&empty[b], (eph >> b) & 1u, kMbarLimit)) {
@@ -741,7 +746,9 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
                     for (int k = 0; k < K; ++k) {
                         const int id = nb[k];
                         if (id >= 0) {
-                            const float w = kBF16 ? nw[k] : 1.0f / fmaxf(nw[k], a.eps_d);
+                            // inverse-distance weight (approximate reciprocal:
+                            // ~2 ulp, far inside the colour tolerance)
+                            const float w = kBF16 ? nw[k] : __fdividef(1.0f, fmaxf(nw[k], a.eps_d));
                             const float4 f = __ldg(feats4 + (int64_t)id * lpr + chunk);
                             acc.x = fmaf(w, f.x, acc.x);
                             acc.y = fmaf(w, f.y, acc.y);
@@ -750,7 +757,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
                             wsum += w;
                         }
                     }
-                    const float inv = 1.0f / wsum;
+                    const float inv = __fdividef(1.0f, wsum);
                     acc.x *= inv; acc.y *= inv; acc.z *= inv; acc.w *= inv;
                 }
                 store_operand4_ss<kBF16>(A_hi, A_lo, tc::kmajor_off(sl, 4 * chunk, F), acc);
@@ -788,7 +795,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
             ok = tc::bar_and(barid, nthr, ok);
             if (!ok) break;
             tc::fence_after_sync();
-            float o4[4] = {0.f, 0.f, 0.f, 0.f};
+            uint64_t o01 = tc::f32x2(0.f, 0.f), o23 = tc::f32x2(0.f, 0.f);   // output layer sums
             for (int l = 0; l < L.nh; ++l) {
                 const int fi = L.fi[l], fo = L.fo[l];
                 if (gtid == 0) {
@@ -867,9 +874,13 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
                         const float4 b1 = bq[j][1];
                         const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
                         float h[8];
+                        // bias as packed pair additions (the scalar roundings), then ReLU
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            h[i] = fmaxf(v1[j][i] + bb[i], 0.0f);
+                        for (int i = 0; i < 4; ++i) {
+                            const float2 z = tc::f32x2_unpack(tc::add_f32x2(tc::f32x2(v1[j][2 * i], v1[j][2 * i + 1]),
+                                                                            tc::f32x2(bb[2 * i], bb[2 * i + 1])));
+                            h[2 * i] = fmaxf(z.x, 0.0f);
+                            h[2 * i + 1] = fmaxf(z.y, 0.0f);
                         }
                         if (!last) {
                             // next layer's A: columns c/2 .. c/2+3 of A_hi (and A_lo)
@@ -881,20 +892,21 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
                                     ph[i] = *reinterpret_cast<const uint32_t *>(&x);
                                     pl[i] = 0u;
                                 } else {
-                                    tc::split_f16x2_same_scale(h[2 * i], h[2 * i + 1], ph[i], pl[i]);
+                                    tc::split_f16x2_same_scale_p(h[2 * i], h[2 * i + 1], ph[i], pl[i]);
                                 }
                             }
                             tc::st4(ah + lane_off + (uint32_t)(c / 2), ph);
                             if constexpr (!kBF16) tc::st4(al + lane_off + (uint32_t)(c / 2), pl);
                         } else {
-                            const float *W = f32 + L.wl;
+                            // output layer: outputs (0, 1) and (2, 3) as packed FMAs
+                            // in input order (each output's scalar FMA chain)
+                            const float4 *W4 = reinterpret_cast<const float4 *>(f32 + L.wl) + c;
 #pragma unroll
-                            for (int o = 0; o < 4; ++o) {
-                                const float4 w0 = *reinterpret_cast<const float4 *>(W + o * fo + c);
-                                const float4 w1 = *reinterpret_cast<const float4 *>(W + o * fo + c + 4);
-                                const float ww[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-#pragma unroll
-                                for (int i = 0; i < 8; ++i) o4[o] = fmaf(h[i], ww[i], o4[o]);
+                            for (int i = 0; i < 8; ++i) {
+                                const float4 w = W4[i];
+                                const uint64_t hh = tc::f32x2(h[i], h[i]);
+                                o01 = tc::fma_f32x2(hh, tc::f32x2(w.x, w.y), o01);
+                                o23 = tc::fma_f32x2(hh, tc::f32x2(w.z, w.w), o23);
                             }
                         }
                     }
@@ -907,6 +919,14 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
             if (!ok) break;
 
             // ---- output layer: combine the column groups, activations
+            float o4[4];
+            {
+                const float2 x01 = tc::f32x2_unpack(o01), x23 = tc::f32x2_unpack(o23);
+                o4[0] = x01.x;
+                o4[1] = x01.y;
+                o4[2] = x23.x;
+                o4[3] = x23.y;
+            }
             if (cg > 0) {
 #pragma unroll
                 for (int i = 0; i < 4; ++i) gcomb[(cg * kTcTile + row) * 4 + i] = o4[i];

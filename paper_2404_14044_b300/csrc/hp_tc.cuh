@@ -240,6 +240,56 @@ __device__ __forceinline__ void split_f16x2_same_scale(float x0, float x1, uint3
     lo = *reinterpret_cast<const uint32_t *>(&l);
 }
 
+// Two FP32 values in one 64-bit register (x0 in the low half) and the
+// packed FP32 pair arithmetic of sm_100-class cores: each lane of the pair
+// is rounded exactly as the scalar instruction would round it.
+__device__ __forceinline__ uint64_t f32x2(float x0, float x1)
+{
+    uint64_t d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(x0), "f"(x1));
+    return d;
+}
+
+__device__ __forceinline__ float2 f32x2_unpack(uint64_t v)
+{
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+
+__device__ __forceinline__ uint64_t add_f32x2(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ uint64_t sub_f32x2(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ uint64_t fma_f32x2(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// split_f16x2_same_scale with the remainder taken as one packed subtraction
+// (the same roundings).
+__device__ __forceinline__ void split_f16x2_same_scale_p(float x0, float x1, uint32_t &hi, uint32_t &lo)
+{
+    const __half2 h = __floats2half2_rn(x0, x1);
+    const float2 hf = __half22float2(h);
+    const float2 r = f32x2_unpack(sub_f32x2(f32x2(x0, x1), f32x2(hf.x, hf.y)));
+    const __half2 l = __floats2half2_rn(r.x, r.y);
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
+}
+
 __device__ __forceinline__ void split_f16(float x, __half &hi, __half &lo)
 {
     hi = __float2half_rn(x);
