@@ -159,12 +159,12 @@ def algorithmic(kernel, N, Nv, P, R, S, K, F, dims, U, tensor_decode=True):
 NCU_TRAFFIC = {
     # the search stage's time (k_search_select) covers the point-major pass
     # (k_search_splat) and the selection launch: their bytes are summed
-    "k_search_select": {"bytes": 35589888 + 15760640 + 87729664 + 31665408,
+    "k_search_select": {"bytes": 35490816 + 15449600 + 93925632 + 34627584,
                         "sources": ("hp_search.cu", "hp_common.cuh", "hp_kernels.cuh"),
-                        "sha256": "41835b4f320036211d61a1648223f30ad5e32a442799dcf5b7052659ad6a282d"},
-    "k_aggregate_decode": {"bytes": 78089984 + 3145216,
+                        "sha256": "72c7cbd28da0f45a05ecfbdf3e2da4bb96cbdaf0a7a8b62995217d639d98322c"},
+    "k_aggregate_decode": {"bytes": 78086144 + 828416,
                            "sources": ("hp_decode_tc.cu", "hp_tc.cuh", "hp_common.cuh", "hp_kernels.cuh"),
-                           "sha256": "aaa267858a72c30cfcb4365d993ed741f938feb57b4ced6a55e42a5ee326841d"},
+                           "sha256": "5e1cb08795708bf94bc0b8bb758e171f5a804b83e9df1544c60bfb9bac1a4e0f"},
 }
 
 
