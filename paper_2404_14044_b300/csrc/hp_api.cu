@@ -548,7 +548,8 @@ static hp_status search_impl(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n
         a.fallback_count = a.ticket + 1;
         a.wide = reinterpret_cast<int32_t *>(base + o);      o += al(4 * (size_t)n_rays);
         a.interval_buf = reinterpret_cast<float2 *>(base + o); o += al(8 * (size_t)n_rays);
-        a.pm_slot = reinterpret_cast<uint2 *>(base + o);
+        a.pm_t = reinterpret_cast<float *>(base + o);
+        a.pm_i = reinterpret_cast<uint32_t *>(base + o + 4 * (size_t)kPmCap * (size_t)n_rays);
         a.pcell = reinterpret_cast<const uint32_t *>(ctx->keyrank);
         a.n_points = ctx->N;
         a.prop_w = d_prop_w;

@@ -90,7 +90,8 @@ struct SearchArgs {
     const uint32_t *pcell;   // bucket of each sorted point (whole frames: point-major candidate pass)
     int64_t n_points;        // points given to the table build (bound of the tabled ones)
     uint32_t *pm_cnt;        // [W*H] candidates each pixel's ray received from the point-major pass
-    uint2 *pm_slot;          // [W*H x kPmCap] (t bits, table index) of those candidates
+    float *pm_t;             // [W*H x kPmCap] depths t of those candidates
+    uint32_t *pm_i;          // [W*H x kPmCap] their table indices
     int32_t *fallback;       // rays whose restricted search kept nothing (original indices)
     uint32_t *fallback_count;
     int32_t *wide;           // rays with more candidates than a lane holds (original indices)

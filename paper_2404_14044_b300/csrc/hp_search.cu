@@ -146,7 +146,10 @@ __global__ void __launch_bounds__(256) k_search_splat(const SearchArgs a)
             float t;
             if (!accept_point(a, ray, p, a.cam.t_near, a.cam.t_far, t)) continue;
             const uint32_t pos = atomicAdd(a.pm_cnt + pix, 1u);
-            if (pos < (uint32_t)kPmCap) a.pm_slot[pix * kPmCap + pos] = make_uint2(__float_as_uint(t), (uint32_t)i);
+            if (pos < (uint32_t)kPmCap) {
+                a.pm_t[pix * kPmCap + pos] = t;
+                a.pm_i[pix * kPmCap + pos] = (uint32_t)i;
+            }
         }
     }
 }
@@ -376,19 +379,22 @@ __device__ __forceinline__ void wide_ray(const SearchArgs &a, const float2 *inte
     uint64_t ckey[4];
     float4 cpos[4];
     if (from_slots) {
-        // (t bits, table index) from the slots, the positions from the table
-        const uint2 *sl = a.pm_slot + (int64_t)pix * kPmCap;
-        uint2 e2[4];
+        // depths and table indices from the slots, the positions from the table
+        const float *st = a.pm_t + (int64_t)pix * kPmCap;
+        const uint32_t *si = a.pm_i + (int64_t)pix * kPmCap;
+        float et[4];
+        uint32_t ei[4];
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const int e = lane + 32 * m;
-            e2[m] = e < C ? __ldg(sl + e) : make_uint2(0u, 0u);
+            et[m] = e < C ? __ldg(st + e) : 0.0f;
+            ei[m] = e < C ? __ldg(si + e) : 0u;
         }
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const int e = lane + 32 * m;
-            cpos[m] = e < C ? __ldg(a.spts + e2[m].y) : make_float4(0.f, 0.f, 0.f, 0.f);
-            ckey[m] = e < C ? ((uint64_t)e2[m].x << 32) | (uint32_t)__float_as_int(cpos[m].w) : ~0ull;
+            cpos[m] = e < C ? __ldg(a.spts + ei[m]) : make_float4(0.f, 0.f, 0.f, 0.f);
+            ckey[m] = e < C ? ((uint64_t)__float_as_uint(et[m]) << 32) | (uint32_t)__float_as_int(cpos[m].w) : ~0ull;
         }
         total = C;
     } else {
@@ -704,68 +710,70 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
             }
             ++n_col;
         };
-        const uint4 *sl = reinterpret_cast<const uint4 *>(a.pm_slot + (int64_t)pix * kPmCap);
-        constexpr int kSlotBatch = 4;        // 16-byte loads in flight (a ray's slots are 16-byte aligned)
-        if (cnt <= (uint32_t)kLaneCap) {
-            // one pass: every slot into the column (the threshold on the way),
-            // then the column compacted to the reachable prefix in place
+        // the depths first (16-byte loads of four, kSlotBatch in flight; a
+        // ray's slots are 16-byte aligned), the table indices of the kept
+        // candidates after: most candidates lie beyond the reachable prefix
+        const float4 *st = reinterpret_cast<const float4 *>(a.pm_t + (int64_t)pix * kPmCap);
+        const uint32_t *si = a.pm_i + (int64_t)pix * kPmCap;
+        constexpr int kSlotBatch = 4;
+        const bool in_col = cnt <= (uint32_t)kLaneCap;   // the depths fit the column
+        {
             float tm[kPruneMax];
 #pragma unroll
             for (int q = 0; q < kPruneMax; ++q) tm[q] = thr;
-            for (uint32_t c0 = 0; c0 < cnt; c0 += 2 * kSlotBatch) {
-                uint4 e[kSlotBatch];
+            for (uint32_t c0 = 0; c0 < cnt; c0 += 4 * kSlotBatch) {
+                float4 e[kSlotBatch];
 #pragma unroll
                 for (int k = 0; k < kSlotBatch; ++k)
-                    if (c0 + 2 * k < cnt) e[k] = __ldg(sl + (c0 >> 1) + k);
+                    if (c0 + 4 * k < cnt) e[k] = __ldg(st + (c0 >> 2) + k);
 #pragma unroll
-                for (int k = 0; k < 2 * kSlotBatch; ++k) {
+                for (int k = 0; k < 4 * kSlotBatch; ++k) {
                     const uint32_t c = c0 + k;
                     if (c >= cnt) break;
-                    const float t = __uint_as_float((k & 1) ? e[k >> 1].z : e[k >> 1].x);
-                    lt[c * 32] = t;
-                    li[c * 32] = (k & 1) ? e[k >> 1].w : e[k >> 1].y;
+                    const float4 q4 = e[k >> 2];
+                    const float t = (k & 3) == 0 ? q4.x : (k & 3) == 1 ? q4.y : (k & 3) == 2 ? q4.z : q4.w;
+                    if (in_col) lt[c * 32] = t;
                     if (prune) top_m(tm, t);
                 }
             }
             if (prune) thr = threshold(mth(tm));
+        }
+        // the reachable prefix into the column, each entry's slot number in
+        // place of its table index for now
+        if (in_col) {
             for (uint32_t c = 0; c < cnt; ++c) {
                 const float t = lt[c * 32];
                 if (!(t <= thr)) continue;
-                keep(t, li[c * 32]);                 // n_col <= c: in place
+                keep(t, c);                          // n_col <= c: in place
             }
         } else {
-            // more than a column holds: the slots twice (the threshold first)
-            if (prune) {
-                float tm[kPruneMax];
-#pragma unroll
-                for (int q = 0; q < kPruneMax; ++q) tm[q] = thr;
-                for (uint32_t c0 = 0; c0 < cnt; c0 += 2 * kSlotBatch) {
-                    uint4 e[kSlotBatch];
-#pragma unroll
-                    for (int k = 0; k < kSlotBatch; ++k)
-                        if (c0 + 2 * k < cnt) e[k] = __ldg(sl + (c0 >> 1) + k);
-#pragma unroll
-                    for (int k = 0; k < 2 * kSlotBatch; ++k) {
-                        if (c0 + k >= cnt) break;
-                        top_m(tm, __uint_as_float((k & 1) ? e[k >> 1].z : e[k >> 1].x));
-                    }
-                }
-                thr = threshold(mth(tm));
-            }
-            for (uint32_t c0 = 0; c0 < cnt; c0 += 2 * kSlotBatch) {
-                uint4 e[kSlotBatch];
+            // more than a column holds: the depths again from global memory
+            for (uint32_t c0 = 0; c0 < cnt; c0 += 4 * kSlotBatch) {
+                float4 e[kSlotBatch];
 #pragma unroll
                 for (int k = 0; k < kSlotBatch; ++k)
-                    if (c0 + 2 * k < cnt) e[k] = __ldg(sl + (c0 >> 1) + k);
+                    if (c0 + 4 * k < cnt) e[k] = __ldg(st + (c0 >> 2) + k);
 #pragma unroll
-                for (int k = 0; k < 2 * kSlotBatch; ++k) {
-                    if (c0 + k >= cnt) break;
-                    const float t = __uint_as_float((k & 1) ? e[k >> 1].z : e[k >> 1].x);
+                for (int k = 0; k < 4 * kSlotBatch; ++k) {
+                    const uint32_t c = c0 + k;
+                    if (c >= cnt) break;
+                    const float4 q4 = e[k >> 2];
+                    const float t = (k & 3) == 0 ? q4.x : (k & 3) == 1 ? q4.y : (k & 3) == 2 ? q4.z : q4.w;
                     if (!(t <= thr)) continue;
                     if (n_col == kLaneCap) return false;   // more than the column holds
-                    keep(t, (k & 1) ? e[k >> 1].w : e[k >> 1].y);
+                    keep(t, c);
                 }
             }
+        }
+        // the kept entries' table indices, their loads in flight together
+        for (int c0 = 0; c0 < n_col; c0 += kSlotBatch) {
+            uint32_t ix[kSlotBatch];
+#pragma unroll
+            for (int k = 0; k < kSlotBatch; ++k)
+                if (c0 + k < n_col) ix[k] = __ldg(si + li[(c0 + k) * 32]);
+#pragma unroll
+            for (int k = 0; k < kSlotBatch; ++k)
+                if (c0 + k < n_col) li[(c0 + k) * 32] = ix[k];
         }
         total = (int)cnt;
     } else {
@@ -1191,7 +1199,7 @@ namespace {
 // Whole frames, plain search: the point-major pass finds the candidates.
 bool point_major_pass(const SearchArgs &a)
 {
-    return !a.prop_w && !a.interval && !a.rays && !a.ray_map && a.pm_slot && a.pm_cnt && a.pcell &&
+    return !a.prop_w && !a.interval && !a.rays && !a.ray_map && a.pm_t && a.pm_i && a.pm_cnt && a.pcell &&
            a.R == (int64_t)a.cam.width * a.cam.height;
 }
 
