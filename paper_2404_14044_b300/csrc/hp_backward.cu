@@ -20,15 +20,19 @@ namespace hp {
 
 namespace {
 
-constexpr int kBwdTile = 32;
-constexpr int kBwdThreads = 128;
+constexpr int kBwdTile = 32;         // samples per tile
+constexpr int kBwdThreads = 256;     // 8 warps; matmul threads hold 4 samples x 4 units
 
 struct BwdLayout {
-    int woff[HP_MLP_MAX_LAYERS], boff[HP_MLP_MAX_LAYERS];
-    int n_params, maxw;
-    size_t feat, h, dz, dh, mask, wsum, total;
+    int woff[HP_MLP_MAX_LAYERS], boff[HP_MLP_MAX_LAYERS];   // float offsets of W_l, b_l in the packed parameters
+    int maxw;
+    size_t feat, act0, act1, dz, dx, mask, wsum, total;
 };
 
+// Shared memory: the tile's IDW features [F][32], two activation buffers and
+// two gradient buffers [maxw][32] (unit-major, sample-minor), the hidden
+// layers' ReLU masks [layer][maxw][32] (bytes) and the IDW weight sums.  The
+// weights stay in global memory (read row-wise through L1).
 BwdLayout bwd_layout(const BwdArgs &a)
 {
     BwdLayout L{};
@@ -39,15 +43,18 @@ BwdLayout bwd_layout(const BwdArgs &a)
         L.boff[l] = o;
         o += a.dims[l + 1];
         maxw = maxw > a.dims[l] ? maxw : a.dims[l];
+        maxw = maxw > a.dims[l + 1] ? maxw : a.dims[l + 1];
     }
-    L.n_params = o;
     L.maxw = maxw;
-    size_t b = ((size_t)o * 4 + 15) & ~size_t(15);
+    const size_t buf = (size_t)maxw * kBwdTile * 4;
+    size_t b = 0;
     L.feat = b;  b += (size_t)a.F * kBwdTile * 4;
-    L.h = b;     b += (size_t)maxw * kBwdTile * 4;
-    L.dz = b;    b += (size_t)maxw * kBwdTile * 4;
-    L.dh = b;    b += (size_t)maxw * kBwdTile * 4;
-    L.mask = b;  b += (size_t)HP_MLP_MAX_LAYERS * 128 * 4;
+    L.act0 = b;  b += buf;
+    L.act1 = b;  b += buf;
+    L.dz = b;    b += buf;
+    L.dx = b;    b += buf;
+    L.mask = b;  b += (size_t)(a.n_layers > 1 ? a.n_layers - 1 : 1) * maxw * kBwdTile;
+    b = (b + 15) & ~size_t(15);
     L.wsum = b;  b += kBwdTile * 4;
     L.total = b;
     return L;
@@ -113,75 +120,125 @@ __global__ void __launch_bounds__(256) k_composite_bwd(const BwdArgs a)
     }
 }
 
-__global__ void __launch_bounds__(kBwdThreads) k_decode_bwd(const BwdArgs a, const BwdLayout L)
+// out[u][s] = sum_i W[u][i] in[i][s] (+ b[u]) for the tile's 32 samples, u <
+// n_out, i < n_in; W row-major [n_out][n_in] in global memory.  Thread t
+// holds samples 4 (t % 8) .. +3 and units 4 (t / 8) .. +3: each step reads
+// one 16-byte activation vector and four weights for 16 multiply-adds.
+// transposed: out[i][s] = sum_u W[u][i] in[u][s] (the backward through W).
+template <bool kTransposed>
+__device__ __forceinline__ void tile_matmul(const float *__restrict__ W, const float *__restrict__ bias, int n_out,
+                                            int n_in, const float *in, float (&acc)[4][4], int sb, int ub)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    float *prm = reinterpret_cast<float *>(smem);              // W^T [in][out] per layer, then biases
-    float *feat = reinterpret_cast<float *>(smem + L.feat);    // [F][32]
-    float *hb = reinterpret_cast<float *>(smem + L.h);         // [w][32]
-    float *dz = reinterpret_cast<float *>(smem + L.dz);
-    float *dh = reinterpret_cast<float *>(smem + L.dh);
-    uint32_t *mask = reinterpret_cast<uint32_t *>(smem + L.mask);   // [layer][128] sample bits
-    float *Wsum = reinterpret_cast<float *>(smem + L.wsum);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    {
-        int g = 0;
-        for (int l = 0; l < a.n_layers; ++l) {
-            const int fi = a.dims[l], fo = a.dims[l + 1], nw = fi * fo;
-            for (int e = tid; e < nw; e += blockDim.x) {
-                const int oo = e / fi, ii = e - oo * fi;
-                prm[L.woff[l] + ii * fo + oo] = __ldg(a.mlp + g + e);
-            }
-            g += nw;
-            for (int e = tid; e < fo; e += blockDim.x) prm[L.boff[l] + e] = __ldg(a.mlp + g + e);
-            g += fo;
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[s][q] = (!kTransposed && bias && 4 * ub + q < n_out) ? __ldg(bias + 4 * ub + q) : 0.0f;
+    if (4 * ub >= n_out) return;
+    const int nsum = kTransposed ? n_in : n_in;     // summed dimension length (rows of `in`)
+#pragma unroll 4
+    for (int k = 0; k < nsum; ++k) {
+        const float4 x = *reinterpret_cast<const float4 *>(in + k * kBwdTile + 4 * sb);
+        float w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int u = 4 * ub + q;
+            // forward: W[u][k] (row u of n_in); transposed: W[k][u] (row k of n_out)
+            w[q] = u < n_out ? __ldg(kTransposed ? W + (int64_t)k * n_out + u : W + (int64_t)u * n_in + k) : 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            acc[0][q] = fmaf(w[q], x.x, acc[0][q]);
+            acc[1][q] = fmaf(w[q], x.y, acc[1][q]);
+            acc[2][q] = fmaf(w[q], x.z, acc[2][q]);
+            acc[3][q] = fmaf(w[q], x.w, acc[3][q]);
         }
     }
-    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBwdThreads, 2) k_decode_bwd(const BwdArgs a, const BwdLayout L)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *feat = reinterpret_cast<float *>(smem + L.feat);    // [F][32]
+    float *act[2] = {reinterpret_cast<float *>(smem + L.act0), reinterpret_cast<float *>(smem + L.act1)};
+    float *dzb = reinterpret_cast<float *>(smem + L.dz);
+    float *dxb = reinterpret_cast<float *>(smem + L.dx);
+    uint8_t *mask = reinterpret_cast<uint8_t *>(smem + L.mask);   // [layer][unit][sample]
+    float *Wsum = reinterpret_cast<float *>(smem + L.wsum);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int sb = tid & 7, ub = tid >> 3;
     const int64_t S_all = __ldg(a.sample_offset + a.R);
     const int64_t S = S_all < a.capacity ? S_all : a.capacity;
     const int F = a.F, K = a.K, NL = a.n_layers;
-    const int nwarps = kBwdThreads / 32;
+    constexpr int kWarps = kBwdThreads / 32;
+    constexpr int kNb = 8;                     // neighbours whose loads are in flight together
 
     for (int64_t base = (int64_t)blockIdx.x * kBwdTile; base < S; base += (int64_t)gridDim.x * kBwdTile) {
-        // ---- IDW features [F][32] (warp w: samples w, w+4, ...; lanes over features)
-        for (int s = warp; s < kBwdTile; s += nwarps) {
+        // ---- IDW features [F][32]: a warp per sample, lanes over features;
+        // a sample's neighbour ids and distances are read by K lanes at once
+        for (int s = warp; s < kBwdTile; s += kWarps) {
             const int64_t g = base + s;
-            for (int k = lane; k < F; k += 32) {
-                float acc = 0.0f, W = 0.0f;
-                if (g < S) {
-                    for (int m = 0; m < K; ++m) {
-                        const int id = __ldg(a.nbr + g * K + m);
-                        if (id < 0) continue;
-                        const float w = 1.0f / fmaxf(__ldg(a.nbr_dist + g * K + m), a.eps_d);
-                        acc = fmaf(w, __ldg(a.feats + (int64_t)id * F + k), acc);
-                        W += w;
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            float W = 0.0f;
+            if (g < S) {
+                for (int m0 = 0; m0 < K; m0 += 32) {
+                    const int m = m0 + lane;
+                    const int id_l = m < K ? __ldg(a.nbr + g * K + m) : -1;
+                    const float w_l = id_l >= 0 ? 1.0f / fmaxf(__ldg(a.nbr_dist + g * K + m), a.eps_d) : 0.0f;
+                    const int mn = min(32, K - m0);
+                    for (int c0 = 0; c0 < mn; c0 += kNb) {
+                        float fv[kNb][4];
+                        int idv[kNb];
+                        float wv[kNb];
+#pragma unroll
+                        for (int q = 0; q < kNb; ++q) {
+                            idv[q] = __shfl_sync(0xffffffffu, id_l, (c0 + q) & 31);
+                            wv[q] = __shfl_sync(0xffffffffu, w_l, (c0 + q) & 31);
+                            if (c0 + q >= mn) idv[q] = -1;
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                const int k = lane + 32 * j;
+                                fv[q][j] = (idv[q] >= 0 && k < F) ? __ldg(a.feats + (int64_t)idv[q] * F + k) : 0.0f;
+                            }
+                        }
+#pragma unroll
+                        for (int q = 0; q < kNb; ++q) {
+                            if (idv[q] < 0) continue;
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) acc[j] = fmaf(wv[q], fv[q][j], acc[j]);
+                            W += wv[q];
+                        }
                     }
                 }
-                feat[k * kBwdTile + s] = g < S ? acc / W : 0.0f;
-                if (k == 0) Wsum[s] = W;
             }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int k = lane + 32 * j;
+                if (k < F) feat[k * kBwdTile + s] = g < S ? acc[j] / W : 0.0f;
+            }
+            if (lane == 0) Wsum[s] = W;
         }
         __syncthreads();
-        // ---- forward through the hidden layers for the ReLU masks (lane = sample)
+        // ---- forward through the hidden layers: ReLU masks
         const float *in = feat;
         for (int l = 0; l + 1 < NL; ++l) {
             const int fi = a.dims[l], fo = a.dims[l + 1];
-            const float *Wt = prm + L.woff[l];
-            for (int oo = warp; oo < fo; oo += nwarps) {
-                float z = prm[L.boff[l] + oo];
-                for (int i = 0; i < fi; ++i) z = fmaf(Wt[i * fo + oo], in[i * kBwdTile + lane], z);
-                const unsigned bits = __ballot_sync(0xffffffffu, z > 0.0f);
-                if (lane == 0) mask[l * 128 + oo] = bits;
-                hb[oo * kBwdTile + lane] = fmaxf(z, 0.0f);
+            float z[4][4];
+            tile_matmul<false>(a.mlp + L.woff[l], a.mlp + L.boff[l], fo, fi, in, z, sb, ub);
+            float *out = act[l & 1];
+            uint8_t *mk = mask + (size_t)l * L.maxw * kBwdTile;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int u = 4 * ub + q;
+                if (u >= fo) break;
+                *reinterpret_cast<float4 *>(out + u * kBwdTile + 4 * sb) =
+                    make_float4(fmaxf(z[0][q], 0.f), fmaxf(z[1][q], 0.f), fmaxf(z[2][q], 0.f), fmaxf(z[3][q], 0.f));
+                *reinterpret_cast<uchar4 *>(mk + u * kBwdTile + 4 * sb) =
+                    make_uchar4(z[0][q] > 0.f, z[1][q] > 0.f, z[2][q] > 0.f, z[3][q] > 0.f);
             }
             __syncthreads();
-            // next layer's input: copy h into dz scratch so hb can be rewritten
-            for (int e = tid; e < fo * kBwdTile; e += blockDim.x) dh[e] = hb[e];
-            __syncthreads();
-            in = dh;
+            in = out;
         }
-        // ---- backward: dz of the output layer = dL/do
+        // ---- backward: the output layer's dz = dL/do
         for (int e = tid; e < 4 * kBwdTile; e += blockDim.x) {
             const int c = e / kBwdTile, s = e - c * kBwdTile;
             const int64_t g = base + s;
@@ -190,28 +247,38 @@ __global__ void __launch_bounds__(kBwdThreads) k_decode_bwd(const BwdArgs a, con
                 const float4 go = a.go[g];
                 v = c == 0 ? go.x : c == 1 ? go.y : c == 2 ? go.z : go.w;
             }
-            dz[c * kBwdTile + s] = v;
+            dzb[c * kBwdTile + s] = v;
         }
         __syncthreads();
+        float *dz = dzb, *dx = dxb;
         for (int l = NL - 1; l >= 0; --l) {
             const int fi = a.dims[l], fo = a.dims[l + 1];
-            const float *Wt = prm + L.woff[l];
-            for (int i = warp; i < fi; i += nwarps) {
-                float acc = 0.0f;
-                for (int oo = 0; oo < fo; ++oo) acc = fmaf(Wt[i * fo + oo], dz[oo * kBwdTile + lane], acc);
-                hb[i * kBwdTile + lane] = acc;
+            float d[4][4];
+            tile_matmul<true>(a.mlp + L.woff[l], nullptr, fi, fo, dz, d, sb, ub);
+            const uint8_t *mk = l > 0 ? mask + (size_t)(l - 1) * L.maxw * kBwdTile : nullptr;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int i = 4 * ub + q;
+                if (i >= fi) break;
+                float4 v = make_float4(d[0][q], d[1][q], d[2][q], d[3][q]);
+                if (mk) {
+                    const uchar4 m4 = *reinterpret_cast<const uchar4 *>(mk + i * kBwdTile + 4 * sb);
+                    v.x = m4.x ? v.x : 0.f;
+                    v.y = m4.y ? v.y : 0.f;
+                    v.z = m4.z ? v.z : 0.f;
+                    v.w = m4.w ? v.w : 0.f;
+                }
+                *reinterpret_cast<float4 *>(dx + i * kBwdTile + 4 * sb) = v;
             }
             __syncthreads();
-            if (l > 0) {
-                for (int e = tid; e < fi * kBwdTile; e += blockDim.x) {
-                    const int i = e / kBwdTile, s = e - i * kBwdTile;
-                    dz[e] = ((mask[(l - 1) * 128 + i] >> s) & 1u) ? hb[e] : 0.0f;
-                }
-                __syncthreads();
-            }
+            float *tmp = dz;
+            dz = dx;
+            dx = tmp;
         }
-        // hb[k][s] = dL/df_j.  IDW backward (warp per sample, lanes over features)
-        for (int s = warp; s < kBwdTile; s += nwarps) {
+        // dz[k][s] = dL/df_j.  IDW backward (warp per sample, lanes over
+        // features, a sample's neighbours kNb at a time with their feature
+        // loads in flight together)
+        for (int s = warp; s < kBwdTile; s += kWarps) {
             const int64_t g = base + s;
             if (g >= S) continue;
             const int ray = __ldg(a.ray + g);
@@ -219,29 +286,63 @@ __global__ void __launch_bounds__(kBwdThreads) k_decode_bwd(const BwdArgs a, con
             const float4 dd = __ldg(a.raytab + pix);
             const float tj = __ldg(a.t + g);
             const float W = Wsum[s];
+            float dfk[4], fj[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int k = lane + 32 * j;
+                dfk[j] = k < F ? dz[k * kBwdTile + s] : 0.0f;
+                fj[j] = k < F ? feat[k * kBwdTile + s] : 0.0f;
+            }
             float gx0 = 0.0f, gx1 = 0.0f, gx2 = 0.0f;
-            for (int m = 0; m < K; ++m) {
-                const int id = __ldg(a.nbr + g * K + m);
-                if (id < 0) continue;
-                const float dist = __ldg(a.nbr_dist + g * K + m);
-                const float w = 1.0f / fmaxf(dist, a.eps_d);
-                float gw_part = 0.0f;
-                for (int k = lane; k < F; k += 32) {
-                    const float dfk = hb[k * kBwdTile + s];
-                    if (a.grad_feats) atomicAdd(a.grad_feats + (int64_t)id * F + k, w / W * dfk);
-                    gw_part = fmaf(dfk, __ldg(a.feats + (int64_t)id * F + k) - feat[k * kBwdTile + s], gw_part);
-                }
-                for (int off = 16; off > 0; off >>= 1) gw_part += __shfl_xor_sync(0xffffffffu, gw_part, off);
-                if (dist > a.eps_d && a.grad_points && lane == 0) {
-                    const float gdist = -(gw_part / W) / (dist * dist);
-                    const float3 P = cam_point(a.cam, __ldg(a.points + 3 * (int64_t)id), __ldg(a.points + 3 * (int64_t)id + 1),
-                                               __ldg(a.points + 3 * (int64_t)id + 2));
-                    const float vx = fmaf(tj, dd.x, -P.x), vy = fmaf(tj, dd.y, -P.y), vz = fmaf(tj, dd.z, -P.z);
-                    const float sc = gdist / dist;
-                    add_world(a.grad_points, id, a.cam, -sc * vx, -sc * vy, -sc * vz);
-                    gx0 = fmaf(sc, vx, gx0);
-                    gx1 = fmaf(sc, vy, gx1);
-                    gx2 = fmaf(sc, vz, gx2);
+            for (int m0 = 0; m0 < K; m0 += 32) {
+                const int m = m0 + lane;
+                const int id_l = m < K ? __ldg(a.nbr + g * K + m) : -1;
+                const float d_l = id_l >= 0 ? __ldg(a.nbr_dist + g * K + m) : 1.0f;
+                const int mn = min(32, K - m0);
+                for (int c0 = 0; c0 < mn; c0 += kNb) {
+                    float fv[kNb][4];
+                    int idv[kNb];
+                    float dv[kNb];
+#pragma unroll
+                    for (int q = 0; q < kNb; ++q) {
+                        idv[q] = __shfl_sync(0xffffffffu, id_l, (c0 + q) & 31);
+                        dv[q] = __shfl_sync(0xffffffffu, d_l, (c0 + q) & 31);
+                        if (c0 + q >= mn) idv[q] = -1;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int k = lane + 32 * j;
+                            fv[q][j] = (idv[q] >= 0 && k < F) ? __ldg(a.feats + (int64_t)idv[q] * F + k) : 0.0f;
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < kNb; ++q) {
+                        const int id = idv[q];
+                        if (id < 0) continue;
+                        const float dist = dv[q];
+                        const float w = 1.0f / fmaxf(dist, a.eps_d);
+                        float gw_part = 0.0f;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int k = lane + 32 * j;
+                            if (k >= F) break;
+                            if (a.grad_feats) atomicAdd(a.grad_feats + (int64_t)id * F + k, w / W * dfk[j]);
+                            gw_part = fmaf(dfk[j], fv[q][j] - fj[j], gw_part);
+                        }
+#pragma unroll
+                        for (int off = 16; off > 0; off >>= 1) gw_part += __shfl_xor_sync(0xffffffffu, gw_part, off);
+                        if (dist > a.eps_d && a.grad_points && lane == 0) {
+                            const float gdist = -(gw_part / W) / (dist * dist);
+                            const float3 P = cam_point(a.cam, __ldg(a.points + 3 * (int64_t)id),
+                                                       __ldg(a.points + 3 * (int64_t)id + 1),
+                                                       __ldg(a.points + 3 * (int64_t)id + 2));
+                            const float vx = fmaf(tj, dd.x, -P.x), vy = fmaf(tj, dd.y, -P.y), vz = fmaf(tj, dd.z, -P.z);
+                            const float sc = gdist / dist;
+                            add_world(a.grad_points, id, a.cam, -sc * vx, -sc * vy, -sc * vz);
+                            gx0 = fmaf(sc, vx, gx0);
+                            gx1 = fmaf(sc, vy, gx1);
+                            gx2 = fmaf(sc, vz, gx2);
+                        }
+                    }
                 }
             }
             if (a.grad_points && lane == 0) {
@@ -267,7 +368,7 @@ cudaError_t launch_backward(const BwdArgs &a, cudaStream_t st, Prof *prof)
     if ((e = cudaFuncSetAttribute(k_decode_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total)) !=
         cudaSuccess)
         return e;
-    int64_t grid = (int64_t)a.num_sms * 2;
+    int64_t grid = (int64_t)a.num_sms * 2;   // two 256-thread blocks per SM
     const int64_t tiles = div_up(a.capacity > 0 ? a.capacity : 1, kBwdTile);
     if (grid > tiles) grid = tiles;
     prof_begin(prof, st, KID_DECODE_BWD);
