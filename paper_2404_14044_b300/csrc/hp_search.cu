@@ -1197,6 +1197,9 @@ namespace {
 // One search pass over the rays `a` describes: the lane-per-ray kernel, then
 // the warp-per-ray kernel over the rays the lanes listed as too wide.
 // Whole frames, plain search: the point-major pass finds the candidates.
+// Listed plain searches of at most this many rays per SM go warp-per-ray.
+constexpr int64_t kSmallListPerSm = 64;
+
 bool point_major_pass(const SearchArgs &a)
 {
     return !a.prop_w && !a.interval && !a.rays && !a.ray_map && a.pm_t && a.pm_i && a.pm_cnt && a.pcell &&
@@ -1231,6 +1234,17 @@ cudaError_t search_pass(const SearchArgs &a, cudaStream_t st, Prof *prof, int ki
     // persistent warps: as many blocks as stay resident, fewer for small work
     const int KB = a.K <= 4 ? 4 : a.K <= 8 ? 8 : a.K <= 16 ? 16 : 32;
     const int64_t blocks = std::min<int64_t>(div_up(units, kLaneWarps), (int64_t)a.n_sm * lane_blocks_per_sm(KB));
+    // A short plain list of rays (a training batch) would give the lane
+    // kernel a few hundred warps for the whole GPU: one warp per ray instead
+    if (!point_major && !a.interval && !a.prop_w && a.rays && a.R <= (int64_t)a.n_sm * kSmallListPerSm) {
+        SearchArgs w = a;
+        w.pm_cnt = nullptr;                      // no point-major slots: the warps walk
+        const int64_t wb = std::min<int64_t>(div_up(a.R, kSearchWarps), (int64_t)a.n_sm * 4);
+        prof_begin(prof, st, kid);
+        wide_k<<<(unsigned)wb, kSearchWarps * 32, wsm, st>>>(w);
+        prof_end(prof, st);
+        return cudaGetLastError();
+    }
     // pm_cnt: cleared with the tickets by launch_search
     prof_begin(prof, st, kid);
     if (point_major && a.n_points > 0)
