@@ -314,43 +314,97 @@ __device__ __forceinline__ void wide_ray(const SearchArgs &a, const float2 *inte
 
     // ---- window walk.  The s rows' runs are concatenated into one index
     // space (lane q holds row q's [lo, lo+len) and its exclusive offset),
-    // so every load instruction serves 32 points whatever the row lengths.
-    for (int r0 = 0; r0 < span && !from_slots; r0 += 32) {
-        const int nrows = min(32, span - r0);
-        uint32_t lo = 0;
-        int len = 0;
-        if (lane < nrows) {
-            const int64_t kb = (int64_t)(pv + off + r0 + lane) * a.Wp + pu + off;
-            lo = __ldg(a.start + kb);
-            len = (int)(__ldg(a.start + kb + span) - lo);
-        }
-        const int incl = warp_incl_scan(len);
-        const int tot = __shfl_sync(kFull, incl, 31);
-        const int excl = incl - len;
-        // point v of the concatenated runs (v < tot); the load for the next
-        // 32 points is issued before the current ones are tested
-        auto fetch = [&](int v) {
-            // row of v: the last row whose exclusive offset is <= v (binary search)
-            int row = 0;
-            for (int step = 16; step > 0; step >>= 1) {
-                const int cand = row + step;
-                const int ec = __shfl_sync(kFull, excl, cand < nrows ? cand : 31);
-                if (cand < nrows && v >= ec) row = cand;
+    // so every load instruction serves 32 points whatever the row lengths;
+    // visit(p, v < tot) runs for every 32 points, all lanes together.
+    auto walk = [&](auto &&visit) {
+        for (int r0 = 0; r0 < span; r0 += 32) {
+            const int nrows = min(32, span - r0);
+            uint32_t lo = 0;
+            int len = 0;
+            if (lane < nrows) {
+                const int64_t kb = (int64_t)(pv + off + r0 + lane) * a.Wp + pu + off;
+                lo = __ldg(a.start + kb);
+                len = (int)(__ldg(a.start + kb + span) - lo);
             }
-            const uint32_t rlo = __shfl_sync(kFull, lo, row);
-            const int rex = __shfl_sync(kFull, excl, row);
-            return v < tot ? __ldg(a.spts + rlo + (uint32_t)(v - rex)) : make_float4(0.f, 0.f, 0.f, 0.f);
-        };
-        float4 pn = tot > 0 ? fetch(lane) : make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int v0 = 0; v0 < tot; v0 += 32) {
-            const int v = v0 + lane;
-            const float4 p = pn;
-            if (v0 + 32 < tot) pn = fetch(v0 + 32 + lane);
+            const int incl = warp_incl_scan(len);
+            const int tot = __shfl_sync(kFull, incl, 31);
+            const int excl = incl - len;
+            // point v of the concatenated runs (v < tot); the load for the next
+            // 32 points is issued before the current ones are tested
+            auto fetch = [&](int v) {
+                // row of v: the last row whose exclusive offset is <= v (binary search)
+                int row = 0;
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int cand = row + step;
+                    const int ec = __shfl_sync(kFull, excl, cand < nrows ? cand : 31);
+                    if (cand < nrows && v >= ec) row = cand;
+                }
+                const uint32_t rlo = __shfl_sync(kFull, lo, row);
+                const int rex = __shfl_sync(kFull, excl, row);
+                return v < tot ? __ldg(a.spts + rlo + (uint32_t)(v - rex)) : make_float4(0.f, 0.f, 0.f, 0.f);
+            };
+            float4 pn = tot > 0 ? fetch(lane) : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int v0 = 0; v0 < tot; v0 += 32) {
+                const float4 p = pn;
+                if (v0 + 32 < tot) pn = fetch(v0 + 32 + lane);
+                visit(p, v0 + lane < tot);
+            }
+        }
+    };
+    // Plain search, pruned (the lane kernel's argument): a first walk finds
+    // the prune_m-th smallest accepted depth (each lane its own smallest,
+    // then prune_m warp minima) and counts the accepted points; the second
+    // appends only the reachable prefix of the (t, id) order, so the
+    // candidate buffer never has to replace entries.
+    float thr = __int_as_float(0x7f800000);
+    int walk_total = -1;
+    if (!from_slots && !interval && a.prune_m > 0) {
+        float tm[kPruneMax];
+#pragma unroll
+        for (int q = 0; q < kPruneMax; ++q) tm[q] = thr;
+        int n_acc = 0;
+        walk([&](const float4 &p, bool in) {
+            float t = 0.0f;
+            if (in && accept_point(a, ray, p, tn, tf, t)) {
+                ++n_acc;
+                float x = t;
+#pragma unroll
+                for (int q = 0; q < kPruneMax; ++q) {
+                    const float lo2 = fminf(tm[q], x);
+                    x = fmaxf(tm[q], x);
+                    tm[q] = lo2;
+                }
+            }
+        });
+        for (int o = 16; o > 0; o >>= 1) n_acc += __shfl_xor_sync(kFull, n_acc, o);
+        if (n_acc > a.prune_m) {
+            // the prune_m-th smallest over the warp: repeated warp minima of
+            // the lanes' smallest unused depths (ties taken one lane at a time)
+            int head = 0;
+            float tl = thr;
+            for (int r = 0; r < a.prune_m; ++r) {
+                float mine = thr;
+#pragma unroll
+                for (int q = 0; q < kPruneMax; ++q)
+                    if (q == head) mine = tm[q];
+                float m = mine;
+                for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(kFull, m, o));
+                const unsigned who = __ballot_sync(kFull, mine == m);
+                if (lane == __ffs(who) - 1) ++head;
+                tl = m;
+            }
+            const float rl = radius_at(a.mode, a.r, ray, tl);
+            thr = tl + (rl * 1.001f + 1e-5f * (1.0f + tl)) * 1.01f;
+        }
+        walk_total = n_acc;
+    }
+    if (!from_slots) {
+        walk([&](const float4 &p, bool in) {
             bool acc = false;
             float t = 0.0f;
-            if (v < tot) {
+            if (in) {
                 if (!interval) {
-                    acc = accept_point(a, ray, p, tn, tf, t);
+                    acc = accept_point(a, ray, p, tn, tf, t) && t <= thr;
                 } else {
                     // restricted: points the plain search would accept outside
                     // [t0, t1] flag a possible miss (a surface in front, or
@@ -363,7 +417,8 @@ __device__ __forceinline__ void wide_ray(const SearchArgs &a, const float2 *inte
             }
             const uint64_t key = ((uint64_t)__float_as_uint(t) << 32) | (uint32_t)__float_as_int(p.w);
             append_candidates(acc, key, p, lane, lt_mask, a.cand_cap, ck, cp, kept, total);
-        }
+        });
+        if (walk_total >= 0) total = walk_total;   // the count is of every accepted point
     }
     __syncwarp();
 
