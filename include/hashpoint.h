@@ -331,7 +331,7 @@ hp_status hp_selftest_mma(hp_ctx *ctx, const uint16_t *d_a, const uint16_t *d_b,
  * the bounded inter-block wait) is copied there on `stream`.
  *
  * Memory: the scratch (look-back words, ticket, status) lives in one
- * file-scope static device array of 262,176 bytes that every device which
+ * file-scope static device array of 65,568 bytes that every device which
  * loads the library holds until the process exits.  The call allocates and
  * frees nothing; it only clears the part of the array it uses.  The first
  * call on a device looks the array's device address up (cudaGetSymbolAddress,

@@ -14,7 +14,7 @@ constexpr int kCandCap = 128;        // candidate buffer per ray (power of two)
 constexpr int kMaxK = 32;            // neighbours per candidate
 constexpr int kMaxSamples = 16;      // samples per ray
 constexpr int kSearchWarps = 8;
-constexpr int kScanThreads = 256;
+constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 8;        // per thread: tile = 2048 entries
 constexpr int kScanTile = kScanThreads * kScanItems;
 constexpr uint32_t kSpinLimitDefault = 1u << 22;

@@ -17,7 +17,7 @@ constexpr int64_t kNoAllocHead = 4;
 constexpr int64_t kNoAllocMaxTiles = HP_SCAN_NOALLOC_MAX_N / kScanTile;
 static_assert(HP_SCAN_NOALLOC_MAX_N % kScanTile == 0, "limit must be whole tiles");
 
-// 32 KiWords + 4 = 262,176 bytes, resident on every device that loads the library.
+// 8 KiWords + 4 = 65,568 bytes (8,192-entry tiles), resident on every device that loads the library.
 static __device__ __align__(256) uint64_t g_noalloc_scratch[kNoAllocHead + kNoAllocMaxTiles];
 
 constexpr int kMaxDevices = 128;

@@ -64,12 +64,13 @@ def _wrapping_exclusive_scan(x: np.ndarray) -> np.ndarray:
 
 @pytest.mark.parametrize("kind", ["all_ones", "near_2_31", "full_range"])
 def test_scan_noalloc_wrapping_uint32(kind):
-    """Sums past 2^31 and 2^32 inside and across 2048-entry tiles, on a ragged
-    length: the result must equal the uint32 exclusive prefix sum modulo 2^32."""
+    """Sums past 2^31 and 2^32 inside and across the scan's 8192-entry tiles,
+    on a ragged length: the result must equal the uint32 exclusive prefix sum
+    modulo 2^32."""
     from paper_2404_14044_b300 import hashpoint as H
     dev = torch.device("cuda", 0)
     rng = np.random.default_rng(7)
-    n = 5 * 2048 + 777
+    n = 5 * 8192 + 777
     if kind == "all_ones":
         x = np.full(n, 0xFFFFFFFF, dtype=np.uint32)
     elif kind == "near_2_31":
