@@ -139,7 +139,7 @@ def algorithmic(kernel, N, Nv, P, R, S, K, F, dims, U, tensor_decode=True):
     table = {
         "k_project_count": ("hbm", 12 * N + 8 * N + 8 * P),
         "k_scan": ("hbm", 8 * (P + 1)),
-        "k_scatter": ("hbm", 12 * N + 8 * N + 4 * Nv + 16 * Nv),
+        "k_scatter": ("hbm", 12 * N + 8 * N + 4 * Nv + 16 * Nv + 4 * Nv),
         "k_bucket_sort": ("hbm", 8 * P + 32 * Nv),
         "k_search_select": ("hbm", 4 * P + 16 * Nv + 12 * R + (12 + 8 * K) * S),
         "k_search_pick": ("hbm", 0),

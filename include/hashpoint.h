@@ -149,7 +149,9 @@ typedef struct {
     const uint32_t *d_start; /* [n_buckets+1] first list position of each bucket */
     const float *d_points;   /* [N][4]: the reordered list, rows 0 .. d_start[n_buckets]-1:
                                 camera-space x, y, z and the point id (int32 bits),
-                                bucket by bucket, each bucket ordered by (z, x, y, id) */
+                                bucket by bucket; inside a bucket in the order the
+                                build's atomics left them (hp_table_copy returns each
+                                bucket ordered by (z, x, y, id)) */
 } hp_table;
 
 /* Create a context for `cfg` on the current CUDA device.  Allocates only the
@@ -179,18 +181,23 @@ hp_status hp_set_workspace(hp_ctx *ctx, void *d_ptr, size_t bytes);
 /* Sec. 3.2 table build for d_points (n_points x 3, world xyz) seen by `cam`.
  * Fixed mode: r is the search radius.  Cone modes: r is used only when
  * cfg.rho <= 0 (r_min at t_near).  n_points may be 0.  Kernels: projection +
- * atomic bucket counts, decoupled-lookback scan, scatter, per-bucket
- * depth sort. */
+ * atomic bucket counts, decoupled-lookback scan, scatter.  No result of the
+ * search, the sampling or the proposal depends on the order of the points
+ * inside a bucket; the per-bucket depth order is established when the table
+ * is read out (hp_table_copy). */
 hp_status hp_build_table(hp_ctx *ctx, const float *d_points, int64_t n_points, const hp_camera *cam,
                          float r, void *stream);
 
 /* Describe the current table (valid after hp_build_table was enqueued). */
 hp_status hp_table_info(const hp_ctx *ctx, hp_table *out);
 
-/* Copy the current table into caller buffers (device-to-device, enqueued on
- * `stream`): d_start receives n_buckets+1 uint32 starts, d_points receives
- * n_points x 4 floats (the reordered list of hp_table.d_points; rows past
- * d_start[n_buckets], the number of kept points, are unspecified). */
+/* Copy the current table into caller buffers (enqueued on `stream`):
+ * d_start receives n_buckets+1 uint32 starts, d_points receives n_points x 4
+ * floats: the reordered list of hp_table.d_points with every bucket sorted by
+ * (camera depth z, x, y, id) -- the canonical, input-order-independent table
+ * (Sec. 3.2, "Z-order manner": reading c1).  Rows past d_start[n_buckets],
+ * the number of kept points, are unspecified.  The sort runs on the GPU and
+ * uses the context's count array as scratch. */
 hp_status hp_table_copy(const hp_ctx *ctx, uint32_t *d_start, float *d_points, void *stream);
 
 /* Sec. 3.2 window search + Sec. 3.3 primary-surface sampling for n_rays rays.

@@ -31,7 +31,7 @@ struct hp_ctx {
     uint32_t *cnt = nullptr, *start = nullptr, *scan_ticket = nullptr;
     uint2 *keyrank = nullptr;
     float4 *spts = nullptr;
-    float4 *spts_tmp = nullptr;
+    uint32_t *pcell = nullptr;           // bucket of each listed point (the scatter writes it)
     uint64_t *scan_flags = nullptr;
     float4 *raytab = nullptr;        // per-pixel rays, cached while the intrinsics are unchanged
     bool raytab_valid = false;
@@ -146,7 +146,7 @@ size_t table_region_bytes(int64_t N, int64_t P, int64_t npix)
     o += al(4 * (size_t)(P + 1));                            // start
     o += al(8 * (size_t)N);                                  // keyrank
     o += al(16 * (size_t)N);                                 // spts
-    o += al(16 * (size_t)N);                                 // spts before the in-bucket order
+    o += al(4 * (size_t)N);                                  // bucket of each listed point
     return o;
 }
 
@@ -421,7 +421,7 @@ hp_status hp_build_table(hp_ctx *ctx, const float *d_points, int64_t n_points, c
     ctx->start = reinterpret_cast<uint32_t *>(base + o);       o += al(4 * (size_t)(P + 1));
     ctx->keyrank = reinterpret_cast<uint2 *>(base + o);        o += al(8 * (size_t)n_points);
     ctx->spts = reinterpret_cast<float4 *>(base + o);          o += al(16 * (size_t)n_points);
-    ctx->spts_tmp = reinterpret_cast<float4 *>(base + o);
+    ctx->pcell = reinterpret_cast<uint32_t *>(base + o);
 
     Cam c{};
     std::memcpy(c.R, cam->R, sizeof(c.R));
@@ -436,10 +436,9 @@ hp_status hp_build_table(hp_ctx *ctx, const float *d_points, int64_t n_points, c
     BuildArgs a{};
     a.pts = d_points; a.N = n_points; a.cam = c; a.h = h; a.P = P;
     a.cnt = ctx->cnt; a.start = ctx->start; a.keyrank = ctx->keyrank; a.spts = ctx->spts;
-    a.spts_tmp = ctx->spts_tmp;
     a.scan_flags = ctx->scan_flags; a.scan_ticket = ctx->scan_ticket; a.err = ctx->d_err;
     a.zmin_enc = ctx->scan_ticket + 1;
-    a.pcell = reinterpret_cast<uint32_t *>(ctx->keyrank);   // the keys are spent once the scatter has run
+    a.pcell = ctx->pcell;
     a.spin_limit = ctx->spin_limit; a.skip_tile = ctx->skip_tile;
     if (launch_build(a, static_cast<cudaStream_t>(stream), &ctx->prof) != cudaSuccess) {
         cudaGetLastError();
@@ -468,9 +467,14 @@ hp_status hp_table_copy(const hp_ctx *ctx, uint32_t *d_start, float *d_points, v
     if (!ctx || !d_start || (ctx->N > 0 && !d_points)) return HP_ERR_INVALID_ARG;
     if (!ctx->built) return HP_ERR_NOT_BUILT;
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (cudaMemcpyAsync(d_start, ctx->start, 4 * (size_t)(ctx->P + 1), cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
-        (ctx->N > 0 &&
-         cudaMemcpyAsync(d_points, ctx->spts, 16 * (size_t)ctx->N, cudaMemcpyDeviceToDevice, st) != cudaSuccess)) {
+    if (cudaMemcpyAsync(d_start, ctx->start, 4 * (size_t)(ctx->P + 1), cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+        cudaGetLastError();
+        return HP_ERR_CUDA;
+    }
+    // the list in its canonical order: every bucket sorted by (z, x, y, id)
+    // into the caller's buffer (the table itself keeps the scatter's order)
+    if (ctx->N > 0 && launch_bucket_sort(ctx->P, ctx->start, ctx->spts, reinterpret_cast<float4 *>(d_points), ctx->cnt,
+                                         ctx->scan_ticket + 2, st) != cudaSuccess) {
         cudaGetLastError();
         return HP_ERR_CUDA;
     }
@@ -550,7 +554,7 @@ static hp_status search_impl(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n
         a.interval_buf = reinterpret_cast<float2 *>(base + o); o += al(8 * (size_t)n_rays);
         a.pm_t = reinterpret_cast<float *>(base + o);
         a.pm_i = reinterpret_cast<uint32_t *>(base + o + 4 * (size_t)kPmCap * (size_t)n_rays);
-        a.pcell = reinterpret_cast<const uint32_t *>(ctx->keyrank);
+        a.pcell = ctx->pcell;
         a.n_points = ctx->N;
         a.prop_w = d_prop_w;
         a.wide_count = a.ticket + 2;

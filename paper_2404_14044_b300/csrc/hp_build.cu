@@ -8,12 +8,17 @@
 //                     the atomic's return value is the point's slot in its run
 // K2 k_scan           exclusive prefix sum of the counts (decoupled look-back)
 // K3 k_scatter        each point written to start[key] + slot as float4
-//                     (camera x, y, z, id bits)
+//                     (camera x, y, z, id bits), with its bucket beside it
 // K4 k_bucket_sort    each run ordered by (z, x, y, id), which makes the list
 //                     independent of the atomics' order and of the input order:
 //                     one thread per bucket sorts a small bucket in registers;
 //                     k_bucket_sort_big ranks the points of larger buckets,
-//                     one warp per bucket
+//                     one warp per bucket.  Nothing the search, the sampling or
+//                     the proposal computes depends on the order inside a
+//                     bucket (every walk tests all of a bucket's points and
+//                     every selection orders candidates by (t, id)), so the
+//                     frame leaves the scatter's order and the sort runs when
+//                     the table is read out (hp_table_copy)
 #include "hp_kernels.cuh"
 
 namespace hp {
@@ -109,7 +114,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t *__restric
 
 __global__ void __launch_bounds__(256) k_scatter(const float *__restrict__ pts, int64_t N, Cam cam,
                                                  const uint2 *__restrict__ keyrank,
-                                                 const uint32_t *__restrict__ start, float4 *__restrict__ spts)
+                                                 const uint32_t *__restrict__ start, float4 *__restrict__ spts,
+                                                 uint32_t *__restrict__ pcell)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -117,7 +123,9 @@ __global__ void __launch_bounds__(256) k_scatter(const float *__restrict__ pts, 
     if (kr.x == kNoKey) return;
     // the same float32 sequence as K1, so the stored position is the one keyed
     float3 X = cam_point(cam, __ldg(pts + 3 * i), __ldg(pts + 3 * i + 1), __ldg(pts + 3 * i + 2));
-    spts[start[kr.x] + kr.y] = make_float4(X.x, X.y, X.z, __int_as_float((int)i));
+    const uint32_t slot = start[kr.x] + kr.y;
+    spts[slot] = make_float4(X.x, X.y, X.z, __int_as_float((int)i));
+    pcell[slot] = kr.x;
 }
 
 __device__ __forceinline__ bool pt_less(const float4 &a, const float4 &b)
@@ -138,8 +146,7 @@ constexpr unsigned kBigSortBlocks = 888;   // warps loop over the large-bucket l
 
 __global__ void __launch_bounds__(256) k_bucket_sort(int64_t P, const uint32_t *__restrict__ start,
                                                      const float4 *__restrict__ tmp, float4 *__restrict__ spts,
-                                                     uint32_t *__restrict__ pcell, uint32_t *__restrict__ big,
-                                                     uint32_t *__restrict__ n_big)
+                                                     uint32_t *__restrict__ big, uint32_t *__restrict__ n_big)
 {
     const int64_t bkt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (bkt >= P) return;
@@ -169,17 +176,13 @@ __global__ void __launch_bounds__(256) k_bucket_sort(int64_t P, const uint32_t *
     }
 #pragma unroll
     for (int i = 0; i < kSmallBucket; ++i)
-        if (i < (int)n) {
-            spts[a + i] = v[i];
-            pcell[a + i] = (uint32_t)bkt;
-        }
+        if (i < (int)n) spts[a + i] = v[i];
 }
 
 constexpr int kBigStage = 128;   // points of a large bucket staged in shared memory per warp (larger ones: from global memory)
 
 __global__ void __launch_bounds__(256) k_bucket_sort_big(const uint32_t *__restrict__ start,
                                                          const float4 *__restrict__ tmp, float4 *__restrict__ spts,
-                                                         uint32_t *__restrict__ pcell,
                                                          const uint32_t *__restrict__ big,
                                                          const uint32_t *__restrict__ n_big)
 {
@@ -199,7 +202,6 @@ __global__ void __launch_bounds__(256) k_bucket_sort_big(const uint32_t *__restr
                 uint32_t rank = 0;
                 for (uint32_t j = 0; j < n; ++j) rank += pt_less(sp[j], x) ? 1u : 0u;
                 spts[a + rank] = x;
-                pcell[a + rank] = bkt;
             }
             __syncwarp();
         } else {
@@ -208,7 +210,6 @@ __global__ void __launch_bounds__(256) k_bucket_sort_big(const uint32_t *__restr
                 uint32_t rank = 0;
                 for (uint32_t j = a; j < b; ++j) rank += pt_less(__ldg(tmp + j), x) ? 1u : 0u;
                 spts[a + rank] = x;
-                pcell[a + rank] = bkt;
             }
         }
     }
@@ -243,20 +244,22 @@ cudaError_t launch_build(const BuildArgs &a, cudaStream_t st, Prof *prof)
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (a.N > 0) {
         prof_begin(prof, st, KID_SCATTER);
-        k_scatter<<<(unsigned)div_up(a.N, 256), 256, 0, st>>>(a.pts, a.N, a.cam, a.keyrank, a.start, a.spts_tmp);
-        prof_end(prof, st);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        prof_begin(prof, st, KID_SORT);
-        // the counts are spent after the scan: cnt holds the large-bucket list
-        k_bucket_sort<<<(unsigned)div_up(a.P, 256), 256, 0, st>>>(a.P, a.start, a.spts_tmp, a.spts, a.pcell,
-                                                                  a.cnt, a.scan_ticket + 2);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        k_bucket_sort_big<<<kBigSortBlocks, 256, 0, st>>>(a.start, a.spts_tmp, a.spts, a.pcell, a.cnt,
-                                                          a.scan_ticket + 2);
+        k_scatter<<<(unsigned)div_up(a.N, 256), 256, 0, st>>>(a.pts, a.N, a.cam, a.keyrank, a.start, a.spts, a.pcell);
         prof_end(prof, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_bucket_sort(int64_t P, const uint32_t *start, const float4 *list, float4 *out, uint32_t *big,
+                               uint32_t *n_big, cudaStream_t st)
+{
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(n_big, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+    k_bucket_sort<<<(unsigned)div_up(P, 256), 256, 0, st>>>(P, start, list, out, big, n_big);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_bucket_sort_big<<<kBigSortBlocks, 256, 0, st>>>(start, list, out, big, n_big);
+    return cudaGetLastError();
 }
 
 }  // namespace hp

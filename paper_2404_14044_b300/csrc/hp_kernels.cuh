@@ -45,9 +45,8 @@ struct BuildArgs {
     uint32_t *cnt;          // [P+1]
     uint32_t *start;        // [P+1]
     uint2 *keyrank;         // [N]
-    float4 *spts;           // [N]
-    float4 *spts_tmp;       // [N] scattered in atomic order, before the in-bucket sort
-    uint32_t *pcell;        // [N] bucket of each sorted point (written by the sort)
+    float4 *spts;           // [N] bucket by bucket, within a bucket in the atomics' order
+    uint32_t *pcell;        // [N] bucket of each listed point (written by the scatter)
     uint64_t *scan_flags;   // [ceil((P+1)/kScanTile)]
     uint32_t *scan_ticket;
     uint32_t *zmin_enc;     // smallest depth of a tabled point, 0x7f800000 - bits (0: none), by atomicMax
@@ -87,7 +86,7 @@ struct SearchArgs {
     float2 *interval_buf;    // ... and leaves it here for the rays it hands to the warp-per-ray search
     float win_fx, cos_max, sin_max;  // window bound terms for a depth lower bound (fixed radius)
     const uint32_t *zmin_enc;        // smallest depth of a tabled point (as BuildArgs::zmin_enc)
-    const uint32_t *pcell;   // bucket of each sorted point (whole frames: point-major candidate pass)
+    const uint32_t *pcell;   // bucket of each listed point (whole frames: point-major candidate pass)
     int64_t n_points;        // points given to the table build (bound of the tabled ones)
     uint32_t *pm_cnt;        // [W*H] candidates each pixel's ray received from the point-major pass
     float *pm_t;             // [W*H x kPmCap] depths t of those candidates
@@ -203,6 +202,11 @@ struct BwdArgs {
 };
 
 cudaError_t launch_build(const BuildArgs &a, cudaStream_t st, Prof *prof);
+// The list of a built table in its canonical order: each bucket's points of
+// `list` sorted by (z, x, y, id) into `out`; big / n_big: scratch for the list
+// of large buckets (P + 1 words) and its counter.
+cudaError_t launch_bucket_sort(int64_t P, const uint32_t *start, const float4 *list, float4 *out, uint32_t *big,
+                               uint32_t *n_big, cudaStream_t st);
 size_t backward_smem_bytes(const BwdArgs &a);
 cudaError_t launch_prop_infer(const PropArgs &a, cudaStream_t st, Prof *prof);
 cudaError_t launch_prop_train(const PropArgs &a, float *m, float *v, int step, float lr, cudaStream_t st);
