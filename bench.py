@@ -159,9 +159,9 @@ def algorithmic(kernel, N, Nv, P, R, S, K, F, dims, U, tensor_decode=True):
 NCU_TRAFFIC = {
     # the search stage's time (k_search_select) covers the point-major pass
     # (k_search_splat) and the selection launch: their bytes are summed
-    "k_search_select": {"bytes": 35490816 + 15449600 + 93925632 + 34627584,
+    "k_search_select": {"bytes": 52981248 + 38299648 + 116570368 + 36192256,
                         "sources": ("hp_search.cu", "hp_common.cuh", "hp_kernels.cuh"),
-                        "sha256": "72c7cbd28da0f45a05ecfbdf3e2da4bb96cbdaf0a7a8b62995217d639d98322c"},
+                        "sha256": "3075612b4f31f063a62b44ef99677d9faa5eec82788393f732fc64b7939e0725"},
     "k_aggregate_decode": {"bytes": 78086144 + 828416,
                            "sources": ("hp_decode_tc.cu", "hp_tc.cuh", "hp_common.cuh", "hp_kernels.cuh"),
                            "sha256": "5e1cb08795708bf94bc0b8bb758e171f5a804b83e9df1544c60bfb9bac1a4e0f"},
