@@ -531,9 +531,9 @@ def run_gpu(args):
         flush.zero_()
         frame(views[k % N_VIEWS])
     prof = hp.profile_stop()
-    launches = sum(n for _, n in prof.values())
-    per_kernel = {name: {"ms_total": ms, "launches": n, "ms_avg": ms / n if n else 0.0}
-                  for name, (ms, n) in prof.items()}
+    launches = sum(nk for _, _, nk in prof.values())      # CUDA kernels, not timed brackets
+    per_kernel = {name: {"ms_total": ms, "launches": n, "kernels": nk, "ms_avg": ms / n if n else 0.0}
+                  for name, (ms, n, nk) in prof.items()}
     dom = max(prof.items(), key=lambda kv: kv[1][0])[0]
     pk = peaks()
 

@@ -303,15 +303,18 @@ hp_status hp_get_status(hp_ctx *ctx, void *stream, int32_t *dev_status, int64_t 
 hp_status hp_debug_fault(hp_ctx *ctx, int32_t skip_tile, int32_t spin_limit);
 
 /* Per-kernel device timing (CUDA events recorded on the launching stream
- * around every kernel the context launches).  hp_profile_start(ctx, n)
- * begins recording up to n launches (events are created here, on the host);
- * hp_profile_stop synchronises those events, writes the summed milliseconds
- * and launch counts per kernel into ms[HP_PROF_KERNELS] and
- * launches[HP_PROF_KERNELS] (either may be NULL), and stops recording.
- * Kernel ids: see hp_profile_kernel_name. */
-#define HP_PROF_KERNELS 13
+ * around every kernel the context launches, or around a kernel and the one
+ * that prepares its input: the point-major pass and the selection of a
+ * whole-frame search; the weight image and the tensor-core decode).
+ * hp_profile_start(ctx, n) begins recording up to n timed launches (events
+ * are created here, on the host); hp_profile_stop synchronises those events,
+ * writes per kernel id the summed milliseconds, the timed launches and the
+ * CUDA kernels those launches ran into ms[HP_PROF_KERNELS],
+ * launches[HP_PROF_KERNELS] and kernels[HP_PROF_KERNELS] (any may be NULL),
+ * and stops recording.  Kernel ids: see hp_profile_kernel_name. */
+#define HP_PROF_KERNELS 14
 hp_status hp_profile_start(hp_ctx *ctx, int32_t max_launches);
-hp_status hp_profile_stop(hp_ctx *ctx, double *ms, int32_t *launches);
+hp_status hp_profile_stop(hp_ctx *ctx, double *ms, int32_t *launches, int32_t *kernels);
 const char *hp_profile_kernel_name(int32_t id);
 
 /* Self-test of the tensor-core path: D = A B^T for A (128 x K) and B (N x K),

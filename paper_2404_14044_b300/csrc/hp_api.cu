@@ -162,11 +162,12 @@ size_t search_region_bytes(int64_t R, int n_max, int K)
            al(8 * (size_t)kPmCap * (size_t)(R > 0 ? R : 1));   // ... and the candidates
 }
 
-// decoded samples, then the backward's per-sample scratch
+// decoded samples, then the backward's per-sample scratch, then the
+// tensor-core decode's weight image and tile counter
 size_t render_region_bytes(int64_t cap)
 {
     const size_t c = (size_t)(cap > 0 ? cap : 1);
-    return al(16 * c) + al(16 * c) + al(4 * c);
+    return al(16 * c) + al(16 * c) + al(4 * c) + al(kWsImageMax) + al(256);
 }
 
 // Region i of the workspace: 0 table, 1 search, 2 render.
@@ -255,6 +256,7 @@ static void prof_release(Prof &p)
         delete[] p.ev;
     }
     delete[] p.kid;
+    delete[] p.nk;
     p = Prof();
 }
 
@@ -265,9 +267,11 @@ hp_status hp_profile_start(hp_ctx *ctx, int32_t max_launches)
     Prof &p = ctx->prof;
     p.ev = new (std::nothrow) cudaEvent_t[2 * (size_t)max_launches];
     p.kid = new (std::nothrow) int[max_launches];
-    if (!p.ev || !p.kid) {
+    p.nk = new (std::nothrow) int[max_launches];
+    if (!p.ev || !p.kid || !p.nk) {
         delete[] p.ev;
         delete[] p.kid;
+        delete[] p.nk;
         p = Prof();
         return HP_ERR_NO_MEMORY;
     }
@@ -285,12 +289,12 @@ hp_status hp_profile_start(hp_ctx *ctx, int32_t max_launches)
     return HP_OK;
 }
 
-hp_status hp_profile_stop(hp_ctx *ctx, double *ms, int32_t *launches)
+hp_status hp_profile_stop(hp_ctx *ctx, double *ms, int32_t *launches, int32_t *kernels)
 {
     if (!ctx) return HP_ERR_INVALID_ARG;
     Prof &p = ctx->prof;
     double acc[KID_COUNT] = {0};
-    int32_t cnt[KID_COUNT] = {0};
+    int32_t cnt[KID_COUNT] = {0}, nk[KID_COUNT] = {0};
     hp_status s = HP_OK;
     for (int i = 0; i < p.n; ++i) {
         float t = 0.f;
@@ -302,10 +306,12 @@ hp_status hp_profile_stop(hp_ctx *ctx, double *ms, int32_t *launches)
         }
         acc[p.kid[i]] += t;
         cnt[p.kid[i]] += 1;
+        nk[p.kid[i]] += p.nk[i];
     }
     for (int k = 0; k < KID_COUNT; ++k) {
         if (ms) ms[k] = acc[k];
         if (launches) launches[k] = cnt[k];
+        if (kernels) kernels[k] = nk[k];
     }
     prof_release(p);
     return s;
@@ -316,7 +322,7 @@ const char *hp_profile_kernel_name(int32_t id)
     static const char *names[KID_COUNT] = {"k_project_count", "k_scan", "k_scatter", "k_bucket_sort",
                                            "k_search_select", "k_pack_samples", "k_aggregate_decode",
                                            "k_composite", "k_composite_bwd", "k_decode_bwd", "k_prop_infer",
-                                           "k_search_select_fallback", "k_search_select_wide"};
+                                           "k_search_select_fallback", "k_search_select_wide", "k_ray_table"};
     static_assert(KID_COUNT == HP_PROF_KERNELS, "profiler kernel count");
     return (id >= 0 && id < KID_COUNT) ? names[id] : "unknown";
 }
@@ -694,6 +700,12 @@ hp_status hp_aggregate_render(hp_ctx *ctx, const hp_samples *smp, int64_t n_rays
     if (a.decode < HP_DECODE_FP32 || a.decode > HP_DECODE_BF16) return HP_ERR_INVALID_ARG;
     if (a.decode == HP_DECODE_BF16 && !decode_tc_supported(a, true, nullptr)) return HP_ERR_INVALID_ARG;
     a.sample_out = reinterpret_cast<float4 *>(base);
+    {
+        const size_t c = (size_t)(smp->capacity > 0 ? smp->capacity : 1);
+        const size_t o = al(16 * c) + al(16 * c) + al(4 * c);
+        a.wimg = reinterpret_cast<unsigned char *>(base + o);
+        a.tile_ctr = reinterpret_cast<uint32_t *>(base + o + al(kWsImageMax));
+    }
     a.rgb = d_rgb; a.wsum = d_wsum; a.num_sms = ctx->num_sms;
     const bool tc_ok = a.decode != HP_DECODE_FP32_SIMT && decode_tc_supported(a, a.decode == HP_DECODE_BF16, nullptr);
     if (!tc_ok && render_smem_bytes(a) > 227 * 1024) return HP_ERR_INVALID_ARG;

@@ -507,16 +507,23 @@ __global__ void __launch_bounds__(128, 1) k_mma_selftest(const uint16_t *A, cons
 // next tiles into two shared-memory buffers of the first A operand; 16
 // consumer warps in two groups of 8 (4 TMEM lane quarters x 2 column groups)
 // take alternate tiles (tile i in buffer i % 2), so one group's epilogues
-// overlap the other's MMAs.  Hidden activations never touch shared memory:
-// the epilogue writes them back into tensor memory (two 16-bit values per
-// column) and the next layer's tcgen05.mma reads its A operand from there.
+// overlap the other's MMAs.  Tiles come from a grid-wide counter.  Hidden
+// activations never touch shared memory: the epilogue writes them back into
+// tensor memory (two 16-bit values per column) and the next layer's
+// tcgen05.mma reads its A operand from there.  The 4-wide output layer runs
+// on the FP32 cores inside the last hidden layer's epilogue (a 16-wide MMA
+// for it measured slower: its round trip queues behind the other group's
+// layer MMAs).
 // FP32-accurate mode: A = A_hi + A_lo and B = B_hi + B_lo with lo the FP16
-// rounding of the remainder (unscaled), and A_hi B_hi + A_hi B_lo + A_lo B_hi
+// rounding of the remainder (unscaled; A_hi rounded toward zero so that the
+// ReLU clamps both parts), and A_hi B_hi + A_hi B_lo + A_lo B_hi
 // accumulate in one FP32 accumulator.  Tensor memory per group g:
 // D [256g, 256g+128), A_hi [256g+128, +64), A_lo [256g+192, +64).
+// The weights arrive as a prepared image (k_ws_image) by bulk copies.
 // Hand-offs: full[b] (producers -> consumers, one arrival per producer warp), empty[b]
 // (tcgen05.commit after the layer-0 MMAs that read buffer b), lbar[b] (bulk
-// copy of a tile's neighbour lists), mma (per layer).  Every wait is bounded.
+// copy of a tile's neighbour lists), mma (per layer), the weights' barrier.
+// Every wait is bounded.
 constexpr int kWsConsumerWarps = 16;      // two groups, each 4 TMEM lane quarters x kWsGroups column groups
 constexpr int kWsProducerWarps = 16;
 constexpr int kWsGroupWarps = kWsConsumerWarps / 2;
@@ -530,12 +537,18 @@ struct WsLayout {
     int fi[HP_MLP_MAX_LAYERS], fo[HP_MLP_MAX_LAYERS];
     int w_hi[HP_MLP_MAX_LAYERS], w_lo[HP_MLP_MAX_LAYERS];
     int bias[HP_MLP_MAX_LAYERS + 1];
-    int wl, f32_block;
+    int wl, f32_block, f32_bytes;
     int a0[2], a0_lo;                    // first A operand buffers; lo part at +a0_lo
     int ids[2], dists[2];                // neighbour list buffers
-    int comb, bars, tslot, total;
+    int comb, bars, tiles, tslot, total;
     int ok;                              // the layout fits this kernel
 };
+
+// The weights' shared-memory image as k_ws_image writes it to global memory:
+// the hidden layers' B operands (bytes [0, a0[0]) of the layout) followed by
+// the FP32 block (biases and the output layer).  Each CTA copies it in with
+// bulk copies.
+__host__ __device__ inline int ws_image_bytes(const WsLayout &L) { return L.a0[0] + L.f32_bytes; }
 
 WsLayout ws_layout(const RenderArgs &a, bool bf16)
 {
@@ -566,7 +579,8 @@ WsLayout ws_layout(const RenderArgs &a, bool bf16)
     }
     L.wl = f;
     f += 4 * a.dims[a.n_layers - 1];
-    o += up16(f * 4);
+    L.f32_bytes = up16(f * 4);
+    o += L.f32_bytes;
     const int list_bytes = kTcTile * a.K * 4;
     for (int b = 0; b < 2; ++b) {
         L.ids[b] = o;
@@ -577,7 +591,9 @@ WsLayout ws_layout(const RenderArgs &a, bool bf16)
     L.comb = o;
     o += 4 * kTcTile * 4 * 4;
     L.bars = o;
-    o += 8 * 8;                           // full[2], empty[2], lbar[2], mma
+    o += 9 * 8;                           // full[2], empty[2], lbar[2], mma[2], weights
+    L.tiles = o;
+    o += 4 * 8;                           // tile of each A buffer: producers' [2], consumers' [2]
     L.tslot = o;
     o += 16;
     L.total = o;
@@ -585,6 +601,45 @@ WsLayout ws_layout(const RenderArgs &a, bool bf16)
     // the gather maps 16-byte chunks of a feature row to lanes
     if (a.dims[0] % 16 != 0 || a.dims[0] > 128) L.ok = 0;
     return L;
+}
+
+// Converts the MLP (global, FP32, W [out][in] then b per layer) once per call
+// into the decode's shared-memory image (see ws_image_bytes) and clears the
+// decode's tile counter.
+template <bool kBF16>
+__global__ void k_ws_image(const RenderArgs a, const WsLayout L)
+{
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+    unsigned char *img = a.wimg;
+    float *f32 = reinterpret_cast<float *>(img + L.a0[0]);
+    if (gid == 0) *a.tile_ctr = 0u;
+    int g = 0;
+    for (int l = 0; l < a.n_layers; ++l) {
+        const int fi = a.dims[l], fo = a.dims[l + 1];
+        const int nw = fi * fo;
+        for (int e = gid; e < nw; e += nthr) {
+            const int o = e / fi, i = e - o * fi;
+            const float w = __ldg(a.mlp + g + e);
+            if (l < L.nh) {
+                const uint32_t off = tc::kmajor_off(o, i, fi);
+                if constexpr (kBF16) {
+                    *reinterpret_cast<__nv_bfloat16 *>(img + L.w_hi[l] + off) = __float2bfloat16_rn(w);
+                } else {
+                    __half h, lo;
+                    tc::split_f16_same_scale(w, h, lo);
+                    *reinterpret_cast<__half *>(img + L.w_hi[l] + off) = h;
+                    *reinterpret_cast<__half *>(img + L.w_lo[l] + off) = lo;
+                }
+            } else {
+                // the output layer's W [4][fi] stored transposed, [fi][4]:
+                // one 16-byte load gives an input's four weights
+                f32[L.wl + i * 4 + o] = w;
+            }
+        }
+        g += nw;
+        for (int e = gid; e < fo; e += nthr) f32[L.bias[l] + e] = __ldg(a.mlp + g + e);
+        g += fo;
+    }
 }
 
 template <bool kBF16>
@@ -595,56 +650,14 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
     float *f32 = reinterpret_cast<float *>(smem + L.f32_block);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.bars);
     uint64_t *full = bars, *empty = bars + 2, *lbar = bars + 4, *mbar = bars + 6;   // mbar: one per group
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + L.tslot);
     float *comb = reinterpret_cast<float *>(smem + L.comb);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + L.tslot);
 
-    // ---- stage weights (global W is [out][in] FP32) and FP32 biases; each
-    // thread has kStageBatch weight loads in flight before it converts any
-    // (one load at a time made the staging ~35k cycles per CTA)
-    {
-        constexpr int kStageBatch = 8;
-        int g = 0;
-        for (int l = 0; l < a.n_layers; ++l) {
-            const int fi = a.dims[l], fo = a.dims[l + 1];
-            const int nw = fi * fo;
-            if (l < L.nh) {
-                for (int e0 = tid; e0 < nw; e0 += kStageBatch * blockDim.x) {
-                    float wv[kStageBatch];
-#pragma unroll
-                    for (int u = 0; u < kStageBatch; ++u) {
-                        const int e = e0 + u * (int)blockDim.x;
-                        wv[u] = e < nw ? __ldg(a.mlp + g + e) : 0.0f;
-                    }
-#pragma unroll
-                    for (int u = 0; u < kStageBatch; ++u) {
-                        const int e = e0 + u * (int)blockDim.x;
-                        if (e >= nw) break;
-                        const int o = e / fi, i = e - o * fi;
-                        const float w = wv[u];
-                        const uint32_t off = tc::kmajor_off(o, i, fi);
-                        if constexpr (kBF16) {
-                            *reinterpret_cast<__nv_bfloat16 *>(smem + L.w_hi[l] + off) = __float2bfloat16_rn(w);
-                        } else {
-                            __half h, lo;
-                            tc::split_f16_same_scale(w, h, lo);
-                            *reinterpret_cast<__half *>(smem + L.w_hi[l] + off) = h;
-                            *reinterpret_cast<__half *>(smem + L.w_lo[l] + off) = lo;
-                        }
-                    }
-                }
-            } else {
-                for (int e = tid; e < nw; e += blockDim.x) {
-                    // the output layer's W [4][fi] stored transposed, [fi][4]:
-                    // one 16-byte load gives an input's four weights
-                    const int o = e / fi, ii = e - o * fi;
-                    f32[L.wl + ii * 4 + o] = __ldg(a.mlp + g + e);
-                }
-            }
-            g += nw;
-            for (int e = tid; e < fo; e += blockDim.x) f32[L.bias[l] + e] = __ldg(a.mlp + g + e);
-            g += fo;
-        }
-    }
+    int64_t *ptile = reinterpret_cast<int64_t *>(smem + L.tiles), *ctile = ptile + 2;
+    uint64_t *wbar = bars + 8;
+
+    // ---- the weights' image (k_ws_image) arrives by two bulk copies while
+    // the producers start on the first tiles; the consumers wait for it
     if (tid == 0) {
         tc::mbar_init(&full[0], kWsProducerWarps);
         tc::mbar_init(&full[1], kWsProducerWarps);
@@ -654,7 +667,14 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
         tc::mbar_init(&lbar[1], 1);
         tc::mbar_init(&mbar[0], 1);
         tc::mbar_init(&mbar[1], 1);
+        tc::mbar_init(wbar, 1);
         tc::mbar_fence_init();
+        const uint32_t wbytes = (uint32_t)L.a0[0], fbytes = (uint32_t)L.f32_bytes;
+        tc::mbar_arrive_expect_tx(wbar, wbytes + fbytes);
+        constexpr uint32_t kChunk = 32768;
+        for (uint32_t o = 0; o < wbytes; o += kChunk)
+            tc::bulk_g2s(smem + o, a.wimg + o, wbytes - o < kChunk ? wbytes - o : kChunk, wbar);
+        tc::bulk_g2s(smem + L.f32_block, a.wimg + wbytes, fbytes, wbar);
     }
     if (warp == 0) tc::tmem_alloc(tslot, kWsCols);
     tc::fence_async_smem();
@@ -666,7 +686,6 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
     const int64_t S_all = __ldg(a.sample_offset + a.R);
     const int64_t S = S_all < a.capacity ? S_all : a.capacity;
     const int F = a.F, K = a.K;
-    const int64_t stride = (int64_t)gridDim.x * kTcTile;
     const uint32_t list_bytes = (uint32_t)(kTcTile * K * 4);
     auto bulk_tile = [&](int64_t b) { return bulk_ok && b < S && b + kTcTile <= a.capacity; };
 
@@ -679,50 +698,64 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
         uint32_t lph = 0u, eph = 3u;   // parity bit per buffer; a fresh barrier's previous phase counts as done
         uint32_t pend = 0u;            // list copies in flight, per buffer (leader only)
         bool ok = true;
-        const int64_t first = (int64_t)blockIdx.x * kTcTile;
-        if (ptid == 0 && bulk_tile(first)) {
-            pend |= 1u;
-            tc::mbar_arrive_expect_tx(&lbar[0], 2 * list_bytes);
-            tc::bulk_g2s(smem + L.ids[0], a.nbr + first * K, list_bytes, &lbar[0]);
-            tc::bulk_g2s(smem + L.dists[0], a.nbr_dist + first * K, list_bytes, &lbar[0]);
+        // Tiles come from a grid-wide counter (cleared by k_ws_image).  The
+        // leader holds the next tile so that its neighbour lists are copied
+        // while the current one is gathered; ptile[b] is the tile of A buffer
+        // b for the producers, ctile[b] the same for the consumers (-1: no
+        // more tiles; each buffer gets one such end mark).
+        int64_t t_next = 0;
+        auto issue_lists = [&](int buf, int64_t tb) {
+            pend |= 1u << buf;
+            tc::mbar_arrive_expect_tx(&lbar[buf], 2 * list_bytes);
+            tc::bulk_g2s(smem + L.ids[buf], a.nbr + tb * K, list_bytes, &lbar[buf]);
+            tc::bulk_g2s(smem + L.dists[buf], a.nbr_dist + tb * K, list_bytes, &lbar[buf]);
+        };
+        if (ptid == 0) {
+            const int64_t t0 = (int64_t)atomicAdd(a.tile_ctr, 1u) * kTcTile;
+            ptile[0] = t0;
+            if (bulk_tile(t0)) issue_lists(0, t0);
+            t_next = t0 < S ? (int64_t)atomicAdd(a.tile_ctr, 1u) * kTcTile : t0;
         }
-        int it = 0;
-        for (int64_t base = first; base < S; base += stride, ++it) {
+        tc::bar_and(3, kWsProducerWarps * 32, true);
+        int ends = 0;
+        for (int it = 0; ends < 2; ++it) {
             const int b = it & 1;
+            const int64_t base = ptile[b];
+            const bool valid = base < S;
             int *s_ids = reinterpret_cast<int *>(smem + L.ids[b]);
             float *s_dst = reinterpret_cast<float *>(smem + L.dists[b]);
             // the next tile's lists into the other buffer (its readers finished:
             // producer barrier at the end of the previous iteration)
-            if (ptid == 0 && bulk_tile(base + stride)) {
-                const int64_t nb = base + stride;
-                pend |= 2u >> b;
-                tc::mbar_arrive_expect_tx(&lbar[b ^ 1], 2 * list_bytes);
-                tc::bulk_g2s(smem + L.ids[b ^ 1], a.nbr + nb * K, list_bytes, &lbar[b ^ 1]);
-                tc::bulk_g2s(smem + L.dists[b ^ 1], a.nbr_dist + nb * K, list_bytes, &lbar[b ^ 1]);
+            if (ptid == 0) {
+                ptile[b ^ 1] = t_next;
+                if (valid && bulk_tile(t_next)) issue_lists(b ^ 1, t_next);
+                if (t_next < S) t_next = (int64_t)atomicAdd(a.tile_ctr, 1u) * kTcTile;
             }
-            if (bulk_tile(base)) {
-                if (!tc::mbar_wait(&lbar[b], (lph >> b) & 1u, kMbarLimit)) {
-                    ok = false;
-                    set_error(a.err, HP_ERR_TIMEOUT, -5);
+            if (valid) {
+                if (bulk_tile(base)) {
+                    if (!tc::mbar_wait(&lbar[b], (lph >> b) & 1u, kMbarLimit)) {
+                        ok = false;
+                        set_error(a.err, HP_ERR_TIMEOUT, -5);
+                    }
+                    lph ^= 1u << b;
+                    pend &= ~(1u << b);
+                } else {
+                    for (int e = ptid; e < kTcTile * K; e += kWsProducerWarps * 32) {
+                        const int64_t g = base * K + e;
+                        const bool in = g < S * (int64_t)K;
+                        s_ids[e] = in ? __ldg(a.nbr + g) : -1;
+                        s_dst[e] = in ? __ldg(a.nbr_dist + g) : 1.0f;
+                    }
+                    ok = tc::bar_and(3, kWsProducerWarps * 32, ok);
                 }
-                lph ^= 1u << b;
-                pend &= ~(1u << b);
-            } else {
-                for (int e = ptid; e < kTcTile * K; e += kWsProducerWarps * 32) {
-                    const int64_t g = base * K + e;
-                    const bool in = g < S * (int64_t)K;
-                    s_ids[e] = in ? __ldg(a.nbr + g) : -1;
-                    s_dst[e] = in ? __ldg(a.nbr_dist + g) : 1.0f;
+                // BF16: the inverse-distance weights, each computed once, in place
+                // of the distances (read by other producers after the barrier
+                // below).  FP32 keeps the division in the gather loop: with the
+                // precomputed weights that variant spills at its 64 registers.
+                if constexpr (kBF16) {
+                    for (int e = ptid; e < kTcTile * K; e += kWsProducerWarps * 32)
+                        s_dst[e] = s_ids[e] >= 0 ? __fdividef(1.0f, fmaxf(s_dst[e], a.eps_d)) : 0.0f;
                 }
-                ok = tc::bar_and(3, kWsProducerWarps * 32, ok);
-            }
-            // BF16: the inverse-distance weights, each computed once, in place
-            // of the distances (read by other producers after the barrier
-            // below).  FP32 keeps the division in the gather loop: with the
-            // precomputed weights that variant spills at its 64 registers.
-            if constexpr (kBF16) {
-                for (int e = ptid; e < kTcTile * K; e += kWsProducerWarps * 32)
-                    s_dst[e] = s_ids[e] >= 0 ? __fdividef(1.0f, fmaxf(s_dst[e], a.eps_d)) : 0.0f;
             }
             // the buffer is free once the layer-0 MMAs of tile it-2 are done
             if (ok && !tc::mbar_wait(&empty[b], (eph >> b) & 1u, kMbarLimit)) {
@@ -732,37 +765,42 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
             eph ^= 1u << b;
             ok = tc::bar_and(3, kWsProducerWarps * 32, ok);   // every producer leaves together
             if (!ok) break;
-            unsigned char *A_hi = smem + L.a0[b];
-            unsigned char *A_lo = A_hi + L.a0_lo;
-            for (int s0 = pw * spw; s0 < kTcTile; s0 += kWsProducerWarps * spw) {
-                const int sl = s0 + sub;
-                const int64_t g = base + sl;
-                float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (g < S) {
-                    float wsum = 0.0f;
-                    const int *nb = s_ids + sl * K;
-                    const float *nw = s_dst + sl * K;
+            if (valid) {
+                unsigned char *A_hi = smem + L.a0[b];
+                unsigned char *A_lo = A_hi + L.a0_lo;
+                for (int s0 = pw * spw; s0 < kTcTile; s0 += kWsProducerWarps * spw) {
+                    const int sl = s0 + sub;
+                    const int64_t g = base + sl;
+                    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (g < S) {
+                        float wsum = 0.0f;
+                        const int *nb = s_ids + sl * K;
+                        const float *nw = s_dst + sl * K;
 #pragma unroll 8
-                    for (int k = 0; k < K; ++k) {
-                        const int id = nb[k];
-                        if (id >= 0) {
-                            // inverse-distance weight (approximate reciprocal:
-                            // ~2 ulp, far inside the colour tolerance)
-                            const float w = kBF16 ? nw[k] : __fdividef(1.0f, fmaxf(nw[k], a.eps_d));
-                            const float4 f = __ldg(feats4 + (int64_t)id * lpr + chunk);
-                            acc.x = fmaf(w, f.x, acc.x);
-                            acc.y = fmaf(w, f.y, acc.y);
-                            acc.z = fmaf(w, f.z, acc.z);
-                            acc.w = fmaf(w, f.w, acc.w);
-                            wsum += w;
+                        for (int k = 0; k < K; ++k) {
+                            const int id = nb[k];
+                            if (id >= 0) {
+                                // inverse-distance weight (approximate reciprocal:
+                                // ~2 ulp, far inside the colour tolerance)
+                                const float w = kBF16 ? nw[k] : __fdividef(1.0f, fmaxf(nw[k], a.eps_d));
+                                const float4 f = __ldg(feats4 + (int64_t)id * lpr + chunk);
+                                acc.x = fmaf(w, f.x, acc.x);
+                                acc.y = fmaf(w, f.y, acc.y);
+                                acc.z = fmaf(w, f.z, acc.z);
+                                acc.w = fmaf(w, f.w, acc.w);
+                                wsum += w;
+                            }
                         }
+                        const float inv = __fdividef(1.0f, wsum);
+                        acc.x *= inv; acc.y *= inv; acc.z *= inv; acc.w *= inv;
                     }
-                    const float inv = __fdividef(1.0f, wsum);
-                    acc.x *= inv; acc.y *= inv; acc.z *= inv; acc.w *= inv;
+                    store_operand4_ss<kBF16>(A_hi, A_lo, tc::kmajor_off(sl, 4 * chunk, F), acc);
                 }
-                store_operand4_ss<kBF16>(A_hi, A_lo, tc::kmajor_off(sl, 4 * chunk, F), acc);
+                tc::fence_async_smem();                  // generic stores -> tensor-core reads
+            } else {
+                ++ends;
             }
-            tc::fence_async_smem();                  // generic stores -> tensor-core reads
+            if (ptid == 0) ctile[b] = valid ? base : -1;
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&full[b]);
             ok = tc::bar_and(3, kWsProducerWarps * 32, ok);
@@ -786,14 +824,19 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
         uint32_t fph = 0u, mph = 0u;
         bool ok = true;
         const int b = grp;                       // this group's tiles all use A buffer grp
-        for (int64_t base = (int64_t)blockIdx.x * kTcTile + grp * stride; base < S; base += 2 * stride) {
-            if (!tc::mbar_wait(&full[b], fph, kMbarLimit)) {
+        if (!tc::mbar_wait(wbar, 0u, kMbarLimit)) {  // the weights' image
+            ok = false;
+            set_error(a.err, HP_ERR_TIMEOUT, -9);
+        }
+        for (;;) {
+            if (ok && !tc::mbar_wait(&full[b], fph, kMbarLimit)) {
                 ok = false;
                 set_error(a.err, HP_ERR_TIMEOUT, -7);
             }
             fph ^= 1u;
+            const int64_t base = ctile[b];           // -1: no more tiles
             ok = tc::bar_and(barid, nthr, ok);
-            if (!ok) break;
+            if (!ok || base < 0) break;
             tc::fence_after_sync();
             uint64_t o01 = tc::f32x2(0.f, 0.f), o23 = tc::f32x2(0.f, 0.f);   // output layer sums
             for (int l = 0; l < L.nh; ++l) {
@@ -837,7 +880,9 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
                 tc::fence_after_sync();
 
                 // ---- epilogue: this thread's row; 8-column chunks round-robin
-                // over the column groups, kWsBatch at a time (TMEM -> registers -> TMEM)
+                // over the column groups, kWsBatch at a time (TMEM -> registers
+                // -> TMEM as the next layer's A operand; the last hidden layer
+                // feeds the output layer's FMAs instead)
                 const float *bias = f32 + L.bias[l];
                 const bool last = (l + 1 == L.nh);
                 const int nch = fo / 8;
@@ -857,9 +902,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
 #pragma unroll
                     for (int j = 0; j < kWsBatch; ++j) {
                         const int ch = ch0 + kWsGroups * j;
-                        if (ch < nch) {
-                            tc::ld8(d1 + lane_off + (uint32_t)(8 * ch), v1[j]);
-                        }
+                        if (ch < nch) tc::ld8(d1 + lane_off + (uint32_t)(8 * ch), v1[j]);
                     }
                     // the first wait completes the loads; the others only tie
                     // each array to the wait
@@ -873,38 +916,36 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
                         const float4 b0 = bq[j][0];
                         const float4 b1 = bq[j][1];
                         const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-                        float h[8];
-                        // bias as packed pair additions (the scalar roundings), then ReLU
+                        // bias as packed pair additions (the scalar roundings)
+                        uint64_t z[4];
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const float2 z = tc::f32x2_unpack(tc::add_f32x2(tc::f32x2(v1[j][2 * i], v1[j][2 * i + 1]),
-                                                                            tc::f32x2(bb[2 * i], bb[2 * i + 1])));
-                            h[2 * i] = fmaxf(z.x, 0.0f);
-                            h[2 * i + 1] = fmaxf(z.y, 0.0f);
-                        }
+                        for (int i = 0; i < 4; ++i)
+                            z[i] = tc::add_f32x2(tc::f32x2(v1[j][2 * i], v1[j][2 * i + 1]),
+                                                 tc::f32x2(bb[2 * i], bb[2 * i + 1]));
                         if (!last) {
-                            // next layer's A: columns c/2 .. c/2+3 of A_hi (and A_lo)
+                            // ReLU inside the conversions; the next layer's A:
+                            // columns c/2 .. c/2+3 of A_hi (and A_lo)
                             uint32_t ph[4], pl[4];
 #pragma unroll
                             for (int i = 0; i < 4; ++i) {
-                                if constexpr (kBF16) {
-                                    const __nv_bfloat162 x = __floats2bfloat162_rn(h[2 * i], h[2 * i + 1]);
-                                    ph[i] = *reinterpret_cast<const uint32_t *>(&x);
-                                    pl[i] = 0u;
-                                } else {
-                                    tc::split_f16x2_same_scale_p(h[2 * i], h[2 * i + 1], ph[i], pl[i]);
-                                }
+                                if constexpr (kBF16)
+                                    ph[i] = tc::relu_bf16x2(z[i]);
+                                else
+                                    tc::split_relu_f16x2(z[i], ph[i], pl[i]);
                             }
                             tc::st4(ah + lane_off + (uint32_t)(c / 2), ph);
                             if constexpr (!kBF16) tc::st4(al + lane_off + (uint32_t)(c / 2), pl);
                         } else {
-                            // output layer: outputs (0, 1) and (2, 3) as packed FMAs
-                            // in input order (each output's scalar FMA chain)
+                            // ReLU; output layer: outputs (0, 1) and (2, 3) as
+                            // packed FMAs in input order (each output's scalar
+                            // FMA chain)
                             const float4 *W4 = reinterpret_cast<const float4 *>(f32 + L.wl) + c;
 #pragma unroll
                             for (int i = 0; i < 8; ++i) {
+                                const float2 zz = tc::f32x2_unpack(z[i >> 1]);
+                                const float h = fmaxf((i & 1) ? zz.y : zz.x, 0.0f);
                                 const float4 w = W4[i];
-                                const uint64_t hh = tc::f32x2(h[i], h[i]);
+                                const uint64_t hh = tc::f32x2(h, h);
                                 o01 = tc::fma_f32x2(hh, tc::f32x2(w.x, w.y), o01);
                                 o23 = tc::fma_f32x2(hh, tc::f32x2(w.z, w.w), o23);
                             }
@@ -969,8 +1010,9 @@ bool decode_tc_supported(const RenderArgs &a, bool bf16, size_t *smem)
     return L.total <= kSmemLimit;
 }
 
-cudaError_t launch_decode_tc(const RenderArgs &a, bool bf16, cudaStream_t st)
+cudaError_t launch_decode_tc(const RenderArgs &a, bool bf16, cudaStream_t st, int *n_kernels)
 {
+    *n_kernels = 1;
     cudaError_t e;
     const int bulk_ok_ws = ((uintptr_t)a.nbr % 16 == 0) && ((uintptr_t)a.nbr_dist % 16 == 0);
     const WsLayout W = ws_layout(a, bf16);
@@ -978,10 +1020,13 @@ cudaError_t launch_decode_tc(const RenderArgs &a, bool bf16, cudaStream_t st)
         auto kern = bf16 ? k_decode_ws<true> : k_decode_ws<false>;
         if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, W.total)) != cudaSuccess)
             return e;
+        if (ws_image_bytes(W) > kWsImageMax || (uintptr_t)a.wimg % 16 != 0) return cudaErrorInvalidValue;
         int64_t grid = a.num_sms;
         const int64_t tiles = div_up(a.capacity > 0 ? a.capacity : 1, kTcTile);
         if (grid > tiles) grid = tiles;
+        (bf16 ? k_ws_image<true> : k_ws_image<false>)<<<(unsigned)a.num_sms, 256, 0, st>>>(a, W);
         kern<<<(unsigned)grid, kWsThreads, W.total, st>>>(a, W, bulk_ok_ws);
+        *n_kernels = 2;
         return cudaGetLastError();
     }
     const TcLayout L = tc_layout(a, bf16);

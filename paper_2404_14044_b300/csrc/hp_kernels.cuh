@@ -8,7 +8,7 @@ namespace hp {
 // Kernel ids of the per-kernel profiler (hp_profile_*).
 enum KernelId {
     KID_PROJECT = 0, KID_SCAN, KID_SCATTER, KID_SORT, KID_SEARCH, KID_PACK, KID_DECODE, KID_COMPOSITE,
-    KID_COMPOSITE_BWD, KID_DECODE_BWD, KID_PROP_INFER, KID_SEARCH_FALLBACK, KID_SEARCH_WIDE, KID_COUNT
+    KID_COMPOSITE_BWD, KID_DECODE_BWD, KID_PROP_INFER, KID_SEARCH_FALLBACK, KID_SEARCH_WIDE, KID_RAY_TABLE, KID_COUNT
 };
 
 // Optional CUDA-event pairs around each launch, on the launching stream.
@@ -18,6 +18,7 @@ struct Prof {
     int n = 0;
     cudaEvent_t *ev = nullptr;   // 2 * cap
     int *kid = nullptr;          // cap
+    int *nk = nullptr;           // cap: kernels launched between the two events
 };
 
 inline void prof_begin(Prof *p, cudaStream_t st, int kid)
@@ -28,10 +29,11 @@ inline void prof_begin(Prof *p, cudaStream_t st, int kid)
     }
 }
 
-inline void prof_end(Prof *p, cudaStream_t st)
+inline void prof_end(Prof *p, cudaStream_t st, int kernels = 1)
 {
     if (p && p->on && p->n < p->cap) {
         cudaEventRecord(p->ev[2 * p->n + 1], st);
+        p->nk[p->n] = kernels;
         ++p->n;
     }
 }
@@ -144,7 +146,12 @@ struct RenderArgs {
     float *rgb;              // [R*3]
     float *wsum;             // [R]
     int num_sms;
+    unsigned char *wimg;     // [kWsImageMax] the tensor-core decode's weight image (16-byte aligned)
+    uint32_t *tile_ctr;      // the tensor-core decode's tile counter
 };
+
+// Largest weight image of the tensor-core decode (its shared-memory limit).
+constexpr int kWsImageMax = 227 * 1024;
 
 __global__ void k_scan(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int64_t n, uint64_t *flags,
                        uint32_t *ticket, ErrWord *err, uint32_t spin_limit, int32_t skip_tile);
@@ -216,7 +223,8 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof);
 size_t render_smem_bytes(const RenderArgs &a);
 cudaError_t launch_render(const RenderArgs &a, cudaStream_t st, Prof *prof);
 bool decode_tc_supported(const RenderArgs &a, bool bf16, size_t *smem);
-cudaError_t launch_decode_tc(const RenderArgs &a, bool bf16, cudaStream_t st);
+// n_kernels: CUDA kernels launched (the weight image and the decode, or the decode alone)
+cudaError_t launch_decode_tc(const RenderArgs &a, bool bf16, cudaStream_t st, int *n_kernels);
 cudaError_t launch_mma_selftest(const uint16_t *A, const uint16_t *B, float *D, int K, int N, int flags, ErrWord *err,
                                 cudaStream_t st);
 

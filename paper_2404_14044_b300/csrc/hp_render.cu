@@ -265,8 +265,9 @@ cudaError_t launch_render(const RenderArgs &a, cudaStream_t st, Prof *prof)
     const bool bf16 = a.decode == HP_DECODE_BF16;
     if (a.decode != HP_DECODE_FP32_SIMT && decode_tc_supported(a, bf16, nullptr)) {
         prof_begin(prof, st, KID_DECODE);
-        e = launch_decode_tc(a, bf16, st);
-        prof_end(prof, st);
+        int nk = 1;
+        e = launch_decode_tc(a, bf16, st, &nk);
+        prof_end(prof, st, nk);
         if (e != cudaSuccess) return e;
         prof_begin(prof, st, KID_COMPOSITE);
         k_composite<<<(unsigned)div_up(a.R, 256), 256, 0, st>>>(a);

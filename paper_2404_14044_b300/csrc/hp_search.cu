@@ -1302,10 +1302,10 @@ cudaError_t search_pass(const SearchArgs &a, cudaStream_t st, Prof *prof, int ki
     }
     // pm_cnt: cleared with the tickets by launch_search
     prof_begin(prof, st, kid);
-    if (point_major && a.n_points > 0)
-        k_search_splat<<<(unsigned)div_up(a.n_points, 256), 256, 0, st>>>(a);
+    const bool splat = point_major && a.n_points > 0;
+    if (splat) k_search_splat<<<(unsigned)div_up(a.n_points, 256), 256, 0, st>>>(a);
     lane_k<<<(unsigned)blocks, kLaneWarps * 32, lsm, st>>>(a);
-    prof_end(prof, st);
+    prof_end(prof, st, splat ? 2 : 1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     SearchArgs b = a;
     b.ray_map = a.wide;
@@ -1330,7 +1330,9 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof)
     cudaError_t e;
     if (a.raytab_stale) {
         const int64_t npix = (int64_t)a.cam.width * a.cam.height;
+        prof_begin(prof, st, KID_RAY_TABLE);
         k_ray_table<<<(unsigned)div_up(npix, 256), 256, 0, st>>>(a.cam, a.mode, a.rdd, a.raytab);
+        prof_end(prof, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const int64_t tiles = div_up(a.R, kPackRays);

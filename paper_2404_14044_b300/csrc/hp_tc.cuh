@@ -278,16 +278,28 @@ __device__ __forceinline__ uint64_t fma_f32x2(uint64_t a, uint64_t b, uint64_t c
     return d;
 }
 
-// split_f16x2_same_scale with the remainder taken as one packed subtraction
-// (the same roundings).
-__device__ __forceinline__ void split_f16x2_same_scale_p(float x0, float x1, uint32_t &hi, uint32_t &lo)
+// ReLU and the two-term FP16 split of a pair (x0 in the low half, x1 in the
+// high half of each result): hi = fp16(max(x, 0)) rounded toward zero, lo =
+// fp16(max(x, 0) - hi) rounded to nearest.  Rounding hi toward zero keeps the
+// remainder x - hi non-negative, so the clamp of each conversion applies the
+// ReLU to both terms (x < 0: hi = 0, and the remainder x clamps to 0).  The
+// remainder is exact in FP32; hi + lo carries about 22 significant bits.
+__device__ __forceinline__ void split_relu_f16x2(uint64_t z, uint32_t &hi, uint32_t &lo)
 {
-    const __half2 h = __floats2half2_rn(x0, x1);
-    const float2 hf = __half22float2(h);
-    const float2 r = f32x2_unpack(sub_f32x2(f32x2(x0, x1), f32x2(hf.x, hf.y)));
-    const __half2 l = __floats2half2_rn(r.x, r.y);
-    hi = *reinterpret_cast<const uint32_t *>(&h);
-    lo = *reinterpret_cast<const uint32_t *>(&l);
+    const float2 x = f32x2_unpack(z);
+    asm("cvt.rz.relu.f16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(x.y), "f"(x.x));
+    const float2 hf = __half22float2(*reinterpret_cast<const __half2 *>(&hi));
+    const float2 r = f32x2_unpack(sub_f32x2(z, f32x2(hf.x, hf.y)));
+    asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(r.y), "f"(r.x));
+}
+
+// ReLU and BF16 rounding (to nearest) of a pair, packed as above.
+__device__ __forceinline__ uint32_t relu_bf16x2(uint64_t z)
+{
+    const float2 x = f32x2_unpack(z);
+    uint32_t r;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(x.y), "f"(x.x));
+    return r;
 }
 
 __device__ __forceinline__ void split_f16(float x, __half &hi, __half &lo)

@@ -32,7 +32,7 @@ SYMBOLS = ("hp_create", "hp_destroy", "hp_workspace_size", "hp_window", "hp_set_
            "hp_debug_fault", "hp_profile_start", "hp_profile_stop", "hp_profile_kernel_name",
            "hp_selftest_mma", "hp_scan_noalloc", "hp_proposal_infer", "hp_proposal_train_step",
            "hp_search_sample_proposal", "hp_search_sample_learned", "hp_status_string", "hp_version")
-PROF_KERNELS = 13
+PROF_KERNELS = 14
 PROP_PARAMS = 1666
 PROP_BINS = 16
 
@@ -101,7 +101,7 @@ def lib():
         L.hp_get_status.argtypes = [vp, vp, C.POINTER(i32), C.POINTER(i64)]
         L.hp_debug_fault.argtypes = [vp, i32, i32]
         L.hp_profile_start.argtypes = [vp, i32]
-        L.hp_profile_stop.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(i32)]
+        L.hp_profile_stop.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(i32), C.POINTER(i32)]
         L.hp_profile_kernel_name.argtypes = [i32]
         L.hp_profile_kernel_name.restype = C.c_char_p
         L.hp_scan_noalloc.argtypes = [vp, vp, i64, vp, vp]
@@ -443,11 +443,13 @@ class HashPoint:
         _check(lib().hp_profile_start(self._ctx, int(max_launches)), "hp_profile_start")
 
     def profile_stop(self):
-        """{kernel name: (total ms, launches)} since profile_start (syncs)."""
+        """{kernel name: (total ms, timed launches, CUDA kernels run)} since
+        profile_start (syncs)."""
         ms = (C.c_double * PROF_KERNELS)()
         n = (C.c_int32 * PROF_KERNELS)()
-        _check(lib().hp_profile_stop(self._ctx, ms, n), "hp_profile_stop")
-        return {lib().hp_profile_kernel_name(i).decode(): (ms[i], n[i]) for i in range(PROF_KERNELS)}
+        nk = (C.c_int32 * PROF_KERNELS)()
+        _check(lib().hp_profile_stop(self._ctx, ms, n, nk), "hp_profile_stop")
+        return {lib().hp_profile_kernel_name(i).decode(): (ms[i], n[i], nk[i]) for i in range(PROF_KERNELS)}
 
     def debug_fault(self, skip_tile: int, spin_limit: int = 0):
         _check(lib().hp_debug_fault(self._ctx, int(skip_tile), int(spin_limit)), "hp_debug_fault")
