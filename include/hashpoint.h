@@ -312,7 +312,7 @@ hp_status hp_debug_fault(hp_ctx *ctx, int32_t skip_tile, int32_t spin_limit);
  * CUDA kernels those launches ran into ms[HP_PROF_KERNELS],
  * launches[HP_PROF_KERNELS] and kernels[HP_PROF_KERNELS] (any may be NULL),
  * and stops recording.  Kernel ids: see hp_profile_kernel_name. */
-#define HP_PROF_KERNELS 14
+#define HP_PROF_KERNELS 15
 hp_status hp_profile_start(hp_ctx *ctx, int32_t max_launches);
 hp_status hp_profile_stop(hp_ctx *ctx, double *ms, int32_t *launches, int32_t *kernels);
 const char *hp_profile_kernel_name(int32_t id);

@@ -322,7 +322,8 @@ const char *hp_profile_kernel_name(int32_t id)
     static const char *names[KID_COUNT] = {"k_project_count", "k_scan", "k_scatter", "k_bucket_sort",
                                            "k_search_select", "k_pack_samples", "k_aggregate_decode",
                                            "k_composite", "k_composite_bwd", "k_decode_bwd", "k_prop_infer",
-                                           "k_search_select_fallback", "k_search_select_wide", "k_ray_table"};
+                                           "k_search_select_fallback", "k_search_select_wide", "k_ray_table",
+                                           "k_clear"};
     static_assert(KID_COUNT == HP_PROF_KERNELS, "profiler kernel count");
     return (id >= 0 && id < KID_COUNT) ? names[id] : "unknown";
 }

@@ -72,6 +72,8 @@ __device__ __forceinline__ void add_world(float *gp, int id, const Cam &cam, flo
 
 __global__ void __launch_bounds__(256) k_composite_bwd(const BwdArgs a)
 {
+    grid_dep_wait();
+    grid_dep_trigger();
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= a.R) return;
     const int64_t o = __ldg(a.sample_offset + r);
@@ -157,6 +159,8 @@ __device__ __forceinline__ void tile_matmul(const float *__restrict__ W, const f
 
 __global__ void __launch_bounds__(kBwdThreads, 2) k_decode_bwd(const BwdArgs a, const BwdLayout L)
 {
+    grid_dep_wait();
+    grid_dep_trigger();
     extern __shared__ __align__(16) unsigned char smem[];
     float *feat = reinterpret_cast<float *>(smem + L.feat);    // [F][32]
     float *act[2] = {reinterpret_cast<float *>(smem + L.act0), reinterpret_cast<float *>(smem + L.act1)};
@@ -361,7 +365,7 @@ cudaError_t launch_backward(const BwdArgs &a, cudaStream_t st, Prof *prof)
     cudaError_t e;
     if (a.R <= 0) return cudaSuccess;
     prof_begin(prof, st, KID_COMPOSITE_BWD);
-    k_composite_bwd<<<(unsigned)div_up(a.R, 256), 256, 0, st>>>(a);
+    launch_chained(k_composite_bwd, (unsigned)div_up(a.R, 256), 256, 0, st, a);
     prof_end(prof, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const BwdLayout L = bwd_layout(a);
@@ -372,7 +376,7 @@ cudaError_t launch_backward(const BwdArgs &a, cudaStream_t st, Prof *prof)
     const int64_t tiles = div_up(a.capacity > 0 ? a.capacity : 1, kBwdTile);
     if (grid > tiles) grid = tiles;
     prof_begin(prof, st, KID_DECODE_BWD);
-    k_decode_bwd<<<(unsigned)grid, kBwdThreads, L.total, st>>>(a, L);
+    launch_chained(k_decode_bwd, (unsigned)grid, kBwdThreads, L.total, st, a, L);
     prof_end(prof, st);
     return cudaGetLastError();
 }

@@ -27,6 +27,8 @@ __global__ void __launch_bounds__(256) k_project_count(const float *__restrict__
                                                        uint32_t *__restrict__ cnt, uint2 *__restrict__ keyrank,
                                                        uint32_t *__restrict__ zmin_enc)
 {
+    grid_dep_wait();
+    grid_dep_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const bool in = i < N;
@@ -59,6 +61,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t *__restric
                                                       int64_t n, uint64_t *flags, uint32_t *ticket, ErrWord *err,
                                                       uint32_t spin_limit, int32_t skip_tile)
 {
+    grid_dep_wait();
+    grid_dep_trigger();
     __shared__ int64_t s_tile;
     __shared__ int64_t s_prefix;
     __shared__ uint32_t s_warp[kScanThreads / 32];
@@ -117,6 +121,8 @@ __global__ void __launch_bounds__(256) k_scatter(const float *__restrict__ pts, 
                                                  const uint32_t *__restrict__ start, float4 *__restrict__ spts,
                                                  uint32_t *__restrict__ pcell)
 {
+    grid_dep_wait();
+    grid_dep_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const uint2 kr = keyrank[i];
@@ -148,6 +154,8 @@ __global__ void __launch_bounds__(256) k_bucket_sort(int64_t P, const uint32_t *
                                                      const float4 *__restrict__ tmp, float4 *__restrict__ spts,
                                                      uint32_t *__restrict__ big, uint32_t *__restrict__ n_big)
 {
+    grid_dep_wait();
+    grid_dep_trigger();
     const int64_t bkt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (bkt >= P) return;
     const uint32_t a = __ldg(start + bkt), n = __ldg(start + bkt + 1) - a;
@@ -186,6 +194,8 @@ __global__ void __launch_bounds__(256) k_bucket_sort_big(const uint32_t *__restr
                                                          const uint32_t *__restrict__ big,
                                                          const uint32_t *__restrict__ n_big)
 {
+    grid_dep_wait();
+    grid_dep_trigger();
     __shared__ float4 s_pts[8][kBigStage];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float4 *sp = s_pts[warp];
@@ -215,6 +225,28 @@ __global__ void __launch_bounds__(256) k_bucket_sort_big(const uint32_t *__restr
     }
 }
 
+// Zeroes n 32-bit words: the tickets, look-back words and counts a pass
+// starts from (a kernel, so that it chains with its neighbours).
+__global__ void __launch_bounds__(256) k_clear(uint32_t *__restrict__ p, int64_t n)
+{
+    grid_dep_wait();
+    grid_dep_trigger();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) p[i] = 0u;
+}
+
+cudaError_t launch_clear(void *p, size_t bytes, cudaStream_t st, Prof *prof)
+{
+    if (bytes % 4 != 0 || reinterpret_cast<uintptr_t>(p) % 4 != 0) return cudaErrorInvalidValue;
+    const int64_t n = (int64_t)(bytes / 4);
+    if (n == 0) return cudaSuccess;
+    const int64_t blocks = div_up(n, 256) < 4096 ? div_up(n, 256) : 4096;
+    prof_begin(prof, st, KID_CLEAR);
+    launch_chained(k_clear, (unsigned)blocks, 256, 0, st, static_cast<uint32_t *>(p), n);
+    prof_end(prof, st);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_build(const BuildArgs &a, cudaStream_t st, Prof *prof)
 {
     cudaError_t e;
@@ -228,23 +260,23 @@ cudaError_t launch_build(const BuildArgs &a, cudaStream_t st, Prof *prof)
     const char *zc = reinterpret_cast<const char *>(a.cnt);
     if (!(zf >= z0 + 3 * sizeof(uint32_t) && zc >= zf + sizeof(uint64_t) * (size_t)scan_tiles))
         return cudaErrorInvalidValue;
-    if ((e = cudaMemsetAsync(a.scan_ticket, 0, (size_t)(zc - z0) + sizeof(uint32_t) * (size_t)n_scan, st)) !=
+    if ((e = launch_clear(a.scan_ticket, (size_t)(zc - z0) + sizeof(uint32_t) * (size_t)n_scan, st, prof)) !=
         cudaSuccess)
         return e;
     if (a.N > 0) {
         prof_begin(prof, st, KID_PROJECT);
-        k_project_count<<<(unsigned)div_up(a.N, 256), 256, 0, st>>>(a.pts, a.N, a.cam, a.h, a.cnt, a.keyrank, a.zmin_enc);
+        launch_chained(k_project_count, (unsigned)div_up(a.N, 256), 256, 0, st, a.pts, a.N, a.cam, a.h, a.cnt, a.keyrank, a.zmin_enc);
         prof_end(prof, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     prof_begin(prof, st, KID_SCAN);
-    k_scan<<<(unsigned)scan_tiles, kScanThreads, 0, st>>>(a.cnt, a.start, n_scan, a.scan_flags, a.scan_ticket,
+    launch_chained(k_scan, (unsigned)scan_tiles, kScanThreads, 0, st, a.cnt, a.start, n_scan, a.scan_flags, a.scan_ticket,
                                                           a.err, a.spin_limit, a.skip_tile);
     prof_end(prof, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (a.N > 0) {
         prof_begin(prof, st, KID_SCATTER);
-        k_scatter<<<(unsigned)div_up(a.N, 256), 256, 0, st>>>(a.pts, a.N, a.cam, a.keyrank, a.start, a.spts, a.pcell);
+        launch_chained(k_scatter, (unsigned)div_up(a.N, 256), 256, 0, st, a.pts, a.N, a.cam, a.keyrank, a.start, a.spts, a.pcell);
         prof_end(prof, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -256,9 +288,9 @@ cudaError_t launch_bucket_sort(int64_t P, const uint32_t *start, const float4 *l
 {
     cudaError_t e;
     if ((e = cudaMemsetAsync(n_big, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
-    k_bucket_sort<<<(unsigned)div_up(P, 256), 256, 0, st>>>(P, start, list, out, big, n_big);
+    launch_chained(k_bucket_sort, (unsigned)div_up(P, 256), 256, 0, st, P, start, list, out, big, n_big);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_bucket_sort_big<<<kBigSortBlocks, 256, 0, st>>>(start, list, out, big, n_big);
+    launch_chained(k_bucket_sort_big, kBigSortBlocks, 256, 0, st, start, list, out, big, n_big);
     return cudaGetLastError();
 }
 

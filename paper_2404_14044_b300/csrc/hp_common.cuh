@@ -15,10 +15,21 @@ constexpr int kMaxK = 32;            // neighbours per candidate
 constexpr int kMaxSamples = 16;      // samples per ray
 constexpr int kSearchWarps = 8;
 constexpr int kScanThreads = 1024;
-constexpr int kScanItems = 8;        // per thread: tile = 2048 entries
+constexpr int kScanItems = 8;        // per thread: tile = 8192 entries
 constexpr int kScanTile = kScanThreads * kScanItems;
 constexpr uint32_t kSpinLimitDefault = 1u << 22;
 constexpr uint32_t kNoKey = 0xFFFFFFFFu;
+
+// ------------------------------------------- programmatic dependent launch
+// The kernels of a frame are launched with programmatic stream serialization
+// (launch_chained): a kernel's blocks may become resident while its
+// predecessor in the stream is still running, and wait in grid_dep_wait()
+// until that grid has completed and its memory operations are visible.  Every
+// kernel calls grid_dep_wait() before it touches global memory (a no-op when
+// it was launched without the attribute) and then grid_dep_trigger(), which
+// lets its own successor launch once every block of this grid has started.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // ------------------------------------------------------ device status word
 struct ErrWord {

@@ -172,6 +172,8 @@ __device__ __forceinline__ void store_operand4_ss(unsigned char *hi_base, unsign
 template <bool kBF16>
 __global__ void __launch_bounds__(kTcThreads, 1) k_decode_tc(const RenderArgs a, const TcLayout L, int bulk_ok)
 {
+    grid_dep_wait();
+    grid_dep_trigger();
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float *f32 = reinterpret_cast<float *>(smem + L.f32_block);
@@ -609,6 +611,8 @@ WsLayout ws_layout(const RenderArgs &a, bool bf16)
 template <bool kBF16>
 __global__ void k_ws_image(const RenderArgs a, const WsLayout L)
 {
+    grid_dep_wait();
+    grid_dep_trigger();
     const int gid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
     unsigned char *img = a.wimg;
     float *f32 = reinterpret_cast<float *>(img + L.a0[0]);
@@ -645,6 +649,8 @@ __global__ void k_ws_image(const RenderArgs a, const WsLayout L)
 template <bool kBF16>
 __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a, const WsLayout L, int bulk_ok)
 {
+    grid_dep_wait();
+    grid_dep_trigger();
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float *f32 = reinterpret_cast<float *>(smem + L.f32_block);
@@ -1024,8 +1030,8 @@ cudaError_t launch_decode_tc(const RenderArgs &a, bool bf16, cudaStream_t st, in
         int64_t grid = a.num_sms;
         const int64_t tiles = div_up(a.capacity > 0 ? a.capacity : 1, kTcTile);
         if (grid > tiles) grid = tiles;
-        (bf16 ? k_ws_image<true> : k_ws_image<false>)<<<(unsigned)a.num_sms, 256, 0, st>>>(a, W);
-        kern<<<(unsigned)grid, kWsThreads, W.total, st>>>(a, W, bulk_ok_ws);
+        launch_chained(bf16 ? k_ws_image<true> : k_ws_image<false>, (unsigned)a.num_sms, 256, 0, st, a, W);
+        launch_chained(kern, (unsigned)grid, kWsThreads, W.total, st, a, W, bulk_ok_ws);
         *n_kernels = 2;
         return cudaGetLastError();
     }
@@ -1037,7 +1043,7 @@ cudaError_t launch_decode_tc(const RenderArgs &a, bool bf16, cudaStream_t st, in
     const int64_t tiles = div_up(a.capacity > 0 ? a.capacity : 1, kTcTile);
     if (grid > tiles) grid = tiles;
     const int bulk_ok = ((uintptr_t)a.nbr % 16 == 0) && ((uintptr_t)a.nbr_dist % 16 == 0);
-    kern<<<(unsigned)grid, kTcThreads, L.total, st>>>(a, L, bulk_ok);
+    launch_chained(kern, (unsigned)grid, kTcThreads, L.total, st, a, L, bulk_ok);
     return cudaGetLastError();
 }
 

@@ -3,12 +3,35 @@
 
 #include "hp_common.cuh"
 
+#include <utility>
+
 namespace hp {
+
+// Launches a kernel with programmatic stream serialization: its blocks may
+// become resident while the previous kernel in the stream still runs, and
+// wait for it in grid_dep_wait() (every kernel of the library calls that
+// first).  Launch errors are also left for cudaGetLastError().
+template <typename... P, typename... A>
+inline cudaError_t launch_chained(void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A &&...args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+}
+
 
 // Kernel ids of the per-kernel profiler (hp_profile_*).
 enum KernelId {
     KID_PROJECT = 0, KID_SCAN, KID_SCATTER, KID_SORT, KID_SEARCH, KID_PACK, KID_DECODE, KID_COMPOSITE,
-    KID_COMPOSITE_BWD, KID_DECODE_BWD, KID_PROP_INFER, KID_SEARCH_FALLBACK, KID_SEARCH_WIDE, KID_RAY_TABLE, KID_COUNT
+    KID_COMPOSITE_BWD, KID_DECODE_BWD, KID_PROP_INFER, KID_SEARCH_FALLBACK, KID_SEARCH_WIDE, KID_RAY_TABLE, KID_CLEAR, KID_COUNT
 };
 
 // Optional CUDA-event pairs around each launch, on the launching stream.
@@ -37,6 +60,10 @@ inline void prof_end(Prof *p, cudaStream_t st, int kernels = 1)
         ++p->n;
     }
 }
+
+// Zeroes `bytes` (a multiple of 4, 4-byte aligned) at p with a chained
+// kernel (a memset would end the chain of programmatic launches).
+cudaError_t launch_clear(void *p, size_t bytes, cudaStream_t st, Prof *prof);
 
 struct BuildArgs {
     const float *pts;

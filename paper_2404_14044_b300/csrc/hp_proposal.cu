@@ -36,6 +36,8 @@ __device__ __forceinline__ int ray_pixel(const PropArgs &a, int64_t r) { return 
 
 __global__ void __launch_bounds__(256) k_prop_infer(const PropArgs a)
 {
+    grid_dep_wait();
+    grid_dep_trigger();
     __shared__ __align__(16) float w[kNP + 2];
     load_weights(a.weights_bf16, w);
     __syncthreads();
@@ -55,6 +57,8 @@ __global__ void __launch_bounds__(256) k_prop_infer(const PropArgs a)
 
 __global__ void __launch_bounds__(256) k_prop_train(const PropArgs a)
 {
+    grid_dep_wait();
+    grid_dep_trigger();
     __shared__ float w[kNP];
     for (int e = threadIdx.x; e < kNP; e += blockDim.x) w[e] = a.params[e];
     __syncthreads();
@@ -146,6 +150,8 @@ __global__ void __launch_bounds__(256) k_prop_train(const PropArgs a)
 __global__ void k_prop_adam(float *params, float *grad, float *m, float *v, uint16_t *bf16, const float *loss_cnt,
                             int step, float lr)
 {
+    grid_dep_wait();
+    grid_dep_trigger();
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= kNP) return;
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
@@ -167,7 +173,7 @@ cudaError_t launch_prop_infer(const PropArgs &a, cudaStream_t st, Prof *prof)
 {
     if (a.R <= 0) return cudaSuccess;
     prof_begin(prof, st, KID_PROP_INFER);
-    k_prop_infer<<<(unsigned)div_up(a.R, 256), 256, 0, st>>>(a);
+    launch_chained(k_prop_infer, (unsigned)div_up(a.R, 256), 256, 0, st, a);
     prof_end(prof, st);
     return cudaGetLastError();
 }
@@ -177,10 +183,10 @@ cudaError_t launch_prop_train(const PropArgs &a, float *m, float *v, int step, f
     cudaError_t e;
     if (a.loss && (e = cudaMemsetAsync(a.loss, 0, 2 * sizeof(float), st)) != cudaSuccess) return e;
     if (a.R > 0) {
-        k_prop_train<<<(unsigned)div_up(a.R, 256), 256, 0, st>>>(a);
+        launch_chained(k_prop_train, (unsigned)div_up(a.R, 256), 256, 0, st, a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    k_prop_adam<<<(unsigned)div_up(kNP, 256), 256, 0, st>>>(a.params, a.grad, m, v, a.weights_out, a.loss, step, lr);
+    launch_chained(k_prop_adam, (unsigned)div_up(kNP, 256), 256, 0, st, a.params, a.grad, m, v, a.weights_out, a.loss, step, lr);
     return cudaGetLastError();
 }
 

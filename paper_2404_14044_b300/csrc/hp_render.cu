@@ -115,6 +115,8 @@ __device__ __forceinline__ float sigmoidf(float x) { return 1.0f / (1.0f + expf(
 __global__ void __launch_bounds__(kRenderThreads) k_aggregate_decode(const RenderArgs a, int n_params, int maxw,
                                                                      int xa_off, int xb_off)
 {
+    grid_dep_wait();
+    grid_dep_trigger();
     extern __shared__ __align__(16) unsigned char smem[];
     float *prm = reinterpret_cast<float *>(smem);
     float *XA = reinterpret_cast<float *>(smem + xa_off);
@@ -233,6 +235,8 @@ __global__ void __launch_bounds__(kRenderThreads) k_aggregate_decode(const Rende
 // Eq. 2: tau_j = exp(-sum_{k<j} sigma_k Delta_k), weight tau_j (1 - exp(-sigma_j Delta_j)).
 __global__ void __launch_bounds__(256) k_composite(const RenderArgs a)
 {
+    grid_dep_wait();
+    grid_dep_trigger();
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= a.R) return;
     int64_t o = __ldg(a.sample_offset + r);
@@ -270,7 +274,7 @@ cudaError_t launch_render(const RenderArgs &a, cudaStream_t st, Prof *prof)
         prof_end(prof, st, nk);
         if (e != cudaSuccess) return e;
         prof_begin(prof, st, KID_COMPOSITE);
-        k_composite<<<(unsigned)div_up(a.R, 256), 256, 0, st>>>(a);
+        launch_chained(k_composite, (unsigned)div_up(a.R, 256), 256, 0, st, a);
         prof_end(prof, st);
         return cudaGetLastError();
     }
@@ -289,11 +293,11 @@ cudaError_t launch_render(const RenderArgs &a, cudaStream_t st, Prof *prof)
     if (grid > max_tiles) grid = max_tiles;
     if (grid < 1) grid = 1;
     prof_begin(prof, st, KID_DECODE);
-    k_aggregate_decode<<<(unsigned)grid, kRenderThreads, L.total, st>>>(a, L.n_params, L.maxw, (int)L.xa, (int)L.xb);
+    launch_chained(k_aggregate_decode, (unsigned)grid, kRenderThreads, L.total, st, a, L.n_params, L.maxw, (int)L.xa, (int)L.xb);
     prof_end(prof, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     prof_begin(prof, st, KID_COMPOSITE);
-    k_composite<<<(unsigned)div_up(a.R, 256), 256, 0, st>>>(a);
+    launch_chained(k_composite, (unsigned)div_up(a.R, 256), 256, 0, st, a);
     prof_end(prof, st);
     return cudaGetLastError();
 }

@@ -122,6 +122,8 @@ __device__ __forceinline__ uint64_t warp_max_u64(uint64_t v)
 // selection takes candidates in (t, id) order whatever their order.
 __global__ void __launch_bounds__(256) k_search_splat(const SearchArgs a)
 {
+    grid_dep_wait();
+    grid_dep_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int Hp = a.cam.height + 2 * a.h;
     const int64_t nv = (int64_t)__ldg(a.start + (int64_t)a.Wp * Hp);
@@ -233,6 +235,8 @@ __device__ __forceinline__ void knn_insert(uint64_t (&keys)[KB], uint64_t x)
 // by every frame whose intrinsics are unchanged.
 __global__ void __launch_bounds__(256) k_ray_table(Cam cam, int mode, float rdd, float4 *__restrict__ tab)
 {
+    grid_dep_wait();
+    grid_dep_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)cam.width * cam.height) return;
     const int pu = (int)(i % cam.width), pv = (int)(i / cam.width);
@@ -616,6 +620,8 @@ __device__ __forceinline__ void wide_ray(const SearchArgs &a, const float2 *inte
 template <int KB>
 __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select_wide(const SearchArgs a)
 {
+    grid_dep_wait();
+    grid_dep_trigger();
     extern __shared__ __align__(16) unsigned char smem[];
     const SearchSmem L = search_layout();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1088,6 +1094,8 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
 template <int KB, int kMode>
 __global__ void __launch_bounds__(kLaneWarps * 32, lane_blocks_per_sm(KB)) k_search_select(const SearchArgs a)
 {
+    grid_dep_wait();
+    grid_dep_trigger();
     constexpr bool kLearned = kMode == 2;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1153,6 +1161,8 @@ constexpr int kPackWarps = kPackRays / 32;
 
 __global__ void __launch_bounds__(kPackRays) k_pack_samples(const SearchArgs a)
 {
+    grid_dep_wait();
+    grid_dep_trigger();
     __shared__ int64_t s_tile, s_prefix;
     __shared__ int s_warp[kPackWarps];
     __shared__ int s_total;
@@ -1296,15 +1306,15 @@ cudaError_t search_pass(const SearchArgs &a, cudaStream_t st, Prof *prof, int ki
         w.pm_cnt = nullptr;                      // no point-major slots: the warps walk
         const int64_t wb = std::min<int64_t>(div_up(a.R, kSearchWarps), (int64_t)a.n_sm * 4);
         prof_begin(prof, st, kid);
-        wide_k<<<(unsigned)wb, kSearchWarps * 32, wsm, st>>>(w);
+        launch_chained(wide_k, (unsigned)wb, kSearchWarps * 32, wsm, st, w);
         prof_end(prof, st);
         return cudaGetLastError();
     }
     // pm_cnt: cleared with the tickets by launch_search
     prof_begin(prof, st, kid);
     const bool splat = point_major && a.n_points > 0;
-    if (splat) k_search_splat<<<(unsigned)div_up(a.n_points, 256), 256, 0, st>>>(a);
-    lane_k<<<(unsigned)blocks, kLaneWarps * 32, lsm, st>>>(a);
+    if (splat) launch_chained(k_search_splat, (unsigned)div_up(a.n_points, 256), 256, 0, st, a);
+    launch_chained(lane_k, (unsigned)blocks, kLaneWarps * 32, lsm, st, a);
     prof_end(prof, st, splat ? 2 : 1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     SearchArgs b = a;
@@ -1318,7 +1328,7 @@ cudaError_t search_pass(const SearchArgs &a, cudaStream_t st, Prof *prof, int ki
     }
     const int64_t wblocks = std::min<int64_t>(div_up(a.R, kSearchWarps), (int64_t)a.n_sm * 4);
     prof_begin(prof, st, KID_SEARCH_WIDE);
-    wide_k<<<(unsigned)wblocks, kSearchWarps * 32, wsm, st>>>(b);
+    launch_chained(wide_k, (unsigned)wblocks, kSearchWarps * 32, wsm, st, b);
     prof_end(prof, st);
     return cudaGetLastError();
 }
@@ -1331,7 +1341,7 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof)
     if (a.raytab_stale) {
         const int64_t npix = (int64_t)a.cam.width * a.cam.height;
         prof_begin(prof, st, KID_RAY_TABLE);
-        k_ray_table<<<(unsigned)div_up(npix, 256), 256, 0, st>>>(a.cam, a.mode, a.rdd, a.raytab);
+        launch_chained(k_ray_table, (unsigned)div_up(npix, 256), 256, 0, st, a.cam, a.mode, a.rdd, a.raytab);
         prof_end(prof, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -1352,7 +1362,7 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof)
           reinterpret_cast<const char *>(a.wide_count) >= z0 && reinterpret_cast<const char *>(a.lane_units) >= z0 &&
           reinterpret_cast<const char *>(a.pull) >= z0))
         return cudaErrorInvalidValue;
-    if ((e = cudaMemsetAsync(a.ticket, 0, (size_t)(ze - z0), st)) != cudaSuccess) return e;
+    if ((e = launch_clear(a.ticket, (size_t)(ze - z0), st, prof)) != cudaSuccess) return e;
     if ((e = search_pass(a, st, prof, KID_SEARCH)) != cudaSuccess) return e;
     if ((a.interval || a.prop_w) && a.fallback) {
         // plain search for the rays the restricted search flagged: few and
@@ -1364,17 +1374,17 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof)
         b.count_ptr = a.fallback_count;
         b.raytab_stale = 0;
         b.pm_cnt = nullptr;
-        if ((e = cudaMemsetAsync(a.pull, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+        if ((e = launch_clear(a.pull, sizeof(unsigned long long), st, prof)) != cudaSuccess) return e;
         auto wide_k = a.K <= 4 ? k_search_select_wide<4> : a.K <= 8 ? k_search_select_wide<8>
                     : a.K <= 16 ? k_search_select_wide<16> : k_search_select_wide<32>;
         const int64_t wblocks = std::min<int64_t>(div_up(a.R, kSearchWarps), (int64_t)a.n_sm * 4);
         prof_begin(prof, st, KID_SEARCH_FALLBACK);
-        wide_k<<<(unsigned)wblocks, kSearchWarps * 32, search_smem_bytes(), st>>>(b);
+        launch_chained(wide_k, (unsigned)wblocks, kSearchWarps * 32, search_smem_bytes(), st, b);
         prof_end(prof, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     prof_begin(prof, st, KID_PACK);
-    k_pack_samples<<<(unsigned)tiles, kPackRays, 0, st>>>(a);
+    launch_chained(k_pack_samples, (unsigned)tiles, kPackRays, 0, st, a);
     prof_end(prof, st);
     return cudaGetLastError();
 }

@@ -32,7 +32,7 @@ SYMBOLS = ("hp_create", "hp_destroy", "hp_workspace_size", "hp_window", "hp_set_
            "hp_debug_fault", "hp_profile_start", "hp_profile_stop", "hp_profile_kernel_name",
            "hp_selftest_mma", "hp_scan_noalloc", "hp_proposal_infer", "hp_proposal_train_step",
            "hp_search_sample_proposal", "hp_search_sample_learned", "hp_status_string", "hp_version")
-PROF_KERNELS = 14
+PROF_KERNELS = 15
 PROP_PARAMS = 1666
 PROP_BINS = 16
 
