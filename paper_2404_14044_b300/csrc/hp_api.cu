@@ -157,6 +157,7 @@ size_t search_region_bytes(int64_t R, int n_max, int K)
     return al(256) + al(8 * (size_t)div_up(R > 0 ? R : 1, 256)) + al(16 * slots) + 2 * al(4 * slots * K) +
            al(4 * (size_t)(R > 0 ? R : 1)) +         // fallback list of the proposal-restricted search
            al(4 * (size_t)(R > 0 ? R : 1)) +         // rays handed to the warp-per-ray search
+           al(4 * (size_t)(R > 0 ? R : 1)) +         // pixels whose point-major slots overflowed
            al(8 * (size_t)(R > 0 ? R : 1)) +         // intervals the learned search inferred for them
            al(4 * (size_t)(R > 0 ? R : 1)) +         // point-major pass: candidates per pixel
            al(8 * (size_t)kPmCap * (size_t)(R > 0 ? R : 1));   // ... and the candidates
@@ -558,6 +559,9 @@ static hp_status search_impl(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n
         a.fallback = reinterpret_cast<int32_t *>(base + o);  o += al(4 * (size_t)n_rays);
         a.fallback_count = a.ticket + 1;
         a.wide = reinterpret_cast<int32_t *>(base + o);      o += al(4 * (size_t)n_rays);
+        a.ovf = reinterpret_cast<int32_t *>(base + o);       o += al(4 * (size_t)n_rays);
+        a.ovf_count = a.ticket + 6;
+        a.ovf_pull = a.ticket + 7;
         a.interval_buf = reinterpret_cast<float2 *>(base + o); o += al(8 * (size_t)n_rays);
         a.pm_t = reinterpret_cast<float *>(base + o);
         a.pm_i = reinterpret_cast<uint32_t *>(base + o + 4 * (size_t)kPmCap * (size_t)n_rays);

@@ -124,6 +124,9 @@ struct SearchArgs {
     uint32_t *fallback_count;
     int32_t *wide;           // rays with more candidates than a lane holds (original indices)
     uint32_t *wide_count;
+    int32_t *ovf;            // whole frames: pixels whose point-major slots overflowed (the pass lists them)
+    uint32_t *ovf_count;
+    uint32_t *ovf_pull;      // next of them for the lane kernel's warps
     unsigned long long *pull;    // next listed ray of the warp-per-ray search
     uint32_t *lane_units;    // next tile / group of 32 rays of the lane-per-ray search
     int n_sm;                // multiprocessors of the device (grid sizing)

@@ -148,6 +148,8 @@ __global__ void __launch_bounds__(256) k_search_splat(const SearchArgs a)
             float t;
             if (!accept_point(a, ray, p, a.cam.t_near, a.cam.t_far, t)) continue;
             const uint32_t pos = atomicAdd(a.pm_cnt + pix, 1u);
+            // the first append past the slots lists the pixel (once)
+            if (pos == (uint32_t)kPmCap) a.ovf[atomicAdd(a.ovf_count, 1u)] = pix;
             if (pos < (uint32_t)kPmCap) {
                 a.pm_t[pix * kPmCap + pos] = t;
                 a.pm_i[pix * kPmCap + pos] = (uint32_t)i;
@@ -732,7 +734,7 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
         // the pass left this ray's accepted points (any order) in its slots;
         // slots that overflowed hold an arbitrary subset: the warp search walks
         const uint32_t cnt = __ldg(a.pm_cnt + pix);
-        if (cnt > (uint32_t)kPmCap) return false;
+        if (cnt > (uint32_t)kPmCap) return true;   // searched already, from the overflow list
         // Candidates the selection can reach: it processes at most prune_m
         // candidates (every one multiplies T by at most 1 - alpha_min, and it
         // stops once gamma T <= eps_w), and a processed candidate's
@@ -1118,6 +1120,24 @@ __global__ void __launch_bounds__(kLaneWarps * 32, lane_blocks_per_sm(KB)) k_sea
     const int64_t n_units = frame ? (int64_t)tiles_x * ((H + 3) >> 2)
                                   : ((a.count_ptr ? (int64_t)*a.count_ptr : a.R) + 31) / 32;
     const int64_t R_eff = frame ? npix : (a.count_ptr ? (int64_t)*a.count_ptr : a.R);
+    if constexpr (kMode == 3) {
+        // the pixels whose slots overflowed walk their whole window with the
+        // warp-per-ray search: the heaviest rays of the frame, so the warps
+        // take them before any tile (their latency then overlaps the tiles)
+        float4 *cp = reinterpret_cast<float4 *>(reinterpret_cast<float *>(smem) + warp * (kLaneCap * 32));
+        uint64_t *ck = reinterpret_cast<uint64_t *>(cp + kCandCap);
+        static_assert(kCandCap * (sizeof(float4) + sizeof(uint64_t)) <= kLaneCap * 32 * sizeof(float),
+                      "the warp search's lists fit one warp's depth column");
+        const uint32_t n_ovf = *a.ovf_count;
+        for (;;) {
+            uint32_t i = 0;
+            if (lane == 0) i = atomicAdd(a.ovf_pull, 1u);
+            i = __shfl_sync(kFull, i, 0);
+            if (i >= n_ovf) break;
+            wide_ray<KB>(a, nullptr, (int64_t)__ldg(a.ovf + i), cp, ck);
+        }
+        __syncwarp();
+    }
     for (;;) {
         unsigned int u = 0;
         if (lane == 0) u = atomicAdd(a.lane_units, 1u);
