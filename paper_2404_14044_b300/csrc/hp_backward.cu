@@ -124,9 +124,11 @@ __global__ void __launch_bounds__(256) k_composite_bwd(const BwdArgs a)
 
 // out[u][s] = sum_i W[u][i] in[i][s] (+ b[u]) for the tile's 32 samples, u <
 // n_out, i < n_in; W row-major [n_out][n_in] in global memory.  Thread t
-// holds samples 4 (t % 8) .. +3 and units 4 (t / 8) .. +3: each step reads
-// one 16-byte activation vector and four weights for 16 multiply-adds.
-// transposed: out[i][s] = sum_u W[u][i] in[u][s] (the backward through W).
+// holds samples 4 (t % 8) .. +3 and units 4 (t / 8) .. +3 (16 multiply-adds
+// per summed index, each output's sum in index order).  When the widths are
+// multiples of 4 the weights come as 16-byte loads: forward, four summed
+// indices of a unit's row at a time; transposed (the backward through W,
+// out[i][s] = sum_u W[u][i] in[u][s]), the four output units of a row.
 template <bool kTransposed>
 __device__ __forceinline__ void tile_matmul(const float *__restrict__ W, const float *__restrict__ bias, int n_out,
                                             int n_in, const float *in, float (&acc)[4][4], int sb, int ub)
@@ -136,9 +138,49 @@ __device__ __forceinline__ void tile_matmul(const float *__restrict__ W, const f
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[s][q] = (!kTransposed && bias && 4 * ub + q < n_out) ? __ldg(bias + 4 * ub + q) : 0.0f;
     if (4 * ub >= n_out) return;
-    const int nsum = kTransposed ? n_in : n_in;     // summed dimension length (rows of `in`)
+    auto fma16 = [&](const float (&w)[4], const float4 x) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            acc[0][q] = fmaf(w[q], x.x, acc[0][q]);
+            acc[1][q] = fmaf(w[q], x.y, acc[1][q]);
+            acc[2][q] = fmaf(w[q], x.z, acc[2][q]);
+            acc[3][q] = fmaf(w[q], x.w, acc[3][q]);
+        }
+    };
+    const bool vec = (n_in & 3) == 0 && (n_out & 3) == 0 && (reinterpret_cast<uintptr_t>(W) & 15) == 0;
+    if (vec && kTransposed) {
+        // W[k][4ub .. 4ub+3]: one 16-byte load per summed index (eight in flight)
+#pragma unroll 8
+        for (int k = 0; k < n_in; ++k) {
+            const float4 x = *reinterpret_cast<const float4 *>(in + k * kBwdTile + 4 * sb);
+            const float4 w4 = __ldg(reinterpret_cast<const float4 *>(W + (int64_t)k * n_out + 4 * ub));
+            const float w[4] = {w4.x, w4.y, w4.z, w4.w};
+            fma16(w, x);
+        }
+        return;
+    }
+    if (vec) {
+        // W[4ub + q][k .. k+3]: four 16-byte loads per four summed indices
 #pragma unroll 4
-    for (int k = 0; k < nsum; ++k) {
+        for (int k0 = 0; k0 < n_in; k0 += 4) {
+            float4 wr[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                wr[q] = __ldg(reinterpret_cast<const float4 *>(W + (int64_t)(4 * ub + q) * n_in + k0));
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const float4 x = *reinterpret_cast<const float4 *>(in + (k0 + kk) * kBwdTile + 4 * sb);
+                float w[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    w[q] = kk == 0 ? wr[q].x : kk == 1 ? wr[q].y : kk == 2 ? wr[q].z : wr[q].w;
+                fma16(w, x);
+            }
+        }
+        return;
+    }
+#pragma unroll 4
+    for (int k = 0; k < n_in; ++k) {
         const float4 x = *reinterpret_cast<const float4 *>(in + k * kBwdTile + 4 * sb);
         float w[4];
 #pragma unroll
@@ -147,13 +189,7 @@ __device__ __forceinline__ void tile_matmul(const float *__restrict__ W, const f
             // forward: W[u][k] (row u of n_in); transposed: W[k][u] (row k of n_out)
             w[q] = u < n_out ? __ldg(kTransposed ? W + (int64_t)k * n_out + u : W + (int64_t)u * n_in + k) : 0.0f;
         }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            acc[0][q] = fmaf(w[q], x.x, acc[0][q]);
-            acc[1][q] = fmaf(w[q], x.y, acc[1][q]);
-            acc[2][q] = fmaf(w[q], x.z, acc[2][q]);
-            acc[3][q] = fmaf(w[q], x.w, acc[3][q]);
-        }
+        fma16(w, x);
     }
 }
 
@@ -303,6 +339,7 @@ __global__ void __launch_bounds__(kBwdThreads, 2) k_decode_bwd(const BwdArgs a, 
                 const int id_l = m < K ? __ldg(a.nbr + g * K + m) : -1;
                 const float d_l = id_l >= 0 ? __ldg(a.nbr_dist + g * K + m) : 1.0f;
                 const int mn = min(32, K - m0);
+                float sc_l = 0.0f;                   // lane m: dL/d|x_j - P_m| / |x_j - P_m|
                 for (int c0 = 0; c0 < mn; c0 += kNb) {
                     float fv[kNb][4];
                     int idv[kNb];
@@ -334,24 +371,34 @@ __global__ void __launch_bounds__(kBwdThreads, 2) k_decode_bwd(const BwdArgs a, 
                         }
 #pragma unroll
                         for (int off = 16; off > 0; off >>= 1) gw_part += __shfl_xor_sync(0xffffffffu, gw_part, off);
-                        if (dist > a.eps_d && a.grad_points && lane == 0) {
-                            const float gdist = -(gw_part / W) / (dist * dist);
-                            const float3 P = cam_point(a.cam, __ldg(a.points + 3 * (int64_t)id),
-                                                       __ldg(a.points + 3 * (int64_t)id + 1),
-                                                       __ldg(a.points + 3 * (int64_t)id + 2));
-                            const float vx = fmaf(tj, dd.x, -P.x), vy = fmaf(tj, dd.y, -P.y), vz = fmaf(tj, dd.z, -P.z);
-                            const float sc = gdist / dist;
-                            add_world(a.grad_points, id, a.cam, -sc * vx, -sc * vy, -sc * vz);
-                            gx0 = fmaf(sc, vx, gx0);
-                            gx1 = fmaf(sc, vy, gx1);
-                            gx2 = fmaf(sc, vz, gx2);
-                        }
+                        // the neighbour's lane keeps its distance gradient
+                        if (lane == ((c0 + q) & 31) && dist > a.eps_d) sc_l = (-(gw_part / W) / (dist * dist)) / dist;
                     }
                 }
+                // position gradients: each lane its own neighbour, the point
+                // loads of all lanes in flight together
+                if (a.grad_points && m < K && id_l >= 0 && d_l > a.eps_d) {
+                    const float3 P = cam_point(a.cam, __ldg(a.points + 3 * (int64_t)id_l),
+                                               __ldg(a.points + 3 * (int64_t)id_l + 1),
+                                               __ldg(a.points + 3 * (int64_t)id_l + 2));
+                    const float vx = fmaf(tj, dd.x, -P.x), vy = fmaf(tj, dd.y, -P.y), vz = fmaf(tj, dd.z, -P.z);
+                    add_world(a.grad_points, id_l, a.cam, -sc_l * vx, -sc_l * vy, -sc_l * vz);
+                    gx0 = fmaf(sc_l, vx, gx0);
+                    gx1 = fmaf(sc_l, vy, gx1);
+                    gx2 = fmaf(sc_l, vz, gx2);
+                }
             }
-            if (a.grad_points && lane == 0) {
-                const float gt = a.gt[g] + (gx0 * dd.x + gx1 * dd.y + gx2 * dd.z);
-                add_world(a.grad_points, __ldg(a.src + g), a.cam, gt * dd.x, gt * dd.y, gt * dd.z);
+            if (a.grad_points) {
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    gx0 += __shfl_xor_sync(0xffffffffu, gx0, off);
+                    gx1 += __shfl_xor_sync(0xffffffffu, gx1, off);
+                    gx2 += __shfl_xor_sync(0xffffffffu, gx2, off);
+                }
+                if (lane == 0) {
+                    const float gt = a.gt[g] + (gx0 * dd.x + gx1 * dd.y + gx2 * dd.z);
+                    add_world(a.grad_points, __ldg(a.src + g), a.cam, gt * dd.x, gt * dd.y, gt * dd.z);
+                }
             }
         }
         __syncthreads();
