@@ -33,6 +33,7 @@
 // order is independent of scheduling and blocks never wait on one another
 // while they search.
 #include <algorithm>
+#include <type_traits>
 
 #include "hp_kernels.cuh"
 #include "hp_proposal.cuh"
@@ -216,17 +217,30 @@ __device__ __forceinline__ void append_candidates(bool acc, uint64_t key, float4
     total += n;
 }
 
-// Insert x into the ascending register array keys (the largest falls off).
+// Insert x into the ascending register array keys (the largest falls off);
+// n counts the keys held (at most KB).  While fewer than 8 (or 16) are held
+// the slots above are empty, so the insertion runs over the first 8 (or 16)
+// only -- most neighbourhoods hold a few points.
 template <int KB>
-__device__ __forceinline__ void knn_insert(uint64_t (&keys)[KB], uint64_t x)
+__device__ __forceinline__ void knn_insert_n(uint64_t (&keys)[KB], uint64_t x, int &n)
 {
+    auto ins = [&](auto width) {
+        constexpr int kW = decltype(width)::value;
 #pragma unroll
-    for (int m = 0; m < KB; ++m) {
-        const uint64_t k = keys[m];
-        const bool lt = x < k;
-        keys[m] = lt ? x : k;
-        x = lt ? k : x;
-    }
+        for (int m = 0; m < kW; ++m) {
+            const uint64_t k = keys[m];
+            const bool lt = x < k;
+            keys[m] = lt ? x : k;
+            x = lt ? k : x;
+        }
+    };
+    if (KB > 8 && n < 8)
+        ins(std::integral_constant<int, (KB > 8 ? 8 : KB)>{});
+    else if (KB > 16 && n < 16)
+        ins(std::integral_constant<int, (KB > 16 ? 16 : KB)>{});
+    else
+        ins(std::integral_constant<int, KB>{});
+    n += n < KB ? 1 : 0;
 }
 
 }  // namespace
@@ -658,8 +672,9 @@ constexpr int kLaneWarps = 4;
 // warp-per-ray search
 constexpr uint32_t kLaneWalkMax = 384;
 
-// resident blocks per SM for each K bucket (shared memory: 48 KB per block)
-__host__ __device__ constexpr int lane_blocks_per_sm(int KB) { return KB <= 8 ? 4 : KB <= 16 ? 4 : 3; }
+// resident blocks per SM for each K bucket (shared memory: 48 KB per block;
+// K > 8: 3, for the registers of the larger neighbour arrays without spills)
+__host__ __device__ constexpr int lane_blocks_per_sm(int KB) { return KB <= 8 ? 4 : 3; }
 
 __host__ __device__ constexpr size_t lane_smem_bytes() { return (size_t)kLaneWarps * kLaneCap * 32 * 8; }
 
@@ -963,6 +978,7 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
         uint64_t keys[KB];
 #pragma unroll
         for (int m = 0; m < KB; ++m) keys[m] = ~0ull;
+        int n_keys = 0;                        // keys held (the rest are empty)
         tq = kInf;
         idq = -2;
         // kNb column entries at a time: the positions of those within lim in
@@ -1006,7 +1022,8 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
                 const float az = dfma(tj, ray.dz, -Pi.z);
                 const float d2 = dadd(dadd(dmul(ax, ax), dmul(ay, ay)), dmul(az, az));
                 if (d2 <= rad2)
-                    knn_insert<KB>(keys, ((uint64_t)__float_as_uint(d2) << 32) | (uint32_t)__float_as_int(Pi.w));
+                    knn_insert_n<KB>(keys, ((uint64_t)__float_as_uint(d2) << 32) | (uint32_t)__float_as_int(Pi.w),
+                                     n_keys);
             }
         }
         float s = 0.0f, dist[KB];
@@ -1014,7 +1031,7 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
 #pragma unroll
         for (int m = 0; m < KB; ++m) {
             dist[m] = 0.0f;
-            if (m < K && keys[m] != ~0ull) {
+            if (m < K && m < n_keys) {
                 dist[m] = dsqrt(__uint_as_float((uint32_t)(keys[m] >> 32)));
                 s = dadd(s, dist[m]);
                 ++kp;
