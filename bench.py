@@ -64,7 +64,8 @@ def config_dict(n_points, res, extra=None):
     d = {"workload": f"objects_{res}: {n_points} points on 6 closed shapes, {res}x{res} rays per frame, "
                      f"8 views on a radius-4 sphere, r=0.005, K=8, n=8, MLP 32-128-128-128-4, FP32",
          "rays_per_step": res * res, "points": n_points, "views": N_VIEWS,
-         "l2": "flushed before every step (256 MB write), flush outside the per-step event timing"}
+         "l2": "flushed before every step (256 MB write), flush outside the per-step event timing",
+         "neighbour_lists": "left in the search workspace, read there by the decode (hp_samples.nbr NULL)"}
     if extra:
         d.update(extra)
     return d
@@ -131,10 +132,12 @@ class ClockSampler:
 
 # -------------------------------------------------- algorithmic traffic/flops
 
-def algorithmic(kernel, N, Nv, P, R, S, K, F, dims, U, tensor_decode=True):
+def algorithmic(kernel, N, Nv, P, R, S, K, F, dims, U, tensor_decode=True, packed_lists=False):
     """Algorithmic bytes (or FLOPs for the decode) of one launch of each kernel.
     The search's bytes are charged to its walk (k_search_select); the pick
-    and the warp-per-ray kernel work on what the walk left."""
+    and the warp-per-ray kernel work on what the walk left.  packed_lists:
+    the pack also copies the neighbour lists (the frame leaves them in the
+    search's slots and writes each sample's slot index instead)."""
     mlp_flops = 2 * S * sum(dims[l] * dims[l + 1] for l in range(len(dims) - 1))
     table = {
         "k_project_count": ("hbm", 12 * N + 8 * N + 8 * P),
@@ -144,7 +147,8 @@ def algorithmic(kernel, N, Nv, P, R, S, K, F, dims, U, tensor_decode=True):
         "k_search_select": ("hbm", 4 * P + 16 * Nv + 12 * R + (12 + 8 * K) * S),
         "k_search_pick": ("hbm", 0),
         "k_search_select_wide": ("hbm", 0),
-        "k_pack_samples": ("hbm", 4 * R + 8 * (R + 1) + (12 + 8 * K) * S + (16 + 8 * K) * S),
+        "k_pack_samples": ("hbm", 4 * R + 8 * (R + 1) + (12 + 8 * K) * S + (16 + 8 * K) * S if packed_lists
+                           else 4 * R + 8 * (R + 1) + 16 * S + 20 * S),
         "k_aggregate_decode": ("tensor" if tensor_decode else "alu", mlp_flops),
         "k_composite": ("hbm", 28 * R + 20 * S),
         # the pass-start clears (table counts, then the search's per-pixel
@@ -476,7 +480,9 @@ def run_gpu(args):
     mlp = torch.from_numpy(mlp_np).to(dev)
     hp = H.HashPoint(params, dev)
     hp.reserve(cams[0], params.r, N, R, params.n_max)
-    smp = H.SampleBuffers.allocate(R, params.K, params.n_max, dev)
+    # the frame's samples without packed neighbour lists: the search leaves
+    # them in its workspace and the decode reads them there (hp_samples.nbr NULL)
+    smp = H.SampleBuffers.allocate(R, params.K, params.n_max, dev, lists=False)
     rgb = torch.empty(R, 3, dtype=torch.float32, device=dev)
     wsum = torch.empty(R, dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -526,7 +532,12 @@ def run_gpu(args):
     P = int(tb.n_buckets)
     nv_t = torch.empty(1, dtype=torch.int32, device=dev)
     Nv = int(hp.table()["start"][-1].item())
-    U = int(torch.unique(smp.nbr[:S][smp.nbr[:S] >= 0]).numel())
+    # distinct points gathered (U): the last view searched once more into
+    # buffers that keep the packed lists (outside the timed region)
+    smp_l = H.SampleBuffers.allocate(R, params.K, params.n_max, dev)
+    hp.search_sample(None, params.K, params.n_max, out=smp_l)
+    U = int(torch.unique(smp_l.nbr[:S][smp_l.nbr[:S] >= 0]).numel())
+    del smp_l
 
     # ---- profiled pass: per-kernel device time on the launching stream
     hp.profile_start(64 * args.steps)

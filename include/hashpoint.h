@@ -109,7 +109,12 @@ typedef struct {
     int32_t *ray;            /* [cap] ray index of the sample */
     int32_t *src;            /* [cap] id of the point whose projection is the sample */
     float *delta;            /* [cap] interval to the next sample; 2 r(t) for the last (Eq. 2) */
-    int32_t *nbr;            /* [cap*K] neighbour point ids, nearest first; -1 pads */
+    int32_t *nbr;            /* [cap*K] neighbour point ids, nearest first; -1 pads.  May be
+                                NULL together with nbr_dist: the lists then stay in the
+                                context's search workspace (not copied), where
+                                hp_aggregate_render reads them; they are valid until the
+                                next search on the context, and the backward needs them
+                                packed */
     float *nbr_dist;         /* [cap*K] distances of those neighbours to the sample */
     int64_t capacity;        /* rows available in the per-sample arrays */
 } hp_samples;
@@ -211,7 +216,10 @@ hp_status hp_search_sample(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n_r
  * d_feats (n_points x F, F in {4,8,16,32,64,128}) blended by inverse distance
  * (weights 1/max(dist, eps_d)), decoded by `mlp`, composited front to back.
  * Writes d_rgb (n_rays x 3) and d_wsum (n_rays, the sum of compositing
- * weights, <= 1).  `samples` must be the buffers given to hp_search_sample. */
+ * weights, <= 1).  `samples` must be the buffers given to hp_search_sample;
+ * when their nbr/nbr_dist are NULL the neighbour lists are read from the
+ * search's workspace (HP_ERR_INVALID_ARG if the last search on this context
+ * packed them or if only one of the two is NULL). */
 hp_status hp_aggregate_render(hp_ctx *ctx, const hp_samples *samples, int64_t n_rays, const float *d_feats,
                               int32_t F, const hp_mlp *mlp, float *d_rgb, float *d_wsum, void *stream);
 
@@ -285,7 +293,8 @@ hp_status hp_search_sample_learned(hp_ctx *ctx, const int32_t *d_ray_pixels, int
  * d_grad_rgb (R x 3) and d_grad_wsum (R, or NULL) the output gradients.
  * Gradients are ADDED (atomically, FP32) into d_grad_feats (N x F) and
  * d_grad_points (N x 3, world space); either may be NULL.  The MLP weights
- * get no gradient. */
+ * get no gradient.  The neighbour lists must be packed (samples.nbr and
+ * samples.nbr_dist non-NULL: HP_ERR_INVALID_ARG otherwise). */
 hp_status hp_aggregate_render_backward(hp_ctx *ctx, const hp_samples *samples, int64_t n_rays,
                                        const float *d_points, const float *d_feats, int32_t F, const hp_mlp *mlp,
                                        const float *d_grad_rgb, const float *d_grad_wsum, float *d_grad_feats,

@@ -44,6 +44,10 @@ struct hp_ctx {
     int64_t R = 0;
     int K = 0, n_max = 0;
     size_t search_bytes = 0;
+    // the last search left its neighbour lists in the slots (hp_samples.nbr NULL)
+    bool lists_in_slots = false;
+    const int32_t *slot_nbr = nullptr, *sample_slot = nullptr;
+    const float *slot_dist = nullptr;
     Prof prof;
 };
 
@@ -155,6 +159,7 @@ size_t search_region_bytes(int64_t R, int n_max, int K)
 {
     const size_t slots = (size_t)(R > 0 ? R : 1) * n_max;
     return al(256) + al(8 * (size_t)div_up(R > 0 ? R : 1, 256)) + al(16 * slots) + 2 * al(4 * slots * K) +
+           al(4 * slots) +                           // slot of each packed sample (lists left in the slots)
            al(4 * (size_t)(R > 0 ? R : 1)) +         // fallback list of the proposal-restricted search
            al(4 * (size_t)(R > 0 ? R : 1)) +         // rays handed to the warp-per-ray search
            al(4 * (size_t)(R > 0 ? R : 1)) +         // pixels whose point-major slots overflowed
@@ -522,10 +527,16 @@ static hp_status search_impl(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n
         return HP_ERR_INVALID_ARG;
     if (!out->sample_offset || out->capacity < 0) return HP_ERR_INVALID_ARG;
     if (n_rays > 0 && (!out->n_s || !out->primary || !out->cand_count)) return HP_ERR_INVALID_ARG;
-    if (out->capacity > 0 && (!out->t || !out->ray || !out->src || !out->delta || !out->nbr || !out->nbr_dist))
+    if (out->capacity > 0 && (!out->t || !out->ray || !out->src || !out->delta))
         return HP_ERR_INVALID_ARG;
+    // the neighbour lists: both packed, or both left in the search's slots
+    // (slot indices must then fit int32)
+    const bool lists_in_slots = !out->nbr;
+    if ((!out->nbr) != (!out->nbr_dist)) return HP_ERR_INVALID_ARG;
+    if (lists_in_slots && n_rays * (int64_t)n_samples > 0x7fffffffLL) return HP_ERR_INVALID_ARG;
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
     ctx->searched = false;
+    ctx->lists_in_slots = false;
     ctx->search_bytes = search_region_bytes(n_rays, n_samples, K);
     char *base = nullptr;
     hp_status s;
@@ -556,6 +567,7 @@ static hp_status search_impl(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n
         a.slot_rec = reinterpret_cast<float4 *>(base + o);   o += al(16 * slots);
         a.slot_nbr = reinterpret_cast<int32_t *>(base + o);  o += al(4 * slots * K);
         a.slot_dist = reinterpret_cast<float *>(base + o);   o += al(4 * slots * K);
+        a.sample_slot = reinterpret_cast<int32_t *>(base + o); o += al(4 * slots);
         a.fallback = reinterpret_cast<int32_t *>(base + o);  o += al(4 * (size_t)n_rays);
         a.fallback_count = a.ticket + 1;
         a.wide = reinterpret_cast<int32_t *>(base + o);      o += al(4 * (size_t)n_rays);
@@ -591,6 +603,12 @@ static hp_status search_impl(hp_ctx *ctx, const int32_t *d_ray_pixels, int64_t n
             return HP_ERR_CUDA;
         }
         ctx->raytab_valid = true;
+        if (lists_in_slots) {
+            ctx->lists_in_slots = true;
+            ctx->slot_nbr = a.slot_nbr;
+            ctx->slot_dist = a.slot_dist;
+            ctx->sample_slot = a.sample_slot;
+        }
         if ((d_interval || d_prop_w) && d_fallback_count &&
             cudaMemcpyAsync(d_fallback_count, a.fallback_count, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st) !=
                 cudaSuccess) {
@@ -698,6 +716,15 @@ hp_status hp_aggregate_render(hp_ctx *ctx, const hp_samples *smp, int64_t n_rays
     RenderArgs a{};
     a.n_s = smp->n_s; a.sample_offset = smp->sample_offset; a.delta = smp->delta; a.nbr = smp->nbr;
     a.nbr_dist = smp->nbr_dist; a.capacity = smp->capacity; a.R = n_rays; a.K = ctx->K;
+    if (!smp->nbr || !smp->nbr_dist) {
+        // the lists stayed in the last search's slots
+        if (smp->nbr || smp->nbr_dist || !ctx->lists_in_slots) return HP_ERR_INVALID_ARG;
+        a.nbr = nullptr;
+        a.nbr_dist = nullptr;
+        a.slot_nbr = ctx->slot_nbr;
+        a.slot_dist = ctx->slot_dist;
+        a.sample_slot = ctx->sample_slot;
+    }
     a.feats = d_feats; a.F = F; a.mlp = mlp->d_params; a.n_layers = mlp->n_layers;
     for (int l = 0; l <= mlp->n_layers; ++l) a.dims[l] = mlp->dims[l];
     a.eps_d = ctx->cfg.eps_d; a.bg_mode = ctx->cfg.bg_mode;
@@ -734,6 +761,8 @@ hp_status hp_aggregate_render_backward(hp_ctx *ctx, const hp_samples *smp, int64
         return HP_ERR_INVALID_ARG;
     for (int l = 0; l <= mlp->n_layers; ++l)
         if (mlp->dims[l] < 1 || mlp->dims[l] > HP_MLP_MAX_WIDTH) return HP_ERR_INVALID_ARG;
+    // the backward reads the packed neighbour lists
+    if (!smp->nbr || !smp->nbr_dist) return HP_ERR_INVALID_ARG;
     if (n_rays == 0) return HP_OK;
     if (!d_grad_rgb || (ctx->N > 0 && (!d_feats || !d_points))) return HP_ERR_INVALID_ARG;
     char *base = nullptr;

@@ -265,10 +265,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_decode_tc(const RenderArgs a,
                 pending = false;
             } else {
                 for (int e = tid; e < kTcTile * K; e += kTcThreads) {
-                    const int64_t g = base * K + e;
-                    const bool in = g < S * (int64_t)K;
-                    s_ids[e] = in ? __ldg(a.nbr + g) : -1;
-                    s_dst[e] = in ? __ldg(a.nbr_dist + g) : 1.0f;
+                    const int64_t g = base + e / K;
+                    const bool in = g < S;
+                    const int64_t at = in ? list_row(a, g) * K + e % K : 0;
+                    s_ids[e] = in ? __ldg(list_ids(a) + at) : -1;
+                    s_dst[e] = in ? __ldg(list_dists(a) + at) : 1.0f;
                 }
             }
             ok = __syncthreads_and(ok) != 0;
@@ -284,8 +285,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_decode_tc(const RenderArgs a,
             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
             if (sl < kTcTile && g < S) {
                 float wsum = 0.0f;
-                const int *nb = staged ? s_ids + sl * K : a.nbr + g * K;
-                const float *nd = staged ? s_dst + sl * K : a.nbr_dist + g * K;
+                const int *nb = staged ? s_ids + sl * K : list_ids(a) + list_row(a, g) * K;
+                const float *nd = staged ? s_dst + sl * K : list_dists(a) + list_row(a, g) * K;
 #pragma unroll 8
                 for (int k = 0; k < K; ++k) {
                     const int id = nb[k];
@@ -693,7 +694,10 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
     const int64_t S = S_all < a.capacity ? S_all : a.capacity;
     const int F = a.F, K = a.K;
     const uint32_t list_bytes = (uint32_t)(kTcTile * K * 4);
-    auto bulk_tile = [&](int64_t b) { return bulk_ok && b < S && b + kTcTile <= a.capacity; };
+    // a tile's neighbour lists: bulk_ok 1, two bulk copies of the packed
+    // rows; 2, copied by the producer warps from the slot rows (the search
+    // left the lists in the slots); 0, plain loads
+    auto bulk_tile = [&](int64_t b) { return bulk_ok == 1 && b < S && b + kTcTile <= a.capacity; };
 
     if (warp >= kWsConsumerWarps) {
         // =============================== producers: gather + blend
@@ -704,39 +708,106 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
         uint32_t lph = 0u, eph = 3u;   // parity bit per buffer; a fresh barrier's previous phase counts as done
         uint32_t pend = 0u;            // list copies in flight, per buffer (leader only)
         bool ok = true;
-        // Tiles come from a grid-wide counter (cleared by k_ws_image).  The
-        // leader holds the next tile so that its neighbour lists are copied
-        // while the current one is gathered; ptile[b] is the tile of A buffer
-        // b for the producers, ctile[b] the same for the consumers (-1: no
-        // more tiles; each buffer gets one such end mark).
-        int64_t t_next = 0;
+        // Tiles come from a grid-wide counter (cleared by k_ws_image); the
+        // leader warp (pw 0) fetches them two ahead.  At the top of iteration
+        // j, ptile[j & 1] holds tile j and ptile[(j + 1) & 1] tile j + 1, so
+        // the lists of tile j + 1 arrive while tile j is gathered.  ctile[b]
+        // is the tile of A buffer b for the consumers (-1: no more tiles; each
+        // buffer gets one such end mark).
+        int64_t t_next = 0;        // (leader warp) tile j + 2
+        auto fetch = [&]() -> int64_t {
+            uint32_t v = 0;
+            if (lane == 0) v = atomicAdd(a.tile_ctr, 1u);
+            return (int64_t)__shfl_sync(0xffffffffu, v, 0) * kTcTile;
+        };
+        // (leader warp, bulk_ok 1) the packed lists of tile tb into buffer buf
         auto issue_lists = [&](int buf, int64_t tb) {
             pend |= 1u << buf;
-            tc::mbar_arrive_expect_tx(&lbar[buf], 2 * list_bytes);
-            tc::bulk_g2s(smem + L.ids[buf], a.nbr + tb * K, list_bytes, &lbar[buf]);
-            tc::bulk_g2s(smem + L.dists[buf], a.nbr_dist + tb * K, list_bytes, &lbar[buf]);
+            if (lane == 0) {
+                tc::mbar_arrive_expect_tx(&lbar[buf], 2 * list_bytes);
+                tc::bulk_g2s(smem + L.ids[buf], a.nbr + tb * K, list_bytes, &lbar[buf]);
+                tc::bulk_g2s(smem + L.dists[buf], a.nbr_dist + tb * K, list_bytes, &lbar[buf]);
+            }
         };
-        if (ptid == 0) {
-            const int64_t t0 = (int64_t)atomicAdd(a.tile_ctr, 1u) * kTcTile;
-            ptile[0] = t0;
+        // bulk_ok 2 (the lists stay in the search's slots): every producer
+        // warp copies the slot rows of its kRowSamples samples of a tile, in
+        // 16-byte chunks (at most two per lane: K <= 16).  The slot indices
+        // are loaded at the top of an iteration, the rows after the producer
+        // barrier, and they are stored into the other list buffer after the
+        // warp's gather, so their latency overlaps the gather.
+        constexpr int kRowSamples = kTcTile / kWsProducerWarps;
+        static_assert(kTcTile % kWsProducerWarps == 0, "samples per producer warp");
+        const int cpr = K >> 2;                                  // 16-byte chunks per row
+        const int n_chunks = kRowSamples * 2 * cpr;              // per warp, <= 64
+        // per lane and chunk u (fixed for the whole kernel): the sample of the
+        // warp's share (-1: no chunk), the row offset (list bit 31 set for the
+        // distances) and the byte offset in a list buffer
+        int rq[2], rsrc[2], rdst[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int e = lane + 32 * u;
+            const int q = cpr > 0 ? e / (2 * cpr) : 0, rem = cpr > 0 ? e - q * 2 * cpr : 0;
+            const int list = rem >= cpr, c = rem - (list ? cpr : 0);
+            rq[u] = (bulk_ok == 2 && e < n_chunks) ? q : -1;
+            rsrc[u] = 4 * c;
+            rdst[u] = (list ? (int)list_bytes : 0) + ((pw * kRowSamples + q) * K + 4 * c) * 4;
+            if (list) rsrc[u] |= 1 << 30;
+        }
+        int32_t rslot[2] = {-1, -1};
+        float4 rval[2];
+        auto row_index = [&](int64_t tb) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int64_t g = tb + pw * kRowSamples + rq[u];
+                rslot[u] = (rq[u] >= 0 && g < S) ? __ldg(a.sample_slot + g) : -1;
+            }
+        };
+        auto row_load = [&]() {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                if (rslot[u] < 0) continue;
+                const int64_t at = (int64_t)rslot[u] * K + (rsrc[u] & 0xffff);
+                const float *src = (rsrc[u] >> 30) ? a.slot_dist : reinterpret_cast<const float *>(a.slot_nbr);
+                rval[u] = __ldg(reinterpret_cast<const float4 *>(src + at));
+            }
+        };
+        auto row_store = [&](int buf) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+                if (rslot[u] >= 0) *reinterpret_cast<float4 *>(smem + L.ids[buf] + rdst[u]) = rval[u];
+        };
+        if (pw == 0) {
+            const int64_t t0 = fetch();
+            const int64_t t1 = t0 < S ? fetch() : t0;
+            if (lane == 0) {
+                ptile[0] = t0;
+                ptile[1] = t1;
+            }
             if (bulk_tile(t0)) issue_lists(0, t0);
-            t_next = t0 < S ? (int64_t)atomicAdd(a.tile_ctr, 1u) * kTcTile : t0;
+            t_next = t1 < S ? fetch() : t1;
         }
         tc::bar_and(3, kWsProducerWarps * 32, true);
+        if (bulk_ok == 2) {
+            // the first tile's rows
+            if (ptile[0] < S) {
+                row_index(ptile[0]);
+                row_load();
+                row_store(0);
+            }
+            tc::bar_and(3, kWsProducerWarps * 32, true);
+        }
         int ends = 0;
         for (int it = 0; ends < 2; ++it) {
             const int b = it & 1;
-            const int64_t base = ptile[b];
+            const int64_t base = ptile[b], nb = ptile[b ^ 1];
             const bool valid = base < S;
             int *s_ids = reinterpret_cast<int *>(smem + L.ids[b]);
             float *s_dst = reinterpret_cast<float *>(smem + L.dists[b]);
             // the next tile's lists into the other buffer (its readers finished:
             // producer barrier at the end of the previous iteration)
-            if (ptid == 0) {
-                ptile[b ^ 1] = t_next;
-                if (valid && bulk_tile(t_next)) issue_lists(b ^ 1, t_next);
-                if (t_next < S) t_next = (int64_t)atomicAdd(a.tile_ctr, 1u) * kTcTile;
-            }
+            if (pw == 0 && valid && bulk_tile(nb)) issue_lists(b ^ 1, nb);
+            const bool rows = bulk_ok == 2 && nb < S;     // this warp's rows of the next tile
+            if (rows) row_index(nb);
             if (valid) {
                 if (bulk_tile(base)) {
                     if (!tc::mbar_wait(&lbar[b], (lph >> b) & 1u, kMbarLimit)) {
@@ -745,12 +816,15 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
                     }
                     lph ^= 1u << b;
                     pend &= ~(1u << b);
-                } else {
+                } else if (bulk_ok != 2) {
+                    // (tiles the bulk copy does not take: plain loads; with
+                    // bulk_ok 2 the producers stored the rows a step earlier)
                     for (int e = ptid; e < kTcTile * K; e += kWsProducerWarps * 32) {
-                        const int64_t g = base * K + e;
-                        const bool in = g < S * (int64_t)K;
-                        s_ids[e] = in ? __ldg(a.nbr + g) : -1;
-                        s_dst[e] = in ? __ldg(a.nbr_dist + g) : 1.0f;
+                        const int64_t g = base + e / K;
+                        const bool in = g < S;
+                        const int64_t at = in ? list_row(a, g) * K + e % K : 0;
+                        s_ids[e] = in ? __ldg(list_ids(a) + at) : -1;
+                        s_dst[e] = in ? __ldg(list_dists(a) + at) : 1.0f;
                     }
                     ok = tc::bar_and(3, kWsProducerWarps * 32, ok);
                 }
@@ -771,6 +845,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
             eph ^= 1u << b;
             ok = tc::bar_and(3, kWsProducerWarps * 32, ok);   // every producer leaves together
             if (!ok) break;
+            if (rows) row_load();
             if (valid) {
                 unsigned char *A_hi = smem + L.a0[b];
                 unsigned char *A_lo = A_hi + L.a0_lo;
@@ -780,11 +855,11 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
                     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
                     if (g < S) {
                         float wsum = 0.0f;
-                        const int *nb = s_ids + sl * K;
+                        const int *nl = s_ids + sl * K;
                         const float *nw = s_dst + sl * K;
 #pragma unroll 8
                         for (int k = 0; k < K; ++k) {
-                            const int id = nb[k];
+                            const int id = nl[k];
                             if (id >= 0) {
                                 // inverse-distance weight (approximate reciprocal:
                                 // ~2 ulp, far inside the colour tolerance)
@@ -805,6 +880,13 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
                 tc::fence_async_smem();                  // generic stores -> tensor-core reads
             } else {
                 ++ends;
+            }
+            if (rows) row_store(b ^ 1);
+            // (leader) tile j + 2 into the slot of tile j, which every producer
+            // read at the top of this iteration (before the barrier above)
+            if (pw == 0) {
+                if (lane == 0) ptile[b] = t_next;
+                if (t_next < S) t_next = fetch();
             }
             if (ptid == 0) ctile[b] = valid ? base : -1;
             __syncwarp();
@@ -1020,7 +1102,9 @@ cudaError_t launch_decode_tc(const RenderArgs &a, bool bf16, cudaStream_t st, in
 {
     *n_kernels = 1;
     cudaError_t e;
-    const int bulk_ok_ws = ((uintptr_t)a.nbr % 16 == 0) && ((uintptr_t)a.nbr_dist % 16 == 0);
+    const int bulk_ok_ws = a.nbr ? (((uintptr_t)a.nbr % 16 == 0) && ((uintptr_t)a.nbr_dist % 16 == 0) ? 1 : 0)
+                                 : ((a.K % 4 == 0) && a.K <= 16 && ((uintptr_t)a.slot_nbr % 16 == 0) &&
+                                    ((uintptr_t)a.slot_dist % 16 == 0) ? 2 : 0);
     const WsLayout W = ws_layout(a, bf16);
     if (W.ok) {
         auto kern = bf16 ? k_decode_ws<true> : k_decode_ws<false>;
@@ -1042,7 +1126,7 @@ cudaError_t launch_decode_tc(const RenderArgs &a, bool bf16, cudaStream_t st, in
     int64_t grid = a.num_sms;
     const int64_t tiles = div_up(a.capacity > 0 ? a.capacity : 1, kTcTile);
     if (grid > tiles) grid = tiles;
-    const int bulk_ok = ((uintptr_t)a.nbr % 16 == 0) && ((uintptr_t)a.nbr_dist % 16 == 0);
+    const int bulk_ok = a.nbr && ((uintptr_t)a.nbr % 16 == 0) && ((uintptr_t)a.nbr_dist % 16 == 0);
     launch_chained(kern, (unsigned)grid, kTcThreads, L.total, st, a, L, bulk_ok);
     return cudaGetLastError();
 }

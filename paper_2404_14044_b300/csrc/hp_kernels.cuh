@@ -142,9 +142,10 @@ struct SearchArgs {
     int32_t *ray;
     int32_t *src;
     float *delta;
-    int32_t *nbr;
+    int32_t *nbr;            // packed lists; NULL: left in the slots, sample_slot written instead
     float *nbr_dist;
     int64_t capacity;
+    int32_t *sample_slot;    // [n_max x R] slot (m R + i) of each packed sample
     float4 *slot_rec;        // [n_max x R] sample slots (scratch), slot m of ray i at m R + i: t, source id bits, delta
     int32_t *slot_nbr;       // [n_max x R x K]
     float *slot_dist;        // [n_max x R x K]
@@ -178,7 +179,22 @@ struct RenderArgs {
     int num_sms;
     unsigned char *wimg;     // [kWsImageMax] the tensor-core decode's weight image (16-byte aligned)
     uint32_t *tile_ctr;      // the tensor-core decode's tile counter
+    // nbr == NULL: the lists stay in the search's slot rows (slot_nbr,
+    // slot_dist: row m R + i holds the K entries of ray i's m-th sample), and
+    // sample_slot[g] is the row of packed sample g
+    const int32_t *slot_nbr;
+    const float *slot_dist;
+    const int32_t *sample_slot;
 };
+
+// Neighbour list of packed sample g: its row in the packed arrays, or its slot
+// row when the search left the lists in the slots.
+__device__ __forceinline__ int64_t list_row(const RenderArgs &a, int64_t g)
+{
+    return a.nbr ? g : (int64_t)__ldg(a.sample_slot + g);
+}
+__device__ __forceinline__ const int32_t *list_ids(const RenderArgs &a) { return a.nbr ? a.nbr : a.slot_nbr; }
+__device__ __forceinline__ const float *list_dists(const RenderArgs &a) { return a.nbr ? a.nbr_dist : a.slot_dist; }
 
 // Largest weight image of the tensor-core decode (its shared-memory limit).
 constexpr int kWsImageMax = 227 * 1024;

@@ -166,12 +166,15 @@ __global__ void __launch_bounds__(kRenderThreads) k_aggregate_decode(const Rende
             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
             float wsum = 0.0f;
             if (g < S) {
+                const int64_t row = list_row(a, g) * K;
+                const int32_t *ids = list_ids(a) + row;
+                const float *dists = list_dists(a) + row;
                 for (int k0 = 0; k0 < K; k0 += rpp) {
                     const int k = k0 + sub;
                     if (k < K) {
-                        const int id = __ldg(a.nbr + g * K + k);
+                        const int id = __ldg(ids + k);
                         if (id >= 0) {
-                            const float w = 1.0f / fmaxf(__ldg(a.nbr_dist + g * K + k), a.eps_d);
+                            const float w = 1.0f / fmaxf(__ldg(dists + k), a.eps_d);
                             const float4 f = __ldg(feats4 + (int64_t)id * lpr + chunk);
                             acc.x = fmaf(w, f.x, acc.x);
                             acc.y = fmaf(w, f.y, acc.y);

@@ -1192,7 +1192,9 @@ __global__ void __launch_bounds__(kLaneWarps * 32, lane_blocks_per_sm(KB)) k_sea
 // Packing (K6): exclusive scan of n_s with a decoupled look-back over
 // uniform tiles of kPackRays rays; the tile's samples form one contiguous packed
 // range, which the whole block copies with coalesced stores (each packed
-// sample's slot is looked up in a shared-memory map).
+// sample's slot is looked up in a shared-memory map).  When the caller leaves
+// the neighbour lists in the slots (hp_samples.nbr NULL), only the per-sample
+// records are copied and each sample's slot index is written instead.
 constexpr int kPackRays = 1024;
 constexpr int kPackWarps = kPackRays / 32;
 
@@ -1248,7 +1250,9 @@ __global__ void __launch_bounds__(kPackRays) k_pack_samples(const SearchArgs a)
         a.src[base + p] = __float_as_int(rec.y);
         a.delta[base + p] = rec.z;
         a.ray[base + p] = (int)r;
+        if (!a.nbr) a.sample_slot[base + p] = (int32_t)sl;   // the lists stay in the slots
     }
+    if (!a.nbr) return;
     // neighbour ids and distances
     const int K = a.K;
     auto slot_of = [&](int64_t p) {

@@ -197,8 +197,8 @@ class SampleBuffers:
     ray: torch.Tensor
     src: torch.Tensor
     delta: torch.Tensor
-    nbr: torch.Tensor
-    nbr_dist: torch.Tensor
+    nbr: Optional[torch.Tensor]          # None: the lists stay in the search's workspace
+    nbr_dist: Optional[torch.Tensor]
     K: int
 
     @property
@@ -208,12 +208,16 @@ class SampleBuffers:
     def struct(self) -> Samples:
         s = Samples()
         for f in ("n_s", "primary", "cand_count", "sample_offset", "t", "ray", "src", "delta", "nbr", "nbr_dist"):
-            setattr(s, f, getattr(self, f).data_ptr())
+            v = getattr(self, f)
+            setattr(s, f, 0 if v is None else v.data_ptr())
         s.capacity = self.capacity
         return s
 
     @staticmethod
-    def allocate(R: int, K: int, n_samples: int, device, capacity: Optional[int] = None) -> "SampleBuffers":
+    def allocate(R: int, K: int, n_samples: int, device, capacity: Optional[int] = None,
+                 lists: bool = True) -> "SampleBuffers":
+        """lists=False: no packed neighbour lists (nbr, nbr_dist None); the
+        search leaves them in its workspace for aggregate_render."""
         cap = R * n_samples if capacity is None else capacity
         cap1 = max(cap, 1)
         i32 = dict(dtype=torch.int32, device=device)
@@ -223,8 +227,9 @@ class SampleBuffers:
             cand_count=torch.empty(max(R, 1), **i32),
             sample_offset=torch.empty(R + 1, dtype=torch.int64, device=device),
             t=torch.empty(cap1, **f32)[:cap], ray=torch.empty(cap1, **i32)[:cap], src=torch.empty(cap1, **i32)[:cap],
-            delta=torch.empty(cap1, **f32)[:cap], nbr=torch.empty(cap1 * K, **i32)[: cap * K].view(cap, K),
-            nbr_dist=torch.empty(cap1 * K, **f32)[: cap * K].view(cap, K), K=K)
+            delta=torch.empty(cap1, **f32)[:cap],
+            nbr=torch.empty(cap1 * K, **i32)[: cap * K].view(cap, K) if lists else None,
+            nbr_dist=torch.empty(cap1 * K, **f32)[: cap * K].view(cap, K) if lists else None, K=K)
 
     def packed(self, R: int) -> Dict[str, torch.Tensor]:
         """Host copies trimmed to the S samples written (syncs)."""
@@ -232,8 +237,9 @@ class SampleBuffers:
         S = min(S, self.capacity)
         return dict(S=S, n_s=self.n_s[:R].cpu(), primary=self.primary[:R].cpu(), cand_count=self.cand_count[:R].cpu(),
                     sample_offset=self.sample_offset.cpu(), t=self.t[:S].cpu(), ray=self.ray[:S].cpu(),
-                    src=self.src[:S].cpu(), delta=self.delta[:S].cpu(), nbr=self.nbr[:S].cpu(),
-                    nbr_dist=self.nbr_dist[:S].cpu())
+                    src=self.src[:S].cpu(), delta=self.delta[:S].cpu(),
+                    nbr=None if self.nbr is None else self.nbr[:S].cpu(),
+                    nbr_dist=None if self.nbr_dist is None else self.nbr_dist[:S].cpu())
 
 
 class HashPoint:
