@@ -167,12 +167,15 @@ def algorithmic(kernel, N, Nv, P, R, S, K, F, dims, U, tensor_decode=True, packe
 NCU_TRAFFIC = {
     # the search stage's time (k_search_select) covers the point-major pass
     # (k_search_splat) and the selection launch: their bytes are summed
-    "k_search_select": {"bytes": 52885760 + 38419968 + 116636928 + 36334336,
-                        "sources": ("hp_search.cu", "hp_common.cuh", "hp_kernels.cuh"),
-                        "sha256": "148e0ba04eb8d86c4fc8614de941f918056787686157b59c573993ff777dec91"},
-    "k_aggregate_decode": {"bytes": 78085888 + 3516672,
-                           "sources": ("hp_decode_tc.cu", "hp_tc.cuh", "hp_common.cuh", "hp_kernels.cuh"),
-                           "sha256": "7dc46d1a8824fa748f0c5c529e5c0aa541b916313c303554ab1da70b128e97b3"},
+    "k_search_select": {"bytes": 52966656 + 38180096 + 116630784 + 36503296,
+                        "sources": ('hp_search.cu', 'hp_common.cuh', 'hp_kernels.cuh'),
+                        "sha256": "193d5704e03de71e2a405ffa6938c7793a80b2a954ed9f1ac1eb0855dc0606ee"},
+    "k_pack_samples": {"bytes": 17948928 + 3584,
+                       "sources": ('hp_search.cu', 'hp_common.cuh', 'hp_kernels.cuh'),
+                       "sha256": "193d5704e03de71e2a405ffa6938c7793a80b2a954ed9f1ac1eb0855dc0606ee"},
+    "k_aggregate_decode": {"bytes": 88079104 + 4423168,
+                           "sources": ('hp_decode_tc.cu', 'hp_tc.cuh', 'hp_common.cuh', 'hp_kernels.cuh'),
+                           "sha256": "9ef8c11eb4141ce67d83f9dd2bd9da77bfeaee62d13d1f61e695d56020d59910"},
 }
 
 
@@ -583,7 +586,7 @@ def run_gpu(args):
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in pk else "fallback 6400 GB/s"}
 
     roof = roofline_of(dom)
-    roof["others"] = {k: {x: roofline_of(k)[x] for x in ("bound", "achieved", "unit", "frac")}
+    roof["others"] = {k: {x: roofline_of(k)[x] for x in ("bound", "achieved", "unit", "frac", "traffic")}
                       for k in ("k_search_select", "k_aggregate_decode", "k_pack_samples", "k_bucket_sort")
                       if k != dom and per_kernel.get(k, {}).get("launches")}
 
