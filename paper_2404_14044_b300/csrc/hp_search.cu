@@ -3,8 +3,9 @@
 //
 // k_search_splat (whole frames, plain search): one thread per tabled point
 // tests it against the ray of every pixel whose window holds its bucket and
-// appends the accepted (t, table index) pairs to that pixel's slots (an
-// atomic count per pixel; kPmCap slots).  Rays then only select.
+// appends the accepted depth and table index to that pixel's slots (two
+// arrays; an atomic count per pixel; kPmCap slots), listing the pixels whose
+// count passes the slots.  Rays then only select.
 //
 // k_search_select: one thread per ray.  A warp owns an 8 x 4 tile of pixels
 // (whole frames) or 32 consecutive listed rays.  The lane gathers its ray's
@@ -18,8 +19,11 @@
 // candidates within r(t_j) of the sample (only those within that distance in
 // t can qualify), forms d_j and alpha_j, applies the weight and the primary-
 // cluster rule, and stops when the cluster ends, when n samples are kept or
-// when gamma * T_j <= eps_w (no later weight can pass).  Rays with more
-// candidates than a column holds are listed for k_search_select_wide.
+// when gamma * T_j <= eps_w (no later weight can pass).  Whole frames: the
+// column keeps only the prefix of the (t, id) order the selection can reach
+// (prune_m), and the warps first search the overflowed pixels with the
+// warp-per-ray code.  Rays with more candidates than a column holds are
+// listed for k_search_select_wide.
 //
 // k_search_select_wide: one warp per listed ray.  The candidates come from
 // the point-major slots, or from a walk that reads the concatenated runs 32
@@ -29,9 +33,10 @@
 // one's K nearest are ranked in shared memory.
 //
 // Each ray writes its samples into n_samples slots of a scratch area (slot m
-// of ray i at m R + i); K6 packs them ray by ray (scan + copy), so the output
-// order is independent of scheduling and blocks never wait on one another
-// while they search.
+// of ray i at m R + i); K6 packs them ray by ray (scan + copy; the neighbour
+// lists may stay in the slots, K6 then writing each sample's slot index), so
+// the output order is independent of scheduling and blocks never wait on one
+// another while they search.
 #include <algorithm>
 #include <type_traits>
 
