@@ -169,13 +169,13 @@ NCU_TRAFFIC = {
     # (k_search_splat) and the selection launch: their bytes are summed
     "k_search_select": {"bytes": 52966656 + 38180096 + 116630784 + 36503296,
                         "sources": ('hp_search.cu', 'hp_common.cuh', 'hp_kernels.cuh'),
-                        "sha256": "5075a4d4388f96f5540e3af61f9aa17ea53213926a2f19f79767c00fb1488754"},
+                        "sha256": "0fad5facf9b0ca4c4129bd8c921bdd86e5e5676529aa4fa75d0bf9773cae0845"},
     "k_pack_samples": {"bytes": 17948928 + 3584,
                        "sources": ('hp_search.cu', 'hp_common.cuh', 'hp_kernels.cuh'),
-                       "sha256": "5075a4d4388f96f5540e3af61f9aa17ea53213926a2f19f79767c00fb1488754"},
+                       "sha256": "0fad5facf9b0ca4c4129bd8c921bdd86e5e5676529aa4fa75d0bf9773cae0845"},
     "k_aggregate_decode": {"bytes": 88079104 + 4423168,
                            "sources": ('hp_decode_tc.cu', 'hp_tc.cuh', 'hp_common.cuh', 'hp_kernels.cuh'),
-                           "sha256": "9ef8c11eb4141ce67d83f9dd2bd9da77bfeaee62d13d1f61e695d56020d59910"},
+                           "sha256": "8adfe88165301d8574d7024a9940c0958d0664862adfd3965fb851b9e156bf47"},
 }
 
 

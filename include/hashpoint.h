@@ -53,7 +53,9 @@ typedef enum {
     HP_ERR_NOT_BUILT = 5,     /* search before build, or build parameters changed */
     HP_ERR_NO_MEMORY = 6,     /* workspace too small / allocation failed */
     HP_ERR_BAD_RAY = 7,       /* device: a ray pixel id outside [0, W*H) */
-    HP_ERR_TOO_LARGE = 8      /* a size above the fixed limit of an allocation-free entry point */
+    HP_ERR_TOO_LARGE = 8,     /* a size above the fixed limit of an allocation-free entry point */
+    HP_ERR_BOUNDS = 9         /* device, bounds-check build (libhashpoint_checks.so) only: an index
+                                 outside its array (detail: the index); the access was skipped */
 } hp_status;
 
 typedef struct hp_ctx hp_ctx;

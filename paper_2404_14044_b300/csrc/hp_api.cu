@@ -222,6 +222,7 @@ const char *hp_status_string(hp_status s)
     case HP_ERR_NO_MEMORY: return "workspace too small or allocation failed";
     case HP_ERR_BAD_RAY: return "ray pixel out of range";
     case HP_ERR_TOO_LARGE: return "size exceeds the allocation-free limit";
+    case HP_ERR_BOUNDS: return "index outside its array (bounds-check build)";
     }
     return "unknown status";
 }
@@ -739,6 +740,8 @@ hp_status hp_aggregate_render(hp_ctx *ctx, const hp_samples *smp, int64_t n_rays
         a.tile_ctr = reinterpret_cast<uint32_t *>(base + o + al(kWsImageMax));
     }
     a.rgb = d_rgb; a.wsum = d_wsum; a.num_sms = ctx->num_sms;
+    a.n_feats = ctx->N;
+    a.n_slots = ctx->R * (int64_t)ctx->n_max;
     const bool tc_ok = a.decode != HP_DECODE_FP32_SIMT && decode_tc_supported(a, a.decode == HP_DECODE_BF16, nullptr);
     if (!tc_ok && render_smem_bytes(a) > 227 * 1024) return HP_ERR_INVALID_ARG;
     if (launch_render(a, st, &ctx->prof) != cudaSuccess) {
@@ -781,6 +784,8 @@ hp_status hp_aggregate_render_backward(hp_ctx *ctx, const hp_samples *smp, int64
     a.go = reinterpret_cast<float4 *>(base + al(16 * c));
     a.gt = reinterpret_cast<float *>(base + 2 * al(16 * c));
     a.grad_rgb = d_grad_rgb; a.grad_wsum = d_grad_wsum; a.grad_feats = d_grad_feats; a.grad_points = d_grad_points;
+    a.n_points = ctx->N;
+    a.err = ctx->d_err;
     a.num_sms = ctx->num_sms;
     if (backward_smem_bytes(a) > 227 * 1024) return HP_ERR_INVALID_ARG;
     if (launch_backward(a, static_cast<cudaStream_t>(stream), &ctx->prof) != cudaSuccess) {

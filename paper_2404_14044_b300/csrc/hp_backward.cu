@@ -222,7 +222,8 @@ __global__ void __launch_bounds__(kBwdThreads, 2) k_decode_bwd(const BwdArgs a, 
             if (g < S) {
                 for (int m0 = 0; m0 < K; m0 += 32) {
                     const int m = m0 + lane;
-                    const int id_l = m < K ? __ldg(a.nbr + g * K + m) : -1;
+                    int id_l = m < K ? __ldg(a.nbr + g * K + m) : -1;
+                    if (id_l >= 0 && !hp_check(id_l < a.n_points, a.err, id_l)) id_l = -1;
                     const float w_l = id_l >= 0 ? 1.0f / fmaxf(__ldg(a.nbr_dist + g * K + m), a.eps_d) : 0.0f;
                     const int mn = min(32, K - m0);
                     for (int c0 = 0; c0 < mn; c0 += kNb) {
@@ -336,7 +337,8 @@ __global__ void __launch_bounds__(kBwdThreads, 2) k_decode_bwd(const BwdArgs a, 
             float gx0 = 0.0f, gx1 = 0.0f, gx2 = 0.0f;
             for (int m0 = 0; m0 < K; m0 += 32) {
                 const int m = m0 + lane;
-                const int id_l = m < K ? __ldg(a.nbr + g * K + m) : -1;
+                int id_l = m < K ? __ldg(a.nbr + g * K + m) : -1;
+                if (id_l >= 0 && !hp_check(id_l < a.n_points, a.err, id_l)) id_l = -1;
                 const float d_l = id_l >= 0 ? __ldg(a.nbr_dist + g * K + m) : 1.0f;
                 const int mn = min(32, K - m0);
                 float sc_l = 0.0f;                   // lane m: dL/d|x_j - P_m| / |x_j - P_m|
@@ -397,7 +399,9 @@ __global__ void __launch_bounds__(kBwdThreads, 2) k_decode_bwd(const BwdArgs a, 
                 }
                 if (lane == 0) {
                     const float gt = a.gt[g] + (gx0 * dd.x + gx1 * dd.y + gx2 * dd.z);
-                    add_world(a.grad_points, __ldg(a.src + g), a.cam, gt * dd.x, gt * dd.y, gt * dd.z);
+                    const int src = __ldg(a.src + g);
+                    if (hp_check(src >= 0 && src < a.n_points, a.err, src))
+                        add_world(a.grad_points, src, a.cam, gt * dd.x, gt * dd.y, gt * dd.z);
                 }
             }
         }

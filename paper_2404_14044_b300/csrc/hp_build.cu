@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t *__restric
 __global__ void __launch_bounds__(256) k_scatter(const float *__restrict__ pts, int64_t N, Cam cam,
                                                  const uint2 *__restrict__ keyrank,
                                                  const uint32_t *__restrict__ start, float4 *__restrict__ spts,
-                                                 uint32_t *__restrict__ pcell)
+                                                 uint32_t *__restrict__ pcell, ErrWord *err)
 {
     grid_dep_wait();
     grid_dep_trigger();
@@ -130,6 +130,7 @@ __global__ void __launch_bounds__(256) k_scatter(const float *__restrict__ pts, 
     // the same float32 sequence as K1, so the stored position is the one keyed
     float3 X = cam_point(cam, __ldg(pts + 3 * i), __ldg(pts + 3 * i + 1), __ldg(pts + 3 * i + 2));
     const uint32_t slot = start[kr.x] + kr.y;
+    if (!hp_check(slot < N, err, slot)) return;
     spts[slot] = make_float4(X.x, X.y, X.z, __int_as_float((int)i));
     pcell[slot] = kr.x;
 }
@@ -276,7 +277,8 @@ cudaError_t launch_build(const BuildArgs &a, cudaStream_t st, Prof *prof)
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (a.N > 0) {
         prof_begin(prof, st, KID_SCATTER);
-        launch_chained(k_scatter, (unsigned)div_up(a.N, 256), 256, 0, st, a.pts, a.N, a.cam, a.keyrank, a.start, a.spts, a.pcell);
+        launch_chained(k_scatter, (unsigned)div_up(a.N, 256), 256, 0, st, a.pts, a.N, a.cam, a.keyrank, a.start, a.spts, a.pcell,
+                       a.err);
         prof_end(prof, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

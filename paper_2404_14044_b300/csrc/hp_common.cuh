@@ -43,6 +43,20 @@ __device__ __forceinline__ void set_error(ErrWord *e, int32_t code, int64_t deta
     if (atomicCAS(&e->status, 0, code) == 0) e->detail = detail;
 }
 
+// Bounds-check build (compiled with -DHP_CHECKS=1, libhashpoint_checks.so):
+// hp_check(ok, err, index) records HP_ERR_BOUNDS with the index when an index
+// check fails and returns false, so that the caller skips the access.  In the
+// normal build it is the constant true and costs nothing.
+#ifdef HP_CHECKS
+__device__ __forceinline__ bool hp_check(bool ok, ErrWord *e, int64_t index)
+{
+    if (!ok) set_error(e, HP_ERR_BOUNDS, index);
+    return ok;
+}
+#else
+__device__ __forceinline__ bool hp_check(bool, ErrWord *, int64_t) { return true; }
+#endif
+
 // --------------------------------------------- decision arithmetic contract
 // Every discrete decision is computed with single IEEE binary32 operations in
 // a written order (no contraction), so that an independent CPU program that

@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_decode_tc(const RenderArgs a,
 #pragma unroll 8
                 for (int k = 0; k < K; ++k) {
                     const int id = nb[k];
-                    if (id >= 0) {
+                    if (id >= 0 && hp_check(id < a.n_feats, a.err, id)) {
                         const float w = 1.0f / fmaxf(nd[k], a.eps_d);
                         const float4 f = __ldg(feats4 + (int64_t)id * lpr + chunk);
                         acc.x = fmaf(w, f.x, acc.x);
@@ -760,6 +760,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
             for (int u = 0; u < 2; ++u) {
                 const int64_t g = tb + pw * kRowSamples + rq[u];
                 rslot[u] = (rq[u] >= 0 && g < S) ? __ldg(a.sample_slot + g) : -1;
+                if (rslot[u] >= 0 && !hp_check(rslot[u] < a.n_slots, a.err, rslot[u])) rslot[u] = -1;
             }
         };
         auto row_load = [&]() {
@@ -860,7 +861,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a,
 #pragma unroll 8
                         for (int k = 0; k < K; ++k) {
                             const int id = nl[k];
-                            if (id >= 0) {
+                            if (id >= 0 && hp_check(id < a.n_feats, a.err, id)) {
                                 // inverse-distance weight (approximate reciprocal:
                                 // ~2 ulp, far inside the colour tolerance)
                                 const float w = kBF16 ? nw[k] : __fdividef(1.0f, fmaxf(nw[k], a.eps_d));

@@ -185,13 +185,17 @@ struct RenderArgs {
     const int32_t *slot_nbr;
     const float *slot_dist;
     const int32_t *sample_slot;
+    int64_t n_feats;         // feature rows (the bounds-check build tests neighbour ids against it)
+    int64_t n_slots;         // slot rows of the last search (the same, for sample_slot)
 };
 
 // Neighbour list of packed sample g: its row in the packed arrays, or its slot
 // row when the search left the lists in the slots.
 __device__ __forceinline__ int64_t list_row(const RenderArgs &a, int64_t g)
 {
-    return a.nbr ? g : (int64_t)__ldg(a.sample_slot + g);
+    if (a.nbr) return g;
+    const int64_t r = __ldg(a.sample_slot + g);
+    return hp_check(r >= 0 && r < a.n_slots, a.err, r) ? r : 0;   // (bounds-check build: row 0 instead)
 }
 __device__ __forceinline__ const int32_t *list_ids(const RenderArgs &a) { return a.nbr ? a.nbr : a.slot_nbr; }
 __device__ __forceinline__ const float *list_dists(const RenderArgs &a) { return a.nbr ? a.nbr_dist : a.slot_dist; }
@@ -249,6 +253,8 @@ struct BwdArgs {
     const float *grad_wsum;     // R or NULL
     float4 *go;                 // scratch: dL/d(MLP output) per sample
     float *gt;                  // scratch: dL/dt_j through the Delta's
+    int64_t n_points;           // N (the bounds-check build tests neighbour ids against it)
+    ErrWord *err;
     float *grad_feats;          // N x F, accumulated (NULL: skip)
     float *grad_points;         // N x 3 world, accumulated (NULL: skip)
     int num_sms;

@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_aggregate_decode(const Rende
                     const int k = k0 + sub;
                     if (k < K) {
                         const int id = __ldg(ids + k);
-                        if (id >= 0) {
+                        if (id >= 0 && hp_check(id < a.n_feats, a.err, id)) {
                             const float w = 1.0f / fmaxf(__ldg(dists + k), a.eps_d);
                             const float4 f = __ldg(feats4 + (int64_t)id * lpr + chunk);
                             acc.x = fmaf(w, f.x, acc.x);

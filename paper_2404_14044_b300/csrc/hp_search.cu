@@ -473,7 +473,8 @@ __device__ __forceinline__ void wide_ray(const SearchArgs &a, const float2 *inte
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const int e = lane + 32 * m;
-            cpos[m] = e < C ? __ldg(a.spts + ei[m]) : make_float4(0.f, 0.f, 0.f, 0.f);
+            cpos[m] = e < C && hp_check(ei[m] < (uint64_t)a.n_points, a.err, ei[m]) ? __ldg(a.spts + ei[m])
+                                                                                     : make_float4(0.f, 0.f, 0.f, 0.f);
             ckey[m] = e < C ? ((uint64_t)__float_as_uint(et[m]) << 32) | (uint32_t)__float_as_int(cpos[m].w) : ~0ull;
         }
         total = C;
@@ -930,7 +931,10 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
     }
     const int C = n_col;
     // the position (and id) of column entry c
-    auto pos_of = [&](int c) -> float4 { return __ldg(a.spts + li[c * 32]); };
+    auto pos_of = [&](int c) -> float4 {
+        const uint32_t ix = li[c * 32];
+        return hp_check(ix < (uint64_t)a.n_points, a.err, ix) ? __ldg(a.spts + ix) : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
 
     // ---- adaptive primary surface sampling, candidates in (t, id) order.
     // Each pass over the column forms candidate j's neighbourhood and, in the

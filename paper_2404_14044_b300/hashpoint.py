@@ -21,7 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhashpoint.so")
 
 HP_OK, HP_ERR_INVALID_ARG, HP_ERR_CUDA, HP_ERR_OVERFLOW, HP_ERR_TIMEOUT = 0, 1, 2, 3, 4
-HP_ERR_NOT_BUILT, HP_ERR_NO_MEMORY, HP_ERR_BAD_RAY, HP_ERR_TOO_LARGE = 5, 6, 7, 8
+HP_ERR_NOT_BUILT, HP_ERR_NO_MEMORY, HP_ERR_BAD_RAY, HP_ERR_TOO_LARGE, HP_ERR_BOUNDS = 5, 6, 7, 8, 9
 SCAN_NOALLOC_MAX_N = 67108864
 MLP_MAX_LAYERS = 8
 
