@@ -662,7 +662,7 @@ def run_gpu(args):
     cc_last = smp.cand_count[:R]
     stats = {"n_s_histogram": [int(x) for x in torch.bincount(ns_last.long(), minlength=params.n_max + 1).tolist()],
              "rays_over_candidate_cap": int((cc_last > params.cand_cap).sum().item()),
-             "rays_over_lane_column_48": int((cc_last > 48).sum().item()),
+             "rays_over_lane_column_40": int((cc_last > 40).sum().item()),
              "sample_capacity_overflow": bool(S > smp.capacity),
              "candidates_per_ray_mean": float(cc_last.float().mean().item())}
 

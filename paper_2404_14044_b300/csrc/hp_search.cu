@@ -9,8 +9,9 @@
 //
 // k_search_select: one thread per ray.  A warp owns an 8 x 4 tile of pixels
 // (whole frames) or 32 consecutive listed rays.  The lane gathers its ray's
-// accepted points into its own column of a [kLaneCap][32] shared-memory
-// array (conflict-free whatever the counts): from the point-major slots, or
+// accepted points into its own column of a [cap][32] shared-memory array
+// (conflict-free whatever the counts; cap kLaneCapPM for the point-major
+// selection, kLaneCap for the walks): from the point-major slots, or
 // by walking the s x s window itself (listed rays, restricted searches; a
 // window row of s buckets is s adjacent keys, so one contiguous run of the
 // reordered list).  The column stays unsorted: candidate j+1 is the smallest
@@ -666,7 +667,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select_wide(const 
 }
 
 // Lane-per-ray search.  A lane appends its accepted points, unsorted, to
-// its own column of a [kLaneCap][32] shared-memory array (a few instructions
+// its own column of a [cap][32] shared-memory array (a few instructions
 // per point, so lanes that accept at different times cost the warp little),
 // then takes its candidates in (t, id) order, finding each next one with a
 // scan of the column -- the selection usually stops after a few.  A ray whose
@@ -678,11 +679,23 @@ constexpr int kLaneWarps = 4;
 // warp-per-ray search
 constexpr uint32_t kLaneWalkMax = 384;
 
-// resident blocks per SM for each K bucket (shared memory: 48 KB per block;
-// K > 8: 3, for the registers of the larger neighbour arrays without spills)
-__host__ __device__ constexpr int lane_blocks_per_sm(int KB) { return KB <= 8 ? 4 : 3; }
+// column entries per lane: the point-major selection (kMode 3) keeps a
+// shorter column than the window walks
+__host__ __device__ constexpr int lane_cap(int kMode) { return kMode == 3 ? kLaneCapPM : kLaneCap; }
 
-__host__ __device__ constexpr size_t lane_smem_bytes() { return (size_t)kLaneWarps * kLaneCap * 32 * 8; }
+// resident blocks per SM for each K bucket and mode (K <= 8: the window walks
+// 4 -- shared memory, 48 KB per block, and registers -- the point-major
+// selection 5, its 40 KB columns and at most 102 registers without spills;
+// K > 8: 3, for the registers of the larger neighbour arrays without spills)
+__host__ __device__ constexpr int lane_blocks_per_sm(int KB, int kMode)
+{
+    return KB <= 8 ? (kMode == 3 ? 5 : 4) : 3;
+}
+
+__host__ __device__ constexpr size_t lane_smem_bytes(int kMode)
+{
+    return (size_t)kLaneWarps * lane_cap(kMode) * 32 * 8;
+}
 
 // One ray on one lane; lt / li point at this lane's column (depth lt[c * 32],
 // table index li[c * 32]).  Returns false when the ray must go to the
@@ -708,6 +721,7 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
     constexpr bool kLearned = kMode == 2;
     constexpr bool restricted = kMode == 1 || kMode == 2;
     constexpr bool kPointMajor = kMode == 3;   // candidates from the point-major pass
+    constexpr int kCap = lane_cap(kMode);      // column entries
     float tn = a.cam.t_near, tf = a.cam.t_far;
     float2 iv = make_float2(tn, tf);
     const int hw = plain_window(a);           // the plain search's window
@@ -799,8 +813,8 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
         // candidates after: most candidates lie beyond the reachable prefix
         const float4 *st = reinterpret_cast<const float4 *>(a.pm_t + (int64_t)pix * kPmCap);
         const uint32_t *si = a.pm_i + (int64_t)pix * kPmCap;
-        constexpr int kSlotBatch = 4;
-        const bool in_col = cnt <= (uint32_t)kLaneCap;   // the depths fit the column
+        constexpr int kSlotBatch = 3;
+        const bool in_col = cnt <= (uint32_t)kCap;   // the depths fit the column
         {
             float tm[kPruneMax];
 #pragma unroll
@@ -844,7 +858,7 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
                     const float4 q4 = e[k >> 2];
                     const float t = (k & 3) == 0 ? q4.x : (k & 3) == 1 ? q4.y : (k & 3) == 2 ? q4.z : q4.w;
                     if (!(t <= thr)) continue;
-                    if (n_col == kLaneCap) return false;   // more than the column holds
+                    if (n_col == kCap) return false;   // more than the column holds
                     keep(t, c);
                 }
             }
@@ -905,7 +919,7 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
                     if (!acc) continue;
                     // more accepted points than the column holds: the warp-per-ray
                     // search takes the ray, so stop walking
-                    if (total == kLaneCap) {
+                    if (total == kCap) {
                         if (kLearned) a.interval_buf[ri] = iv;
                         return false;
                     }
@@ -992,7 +1006,7 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
         idq = -2;
         // kNb column entries at a time: the positions of those within lim in
         // depth are loaded together before any is used (their latencies overlap)
-        constexpr int kNb = 4;
+        constexpr int kNb = kPointMajor ? 2 : 4;
         for (int c0 = 0; c0 < C; c0 += kNb) {
             float tcs[kNb];
             float4 P[kNb];
@@ -1120,7 +1134,7 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
 // Warps pull work units from a grid-wide counter: an 8 x 4 pixel tile (whole
 // frames; ray i is pixel i) or 32 consecutive listed rays.
 template <int KB, int kMode>
-__global__ void __launch_bounds__(kLaneWarps * 32, lane_blocks_per_sm(KB)) k_search_select(const SearchArgs a)
+__global__ void __launch_bounds__(kLaneWarps * 32, lane_blocks_per_sm(KB, kMode)) k_search_select(const SearchArgs a)
 {
     grid_dep_wait();
     grid_dep_trigger();
@@ -1128,13 +1142,14 @@ __global__ void __launch_bounds__(kLaneWarps * 32, lane_blocks_per_sm(KB)) k_sea
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // this lane's candidate list: depth lt[c * 32] and table index li[c * 32]
-    float *lt = reinterpret_cast<float *>(smem) + warp * (kLaneCap * 32) + lane;
-    uint32_t *li = reinterpret_cast<uint32_t *>(smem) + kLaneWarps * kLaneCap * 32 + warp * (kLaneCap * 32) + lane;
+    constexpr int kCap = lane_cap(kMode);
+    float *lt = reinterpret_cast<float *>(smem) + warp * (kCap * 32) + lane;
+    uint32_t *li = reinterpret_cast<uint32_t *>(smem) + kLaneWarps * kCap * 32 + warp * (kCap * 32) + lane;
 
     // proposal weights (FP32 copy of the BF16 ones) behind the columns
     float *pw = nullptr;
     if constexpr (kLearned) {
-        pw = reinterpret_cast<float *>(smem + lane_smem_bytes());
+        pw = reinterpret_cast<float *>(smem + lane_smem_bytes(kMode));
         prop::load_weights(a.prop_w, pw);
         __syncthreads();
     }
@@ -1150,9 +1165,9 @@ __global__ void __launch_bounds__(kLaneWarps * 32, lane_blocks_per_sm(KB)) k_sea
         // the pixels whose slots overflowed walk their whole window with the
         // warp-per-ray search: the heaviest rays of the frame, so the warps
         // take them before any tile (their latency then overlaps the tiles)
-        float4 *cp = reinterpret_cast<float4 *>(reinterpret_cast<float *>(smem) + warp * (kLaneCap * 32));
+        float4 *cp = reinterpret_cast<float4 *>(reinterpret_cast<float *>(smem) + warp * (kCap * 32));
         uint64_t *ck = reinterpret_cast<uint64_t *>(cp + kCandCap);
-        static_assert(kCandCap * (sizeof(float4) + sizeof(uint64_t)) <= kLaneCap * 32 * sizeof(float),
+        static_assert(kCandCap * (sizeof(float4) + sizeof(uint64_t)) <= kCap * 32 * sizeof(float),
                       "the warp search's lists fit one warp's depth column");
         const uint32_t n_ovf = *a.ovf_count;
         for (;;) {
@@ -1335,7 +1350,9 @@ cudaError_t search_pass(const SearchArgs &a, cudaStream_t st, Prof *prof, int ki
                                   : a.K <= 16 ? k_search_select<16, 0> : k_search_select<32, 0>);
     auto wide_k = a.K <= 4 ? k_search_select_wide<4> : a.K <= 8 ? k_search_select_wide<8>
                 : a.K <= 16 ? k_search_select_wide<16> : k_search_select_wide<32>;
-    const size_t lsm = lane_smem_bytes() + (a.prop_w ? (size_t)(prop::kNP + 4) * 4 : 0), wsm = search_smem_bytes();
+    const int lane_mode = a.prop_w ? 2 : a.interval ? 1 : point_major ? 3 : 0;
+    const size_t lsm = lane_smem_bytes(lane_mode) + (a.prop_w ? (size_t)(prop::kNP + 4) * 4 : 0),
+                 wsm = search_smem_bytes();
     if ((e = cudaFuncSetAttribute(lane_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm)) != cudaSuccess)
         return e;
     if ((e = cudaFuncSetAttribute(wide_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm)) != cudaSuccess)
@@ -1348,7 +1365,8 @@ cudaError_t search_pass(const SearchArgs &a, cudaStream_t st, Prof *prof, int ki
         units = div_up(a.R, 32);
     // persistent warps: as many blocks as stay resident, fewer for small work
     const int KB = a.K <= 4 ? 4 : a.K <= 8 ? 8 : a.K <= 16 ? 16 : 32;
-    const int64_t blocks = std::min<int64_t>(div_up(units, kLaneWarps), (int64_t)a.n_sm * lane_blocks_per_sm(KB));
+    const int64_t blocks =
+        std::min<int64_t>(div_up(units, kLaneWarps), (int64_t)a.n_sm * lane_blocks_per_sm(KB, lane_mode));
     // A short plain list of rays (a training batch) would give the lane
     // kernel a few hundred warps for the whole GPU: one warp per ray instead
     if (!point_major && !a.interval && !a.prop_w && a.rays && a.R <= (int64_t)a.n_sm * kSmallListPerSm) {
