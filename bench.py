@@ -169,15 +169,15 @@ NCU_TRAFFIC_WORKLOAD = (1_000_000, 800)
 NCU_TRAFFIC = {
     # the search stage's time (k_search_select) covers the point-major pass
     # (k_search_splat) and the selection launch: their bytes are summed
-    "k_search_select": {"bytes": 52966656 + 38180096 + 116630784 + 36503296,
+    "k_search_select": {"bytes": 52894720 + 38134784 + 116590848 + 33305856,
                         "sources": ('hp_search.cu', 'hp_common.cuh', 'hp_kernels.cuh'),
-                        "sha256": "0fad5facf9b0ca4c4129bd8c921bdd86e5e5676529aa4fa75d0bf9773cae0845"},
-    "k_pack_samples": {"bytes": 17948928 + 3584,
+                        "sha256": "b68e6a5d41c4a14fc05d68c3d1ca507b9ab5be61a15e664ad85ec2145d7adafe"},
+    "k_pack_samples": {"bytes": 17949696 + 2816,
                        "sources": ('hp_search.cu', 'hp_common.cuh', 'hp_kernels.cuh'),
-                       "sha256": "0fad5facf9b0ca4c4129bd8c921bdd86e5e5676529aa4fa75d0bf9773cae0845"},
-    "k_aggregate_decode": {"bytes": 88079104 + 4423168,
+                       "sha256": "b68e6a5d41c4a14fc05d68c3d1ca507b9ab5be61a15e664ad85ec2145d7adafe"},
+    "k_aggregate_decode": {"bytes": 88081152 + 4401152,
                            "sources": ('hp_decode_tc.cu', 'hp_tc.cuh', 'hp_common.cuh', 'hp_kernels.cuh'),
-                           "sha256": "8adfe88165301d8574d7024a9940c0958d0664862adfd3965fb851b9e156bf47"},
+                           "sha256": "5d497f5336dcfe6f5d13cb7044f71f702da0d0f1e9eb5d2e5ab5509be9857d25"},
 }
 
 

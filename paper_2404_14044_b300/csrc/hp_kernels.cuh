@@ -87,9 +87,9 @@ struct BuildArgs {
 // Candidates per ray held by the lane-per-ray search (its shared-memory
 // column); rays with more go to the warp-per-ray search.
 constexpr int kLaneCap = 48;
-// The point-major selection's column (its candidates come from the slots;
-// a shorter column leaves room for a fifth block per SM).
-constexpr int kLaneCapPM = 40;
+// The column of the point-major selection and of the restricted walk: a
+// shorter column leaves room for a fifth block per SM (K <= 8).
+constexpr int kLaneCapShort = 40;
 // Slots per ray of the point-major pass: the lane search reads rays of up to
 // kLaneCap candidates from them, the warp-per-ray search rays of up to kPmCap.
 constexpr int kPmCap = 128;

@@ -10,8 +10,9 @@
 // k_search_select: one thread per ray.  A warp owns an 8 x 4 tile of pixels
 // (whole frames) or 32 consecutive listed rays.  The lane gathers its ray's
 // accepted points into its own column of a [cap][32] shared-memory array
-// (conflict-free whatever the counts; cap kLaneCapPM for the point-major
-// selection, kLaneCap for the walks): from the point-major slots, or
+// (conflict-free whatever the counts; cap kLaneCapShort for the point-major
+// selection and the restricted walk, kLaneCap for the plain and learned
+// walks): from the point-major slots, or
 // by walking the s x s window itself (listed rays, restricted searches; a
 // window row of s buckets is s adjacent keys, so one contiguous run of the
 // reordered list).  The column stays unsorted: candidate j+1 is the smallest
@@ -679,17 +680,22 @@ constexpr int kLaneWarps = 4;
 // warp-per-ray search
 constexpr uint32_t kLaneWalkMax = 384;
 
-// column entries per lane: the point-major selection (kMode 3) keeps a
-// shorter column than the window walks
-__host__ __device__ constexpr int lane_cap(int kMode) { return kMode == 3 ? kLaneCapPM : kLaneCap; }
+// The point-major selection (kMode 3) and the restricted walk (kMode 1) run
+// with shorter columns, two position loads in flight instead of four and
+// more blocks per SM (no register spills at those bounds); the plain and
+// learned walks keep the longer column.
+__host__ __device__ constexpr bool lane_short(int kMode) { return kMode == 3 || kMode == 1; }
 
-// resident blocks per SM for each K bucket and mode (K <= 8: the window walks
-// 4 -- shared memory, 48 KB per block, and registers -- the point-major
-// selection 5, its 40 KB columns and at most 102 registers without spills;
-// K > 8: 3, for the registers of the larger neighbour arrays without spills)
+// column entries per lane
+__host__ __device__ constexpr int lane_cap(int kMode) { return lane_short(kMode) ? kLaneCapShort : kLaneCap; }
+
+// resident blocks per SM for each K bucket and mode (K <= 8: 5 with the
+// short columns -- 40 KB of shared memory and at most 102 registers a
+// block -- else 4 (48 KB); K <= 16: 4 with the short columns, else 3; K >
+// 16: 3, for the registers of the larger neighbour arrays)
 __host__ __device__ constexpr int lane_blocks_per_sm(int KB, int kMode)
 {
-    return KB <= 8 ? (kMode == 3 ? 5 : 4) : 3;
+    return KB <= 8 ? (lane_short(kMode) ? 5 : 4) : (KB <= 16 && lane_short(kMode) ? 4 : 3);
 }
 
 __host__ __device__ constexpr size_t lane_smem_bytes(int kMode)
@@ -1006,7 +1012,7 @@ __device__ __forceinline__ bool lane_ray(const SearchArgs &a, int64_t ri, int pi
         idq = -2;
         // kNb column entries at a time: the positions of those within lim in
         // depth are loaded together before any is used (their latencies overlap)
-        constexpr int kNb = kPointMajor ? 2 : 4;
+        constexpr int kNb = lane_short(kMode) ? 2 : 4;
         for (int c0 = 0; c0 < C; c0 += kNb) {
             float tcs[kNb];
             float4 P[kNb];
