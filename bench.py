@@ -171,13 +171,13 @@ NCU_TRAFFIC = {
     # (k_search_splat) and the selection launch: their bytes are summed
     "k_search_select": {"bytes": 52894720 + 38134784 + 116590848 + 33305856,
                         "sources": ('hp_search.cu', 'hp_common.cuh', 'hp_kernels.cuh'),
-                        "sha256": "b68e6a5d41c4a14fc05d68c3d1ca507b9ab5be61a15e664ad85ec2145d7adafe"},
+                        "sha256": "e95cb54ad78bf32ce1b860dfa1f9165c547af41c04c92f38158b02300d141b98"},
     "k_pack_samples": {"bytes": 17949696 + 2816,
                        "sources": ('hp_search.cu', 'hp_common.cuh', 'hp_kernels.cuh'),
-                       "sha256": "b68e6a5d41c4a14fc05d68c3d1ca507b9ab5be61a15e664ad85ec2145d7adafe"},
+                       "sha256": "e95cb54ad78bf32ce1b860dfa1f9165c547af41c04c92f38158b02300d141b98"},
     "k_aggregate_decode": {"bytes": 88081152 + 4401152,
                            "sources": ('hp_decode_tc.cu', 'hp_tc.cuh', 'hp_common.cuh', 'hp_kernels.cuh'),
-                           "sha256": "5d497f5336dcfe6f5d13cb7044f71f702da0d0f1e9eb5d2e5ab5509be9857d25"},
+                           "sha256": "3cd97c3fade41cc6c42c82c3ac31ecdc290e632cca614573495ba35abbfedcfb"},
 }
 
 
