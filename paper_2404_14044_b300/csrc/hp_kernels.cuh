@@ -135,6 +135,10 @@ struct SearchArgs {
     int n_sm;                // multiprocessors of the device (grid sizing)
     const int32_t *ray_map;  // fallback pass: original index of listed ray i
     const uint32_t *count_ptr;   // fallback pass: number of listed rays (device)
+    // fallback pass (0: off): the lane-per-ray kernel takes the list only
+    // when it holds more than list_split rays; the warp-per-ray kernel takes
+    // the whole list up to that many, else the rays the lanes listed as wide
+    uint32_t list_split;
     const int32_t *rays;     // NULL: ray i is pixel i
     int64_t R;
     int32_t *n_s;

@@ -651,7 +651,11 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select_wide(const 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float4 *cp = reinterpret_cast<float4 *>(smem + L.cp) + warp * kCandCap;
     uint64_t *ck = reinterpret_cast<uint64_t *>(smem + L.ck) + warp * kCandCap;
-    const int64_t R_eff = a.count_ptr ? (int64_t)*a.count_ptr : a.R;
+    // a long fallback list went to the lane kernel: its wide rays come here
+    const bool to_lanes = a.list_split && a.count_ptr && *a.count_ptr > a.list_split;
+    const int32_t *map = to_lanes ? a.wide : a.ray_map;
+    const uint32_t *cnt = to_lanes ? a.wide_count : a.count_ptr;
+    const int64_t R_eff = cnt ? (int64_t)*cnt : a.R;
 
     // every warp pulls the next listed ray from a grid-wide counter, so heavy
     // rays never hold up a block; blocks past the list's end leave at once
@@ -662,7 +666,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_select_wide(const 
         rl = __shfl_sync(kFull, rl, 0);
         if ((int64_t)rl >= R_eff) break;
         // ri: the ray's index in the outputs (listed passes: from the list)
-        const int64_t ri = a.ray_map ? (int64_t)__ldg(a.ray_map + (int64_t)rl) : (int64_t)rl;
+        const int64_t ri = map ? (int64_t)__ldg(map + (int64_t)rl) : (int64_t)rl;
         wide_ray<KB>(a, a.interval, ri, cp, ck);
     }
 }
@@ -1164,8 +1168,10 @@ __global__ void __launch_bounds__(kLaneWarps * 32, lane_blocks_per_sm(KB, kMode)
     const int64_t npix = (int64_t)W * H;
     const bool frame = !a.rays && !a.ray_map;
     const int tiles_x = (W + 7) >> 3;
+    const int64_t n_list = a.count_ptr ? (int64_t)*a.count_ptr : a.R;
+    // a short fallback list is the warp-per-ray kernel's (list_split)
     const int64_t n_units = frame ? (int64_t)tiles_x * ((H + 3) >> 2)
-                                  : ((a.count_ptr ? (int64_t)*a.count_ptr : a.R) + 31) / 32;
+                                  : (a.list_split && n_list <= (int64_t)a.list_split ? 0 : (n_list + 31) / 32);
     const int64_t R_eff = frame ? npix : (a.count_ptr ? (int64_t)*a.count_ptr : a.R);
     if constexpr (kMode == 3) {
         // the pixels whose slots overflowed walk their whole window with the
@@ -1439,8 +1445,12 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof)
     if ((e = launch_clear(a.ticket, (size_t)(ze - z0), st, prof)) != cudaSuccess) return e;
     if ((e = search_pass(a, st, prof, KID_SEARCH)) != cudaSuccess) return e;
     if ((a.interval || a.prop_w) && a.fallback) {
-        // plain search for the rays the restricted search flagged: few and
-        // scattered rays, so one warp per ray
+        // plain search for the rays the restricted search flagged.  Few and
+        // scattered rays go one warp per ray; a list of more than
+        // kSmallListPerSm rays per SM (the count is on the device) goes to
+        // the lane-per-ray kernel, whose too-wide rays the warp kernel then
+        // takes: both kernels launch, and each reads the count to see which
+        // part is its own
         SearchArgs b = a;
         b.interval = nullptr;
         b.prop_w = nullptr;
@@ -1448,13 +1458,27 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof)
         b.count_ptr = a.fallback_count;
         b.raytab_stale = 0;
         b.pm_cnt = nullptr;
-        if ((e = launch_clear(a.pull, sizeof(unsigned long long), st, prof)) != cudaSuccess) return e;
+        b.list_split = (uint32_t)std::min<int64_t>((int64_t)a.n_sm * kSmallListPerSm, 0x7fffffff);
+        // wide_count, lane_units and the 64-bit pull counter (ticket words 2-5)
+        if (reinterpret_cast<const char *>(a.lane_units) != reinterpret_cast<const char *>(a.wide_count) + 4 ||
+            reinterpret_cast<const char *>(a.pull) != reinterpret_cast<const char *>(a.wide_count) + 8)
+            return cudaErrorInvalidValue;
+        if ((e = launch_clear(a.wide_count, 4 * sizeof(uint32_t), st, prof)) != cudaSuccess) return e;
+        auto lane0 = a.K <= 4 ? k_search_select<4, 0> : a.K <= 8 ? k_search_select<8, 0>
+                   : a.K <= 16 ? k_search_select<16, 0> : k_search_select<32, 0>;
         auto wide_k = a.K <= 4 ? k_search_select_wide<4> : a.K <= 8 ? k_search_select_wide<8>
                     : a.K <= 16 ? k_search_select_wide<16> : k_search_select_wide<32>;
+        const int KB = a.K <= 4 ? 4 : a.K <= 8 ? 8 : a.K <= 16 ? 16 : 32;
+        const size_t lsm = lane_smem_bytes(0);
+        if ((e = cudaFuncSetAttribute(lane0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm)) != cudaSuccess)
+            return e;
+        const int64_t lblocks =
+            std::min<int64_t>(div_up(div_up(a.R, 32), kLaneWarps), (int64_t)a.n_sm * lane_blocks_per_sm(KB, 0));
         const int64_t wblocks = std::min<int64_t>(div_up(a.R, kSearchWarps), (int64_t)a.n_sm * 4);
         prof_begin(prof, st, KID_SEARCH_FALLBACK);
+        launch_chained(lane0, (unsigned)lblocks, kLaneWarps * 32, lsm, st, b);
         launch_chained(wide_k, (unsigned)wblocks, kSearchWarps * 32, search_smem_bytes(), st, b);
-        prof_end(prof, st);
+        prof_end(prof, st, 2);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     prof_begin(prof, st, KID_PACK);
