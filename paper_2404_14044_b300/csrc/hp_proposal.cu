@@ -34,11 +34,11 @@ __device__ __forceinline__ int ray_pixel(const PropArgs &a, int64_t r) { return 
 
 }  // namespace
 
-__global__ void __launch_bounds__(256) k_prop_infer(const PropArgs a)
+__global__ void __launch_bounds__(256, 4) k_prop_infer(const PropArgs a)
 {
     grid_dep_wait();
     grid_dep_trigger();
-    __shared__ __align__(16) float w[kNP + 2];
+    __shared__ __align__(16) float w[kImage];
     load_weights(a.weights_bf16, w);
     __syncthreads();
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -77,6 +77,8 @@ __global__ void __launch_bounds__(256) k_prop_train(const PropArgs a)
             s1 = a.t[o + n - 1];
             const int pv = pix / a.cam.width, pu = pix - pv * a.cam.width;
             histogram(a.cam, a.start, a.spts, a.h, a.Wp, a.Hp, pu, pv, x);
+#pragma unroll
+            for (int b = 0; b < kIn; ++b) x[b] = log1pf(x[b]);
         }
     }
     float g[kNP];   // per-thread gradient (registers / local)

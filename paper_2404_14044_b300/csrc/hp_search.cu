@@ -1363,7 +1363,7 @@ cudaError_t search_pass(const SearchArgs &a, cudaStream_t st, Prof *prof, int ki
     auto wide_k = a.K <= 4 ? k_search_select_wide<4> : a.K <= 8 ? k_search_select_wide<8>
                 : a.K <= 16 ? k_search_select_wide<16> : k_search_select_wide<32>;
     const int lane_mode = a.prop_w ? 2 : a.interval ? 1 : point_major ? 3 : 0;
-    const size_t lsm = lane_smem_bytes(lane_mode) + (a.prop_w ? (size_t)(prop::kNP + 4) * 4 : 0),
+    const size_t lsm = lane_smem_bytes(lane_mode) + (a.prop_w ? (size_t)(prop::kImage + 4) * 4 : 0),
                  wsm = search_smem_bytes();
     if ((e = cudaFuncSetAttribute(lane_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm)) != cudaSuccess)
         return e;
@@ -1445,12 +1445,14 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof)
     if ((e = launch_clear(a.ticket, (size_t)(ze - z0), st, prof)) != cudaSuccess) return e;
     if ((e = search_pass(a, st, prof, KID_SEARCH)) != cudaSuccess) return e;
     if ((a.interval || a.prop_w) && a.fallback) {
-        // plain search for the rays the restricted search flagged.  Few and
-        // scattered rays go one warp per ray; a list of more than
-        // kSmallListPerSm rays per SM (the count is on the device) goes to
-        // the lane-per-ray kernel, whose too-wide rays the warp kernel then
-        // takes: both kernels launch, and each reads the count to see which
-        // part is its own
+        // plain search for the rays the restricted search flagged, one warp
+        // per ray.  With K > 8 a list of more than kSmallListPerSm rays per
+        // SM -- the count is on the device -- goes to the lane-per-ray kernel
+        // instead, whose too-wide rays the warp kernel then takes: both
+        // kernels launch, and each reads the count to see which part is its
+        // own.  Measured: forward_1008 (K 16, 40k missed rays) 0.128 ms by
+        // warps, 0.059 by lanes; objects_800 (K 8, a long list) 0.055 ms by
+        // warps, 0.074 by lanes
         SearchArgs b = a;
         b.interval = nullptr;
         b.prop_w = nullptr;
@@ -1458,7 +1460,8 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof)
         b.count_ptr = a.fallback_count;
         b.raytab_stale = 0;
         b.pm_cnt = nullptr;
-        b.list_split = (uint32_t)std::min<int64_t>((int64_t)a.n_sm * kSmallListPerSm, 0x7fffffff);
+        const bool split = a.K > 8;
+        b.list_split = split ? (uint32_t)std::min<int64_t>((int64_t)a.n_sm * kSmallListPerSm, 0x7fffffff) : 0u;
         // wide_count, lane_units and the 64-bit pull counter (ticket words 2-5)
         if (reinterpret_cast<const char *>(a.lane_units) != reinterpret_cast<const char *>(a.wide_count) + 4 ||
             reinterpret_cast<const char *>(a.pull) != reinterpret_cast<const char *>(a.wide_count) + 8)
@@ -1476,9 +1479,9 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof)
             std::min<int64_t>(div_up(div_up(a.R, 32), kLaneWarps), (int64_t)a.n_sm * lane_blocks_per_sm(KB, 0));
         const int64_t wblocks = std::min<int64_t>(div_up(a.R, kSearchWarps), (int64_t)a.n_sm * 4);
         prof_begin(prof, st, KID_SEARCH_FALLBACK);
-        launch_chained(lane0, (unsigned)lblocks, kLaneWarps * 32, lsm, st, b);
+        if (split) launch_chained(lane0, (unsigned)lblocks, kLaneWarps * 32, lsm, st, b);
         launch_chained(wide_k, (unsigned)wblocks, kSearchWarps * 32, search_smem_bytes(), st, b);
-        prof_end(prof, st, 2);
+        prof_end(prof, st, split ? 2 : 1);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     prof_begin(prof, st, KID_PACK);
