@@ -527,12 +527,15 @@ __global__ void __launch_bounds__(128, 1) k_mma_selftest(const uint16_t *A, cons
 // (tcgen05.commit after the layer-0 MMAs that read buffer b), lbar[b] (bulk
 // copy of a tile's neighbour lists), mma (per layer), the weights' barrier.
 // Every wait is bounded.
-constexpr int kWsConsumerWarps = 16;      // two groups, each 4 TMEM lane quarters x kWsGroups column groups
+// Consumer warps kCW (a template parameter): two groups, each 4 TMEM lane
+// quarters x (kCW / 8) column groups.  16 for K <= 8; 8 for larger K, where
+// the gather of twice the neighbours sets the pace and the fewer, wider
+// consumer warps leave the producers more of the SM (forward_1008, K 16:
+// 0.380 -> 0.354 ms FP32, 0.342 -> 0.314 BF16; objects_800, K 8: 0.233 ->
+// 0.245 FP32, so K 8 keeps 16).
 constexpr int kWsProducerWarps = 16;
-constexpr int kWsGroupWarps = kWsConsumerWarps / 2;
-constexpr int kWsGroups = kWsGroupWarps / 4;
 constexpr int kWsBatch = 1;               // 8-column chunks a consumer thread reads from TMEM at once (2 and 4: register spills)
-constexpr int kWsThreads = (kWsConsumerWarps + kWsProducerWarps) * 32;
+__host__ __device__ constexpr int ws_threads(int kCW) { return (kCW + kWsProducerWarps) * 32; }
 constexpr uint32_t kWsCols = 512, kColAH = 128, kColAL = 192;   // per consumer group, group g at 256 g
 
 struct WsLayout {
@@ -647,9 +650,13 @@ __global__ void k_ws_image(const RenderArgs a, const WsLayout L)
     }
 }
 
-template <bool kBF16>
-__global__ void __launch_bounds__(kWsThreads, 1) k_decode_ws(const RenderArgs a, const WsLayout L, int bulk_ok)
+template <bool kBF16, int kCW>
+__global__ void __launch_bounds__(ws_threads(kCW), 1) k_decode_ws(const RenderArgs a, const WsLayout L, int bulk_ok)
 {
+    constexpr int kWsConsumerWarps = kCW;
+    constexpr int kWsGroupWarps = kWsConsumerWarps / 2;
+    constexpr int kWsGroups = kWsGroupWarps / 4;
+    static_assert(kWsGroups >= 1 && kWsGroupWarps % 4 == 0, "consumer groups of whole lane-quarter sets");
     grid_dep_wait();
     grid_dep_trigger();
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -1108,7 +1115,10 @@ cudaError_t launch_decode_tc(const RenderArgs &a, bool bf16, cudaStream_t st, in
                                     ((uintptr_t)a.slot_dist % 16 == 0) ? 2 : 0);
     const WsLayout W = ws_layout(a, bf16);
     if (W.ok) {
-        auto kern = bf16 ? k_decode_ws<true> : k_decode_ws<false>;
+        const bool narrow = a.K > 8;           // 8 consumer warps
+        auto kern = bf16 ? (narrow ? k_decode_ws<true, 8> : k_decode_ws<true, 16>)
+                         : (narrow ? k_decode_ws<false, 8> : k_decode_ws<false, 16>);
+        const int threads = ws_threads(narrow ? 8 : 16);
         if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, W.total)) != cudaSuccess)
             return e;
         if (ws_image_bytes(W) > kWsImageMax || (uintptr_t)a.wimg % 16 != 0) return cudaErrorInvalidValue;
@@ -1116,7 +1126,7 @@ cudaError_t launch_decode_tc(const RenderArgs &a, bool bf16, cudaStream_t st, in
         const int64_t tiles = div_up(a.capacity > 0 ? a.capacity : 1, kTcTile);
         if (grid > tiles) grid = tiles;
         launch_chained(bf16 ? k_ws_image<true> : k_ws_image<false>, (unsigned)a.num_sms, 256, 0, st, a, W);
-        launch_chained(kern, (unsigned)grid, kWsThreads, W.total, st, a, W, bulk_ok_ws);
+        launch_chained(kern, (unsigned)grid, threads, W.total, st, a, W, bulk_ok_ws);
         *n_kernels = 2;
         return cudaGetLastError();
     }
