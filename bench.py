@@ -169,15 +169,15 @@ NCU_TRAFFIC_WORKLOAD = (1_000_000, 800)
 NCU_TRAFFIC = {
     # the search stage's time (k_search_select) covers the point-major pass
     # (k_search_splat) and the selection launch: their bytes are summed
-    "k_search_select": {"bytes": 52894720 + 38134784 + 116590848 + 33305856,
+    "k_search_select": {"bytes": 52944640 + 38285568 + 116661248 + 33304576,
                         "sources": ('hp_search.cu', 'hp_common.cuh', 'hp_kernels.cuh'),
-                        "sha256": "e95cb54ad78bf32ce1b860dfa1f9165c547af41c04c92f38158b02300d141b98"},
-    "k_pack_samples": {"bytes": 17949696 + 2816,
+                        "sha256": "09ea9a1b3acab95524144f805abe6737b8b05a4a4f2311cf0d0aeb2e6863c8f3"},
+    "k_pack_samples": {"bytes": 17950208 + 2560,
                        "sources": ('hp_search.cu', 'hp_common.cuh', 'hp_kernels.cuh'),
-                       "sha256": "e95cb54ad78bf32ce1b860dfa1f9165c547af41c04c92f38158b02300d141b98"},
-    "k_aggregate_decode": {"bytes": 88081152 + 4401152,
+                       "sha256": "09ea9a1b3acab95524144f805abe6737b8b05a4a4f2311cf0d0aeb2e6863c8f3"},
+    "k_aggregate_decode": {"bytes": 88080896 + 4325120,
                            "sources": ('hp_decode_tc.cu', 'hp_tc.cuh', 'hp_common.cuh', 'hp_kernels.cuh'),
-                           "sha256": "3cd97c3fade41cc6c42c82c3ac31ecdc290e632cca614573495ba35abbfedcfb"},
+                           "sha256": "038425bd0aa8d0554f384bc3935e10db49c9db21af711c208b632b4907a5c67c"},
 }
 
 
