@@ -177,7 +177,7 @@ NCU_TRAFFIC = {
                        "sha256": "09ea9a1b3acab95524144f805abe6737b8b05a4a4f2311cf0d0aeb2e6863c8f3"},
     "k_aggregate_decode": {"bytes": 88080896 + 4325120,
                            "sources": ('hp_decode_tc.cu', 'hp_tc.cuh', 'hp_common.cuh', 'hp_kernels.cuh'),
-                           "sha256": "038425bd0aa8d0554f384bc3935e10db49c9db21af711c208b632b4907a5c67c"},
+                           "sha256": "0a123ecbffd333950c33ce5a5e6e1308eedac9dc0835800c41604c2dcbbcddc2"},
 }
 
 
