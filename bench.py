@@ -329,7 +329,10 @@ def proposal_section(hp, H, pts_np, feats_np, params, dims, mlp_np, cam, train_c
             if k >= 2:
                 ev[k - 2][1].record()
         torch.cuda.synchronize()
-        ms = sum(a.elapsed_time(b) for a, b in ev) / n
+        # the median frame: these auxiliary comparisons launch from Python
+        # frame by frame, and one host-side stall inside a frame would
+        # otherwise move a 20-frame mean by a third
+        ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
         return ms, rgb.clone(), smp
     n = max(5, min(steps, 20))
     fb = torch.zeros(1, dtype=torch.int32, device=dev)
@@ -363,7 +366,7 @@ def proposal_section(hp, H, pts_np, feats_np, params, dims, mlp_np, cam, train_c
                         "oracle to 1e-4); features fitted 200 Adam steps (8192 rays/step) with "
                         "hp_aggregate_render_backward; proposal frames: hp_proposal_infer then "
                         "hp_search_sample_proposal; misses = hit rays whose sample sources differ from the "
-                        "plain search"}
+                        "plain search; ms = median of the frames' device times (L2 flushed before each)"}
 
 
 # ------------------------------------------------------ training step (f2)
