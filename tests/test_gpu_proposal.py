@@ -204,6 +204,54 @@ def test_restricted_search_against_oracle(crowded):
     hp.close()
 
 
+@pytest.mark.parametrize("case", ["k16_short_list", "k16_long_list"])
+def test_restricted_search_k16_fallback_lists(case):
+    # K > 8: a fallback list of more than 64 rays per SM goes through the
+    # lane-per-ray kernel (its too-wide rays then through the warp kernel),
+    # a shorter one through the warp kernel alone; both must give the
+    # oracle's result.  The long list: every hit ray's interval starts behind
+    # its first sample, so it falls back.
+    H = _H()
+    dev = torch.device("cuda", 0)
+    sc = scenes.sphere_plane_64() if case == "k16_short_list" else _scene()
+    sc.params.K = 16
+    cam, p = sc.camera, sc.params
+    R = cam.width * cam.height
+    fr = oracle.render(sc.points, sc.feats, cam, p, sc.mlp_dims, sc.mlp_params, nthreads=8)
+    if case == "k16_short_list":
+        tab = oracle.build_table(sc.points, cam, p)
+        n = OP.counts(tab, cam, np.arange(R))
+        iv = _oracle_intervals(fr, cam, n, scenes.proposal_params(2), np.random.default_rng(5))
+    else:
+        iv = np.tile(np.array([[cam.t_near, cam.t_far]], np.float32), (R, 1))
+        ns, off, tt = fr["n_s"], fr["sample_offset"], fr["t"]
+        hit = np.nonzero(ns > 0)[0]
+        s0 = tt[off[hit]].astype(np.float64)
+        s1 = tt[off[hit] + ns[hit] - 1].astype(np.float64)
+        iv[hit, 0] = np.clip(s0 + 1e-4, cam.t_near, cam.t_far)
+        iv[hit, 1] = np.clip(s1 + 0.1, iv[hit, 0], cam.t_far)
+    o = oracle.render(sc.points, sc.feats, cam, p, sc.mlp_dims, sc.mlp_params, nthreads=8, intervals=iv)
+    hp = H.HashPoint(p, dev)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    fb = torch.zeros(1, dtype=torch.int32, device=dev)
+    hp.build_table(t(sc.points), cam, p.r)
+    smp = hp.search_sample_proposal(None, p.K, p.n_max, t(iv), fallback_count=fb)
+    rgb, wsum = hp.aggregate_render(smp, t(sc.feats), sc.mlp_dims, t(sc.mlp_params))
+    g = smp.packed(R)
+    g = {k: (v.numpy() if isinstance(v, torch.Tensor) else v) for k, v in g.items()}
+    g["rgb"] = rgb.cpu().numpy().astype(np.float64)
+    g["wsum"] = wsum.cpu().numpy().astype(np.float64)
+    g["status"] = hp.status()
+    hp.close()
+    assert_parity(g, o, p.K)
+    limit = 64 * torch.cuda.get_device_properties(0).multi_processor_count
+    n_fb = int(fb.item())
+    if case == "k16_short_list":
+        assert 0 < n_fb <= limit, n_fb
+    else:
+        assert n_fb > limit, (n_fb, limit)
+
+
 def test_training_loop_and_miss_rate():
     H = _H()
     dev = torch.device("cuda", 0)
