@@ -376,8 +376,11 @@ def train_section(hp, H, pts_np, feats_np, params, dims, mlp_np, cams, steps, de
     random pixels per view; per view the forward (table build, search on the
     listed rays, aggregate + render) and hp_aggregate_render_backward with
     respect to the point features and positions, for the MSE loss against a
-    target image (the forward with a second feature draw).  Rays/s = 16,384
-    rays per step over the step's device time."""
+    target image (the forward with a second feature draw).  The views are
+    independent until the gradient sums (the backward accumulates them with
+    atomics), so each runs on its own stream with its own library context;
+    a step forks from and joins the current stream.  Rays/s = 16,384 rays per
+    step over the step's device time."""
     import torch
     t = lambda a: torch.from_numpy(a).to(dev)
     pts, feats, mlp = t(pts_np), t(feats_np), t(mlp_np)
@@ -393,20 +396,44 @@ def train_section(hp, H, pts_np, feats_np, params, dims, mlp_np, cams, steps, de
     gf = torch.zeros_like(feats)
     gp = torch.zeros_like(pts)
     smp = H.SampleBuffers.allocate(n_rays, params.K, params.n_max, dev)
+    ctxs = [hp] + [H.HashPoint(params, dev) for _ in range(len(views) - 1)]
+    smps = [smp] + [H.SampleBuffers.allocate(n_rays, params.K, params.n_max, dev) for _ in range(len(views) - 1)]
+    streams = [torch.cuda.Stream() for _ in views]
+
+    def view_pass(c, v, cam, sm):
+        c.build_table(pts, cam, params.r)
+        c.search_sample(rays[v], params.K, params.n_max, out=sm)
+        rgb, wsum = c.aggregate_render(sm, feats, dims, mlp)
+        d = rgb - tgt[v]
+        c.aggregate_render_backward(sm, pts, feats, dims, mlp, (2.0 / d.numel()) * d, grad_feats=gf,
+                                    grad_points=gp)
+        return (d * d).mean()
 
     def step():
+        # the views on their own streams and contexts, forked from and joined
+        # to the current stream
+        main = torch.cuda.current_stream()
         gf.zero_()
         gp.zero_()
-        loss = []
+        fork = torch.cuda.Event()
+        fork.record(main)
+        loss, joins = [], []
         for v, cam in enumerate(views):
-            hp.build_table(pts, cam, params.r)
-            hp.search_sample(rays[v], params.K, params.n_max, out=smp)
-            rgb, wsum = hp.aggregate_render(smp, feats, dims, mlp)
-            d = rgb - tgt[v]
-            loss.append((d * d).mean())
-            hp.aggregate_render_backward(smp, pts, feats, dims, mlp, (2.0 / d.numel()) * d, grad_feats=gf,
-                                         grad_points=gp)
+            streams[v].wait_event(fork)
+            with torch.cuda.stream(streams[v]):
+                loss.append(view_pass(ctxs[v], v, cam, smps[v]))
+                e = torch.cuda.Event()
+                e.record(streams[v])
+                joins.append(e)
+        for e in joins:
+            main.wait_event(e)
         return loss
+
+    def step_serial():
+        # one context, one stream: the per-kernel profile of a step
+        gf.zero_()
+        gp.zero_()
+        return [view_pass(hp, v, cam, smp) for v, cam in enumerate(views)]
 
     for _ in range(3):
         step()
@@ -420,11 +447,14 @@ def train_section(hp, H, pts_np, feats_np, params, dims, mlp_np, cams, steps, de
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in ev) / n
     hp.profile_start(256)
-    step()
+    step_serial()
     prof = hp.profile_stop()
-    code, detail = hp.status()
-    if code != 0:
-        raise SystemExit(f"device status after training pass: {H.status_string(code)} ({detail})")
+    for c in ctxs:
+        code, detail = c.status()
+        if code != 0:
+            raise SystemExit(f"device status after training pass: {H.status_string(code)} ({detail})")
+    for c in ctxs[1:]:
+        c.close()
     per_kernel = {k: round(v[0] / max(v[1], 1), 5) for k, v in prof.items() if v[1]}
     launches = {k: v[1] for k, v in prof.items() if v[1]}
     # the last view's samples: the backward's work per launch
@@ -442,7 +472,9 @@ def train_section(hp, H, pts_np, feats_np, params, dims, mlp_np, cams, steps, de
                                     "peak_source": "derived: 148 SMs x 128 FP32 FMA lanes x 2 FLOP x 2032 MHz"},
             "protocol": "per view: hp_build_table, hp_search_sample on 4096 random pixels, hp_aggregate_render, "
                         "MSE loss against the forward with a second feature draw, "
-                        "hp_aggregate_render_backward (features and positions); L2 flushed before each step"}
+                        "hp_aggregate_render_backward (features and positions); the 4 views on 4 streams with "
+                        "one library context each, the gradients summed by the backward's atomics; L2 flushed "
+                        "before each step; per_kernel_ms from a serial step on one context"}
 
 
 # ------------------------------------------------------------------ GPU side
