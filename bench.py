@@ -171,10 +171,10 @@ NCU_TRAFFIC = {
     # (k_search_splat) and the selection launch: their bytes are summed
     "k_search_select": {"bytes": 52944640 + 38285568 + 116661248 + 33304576,
                         "sources": ('hp_search.cu', 'hp_common.cuh', 'hp_kernels.cuh'),
-                        "sha256": "09ea9a1b3acab95524144f805abe6737b8b05a4a4f2311cf0d0aeb2e6863c8f3"},
+                        "sha256": "6a84c8f727c389c5b3ab049c6bf856b9dd57ffbb256b3ca96722245deab79ddd"},
     "k_pack_samples": {"bytes": 17950208 + 2560,
                        "sources": ('hp_search.cu', 'hp_common.cuh', 'hp_kernels.cuh'),
-                       "sha256": "09ea9a1b3acab95524144f805abe6737b8b05a4a4f2311cf0d0aeb2e6863c8f3"},
+                       "sha256": "6a84c8f727c389c5b3ab049c6bf856b9dd57ffbb256b3ca96722245deab79ddd"},
     "k_aggregate_decode": {"bytes": 88080896 + 4325120,
                            "sources": ('hp_decode_tc.cu', 'hp_tc.cuh', 'hp_common.cuh', 'hp_kernels.cuh'),
                            "sha256": "0a123ecbffd333950c33ce5a5e6e1308eedac9dc0835800c41604c2dcbbcddc2"},

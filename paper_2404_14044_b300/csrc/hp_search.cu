@@ -1473,7 +1473,8 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof)
                     : a.K <= 16 ? k_search_select_wide<16> : k_search_select_wide<32>;
         const int KB = a.K <= 4 ? 4 : a.K <= 8 ? 8 : a.K <= 16 ? 16 : 32;
         const size_t lsm = lane_smem_bytes(0);
-        if ((e = cudaFuncSetAttribute(lane0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm)) != cudaSuccess)
+        if (split &&
+            (e = cudaFuncSetAttribute(lane0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm)) != cudaSuccess)
             return e;
         const int64_t lblocks =
             std::min<int64_t>(div_up(div_up(a.R, 32), kLaneWarps), (int64_t)a.n_sm * lane_blocks_per_sm(KB, 0));
