@@ -1,7 +1,8 @@
 """The bounds-check build (libhashpoint_checks.so, compiled with
 -DHP_CHECKS=1): the hot path over the test scenes -- table build, search,
 render with packed lists and with the lists left in the slots, every decode
-path, the backward -- records no bounds error; an out-of-range neighbour id
+path, the backward, the proposal's restricted search with both fallback
+paths and the learned search -- records no bounds error; an out-of-range neighbour id
 planted in caller-owned packed lists is reported as HP_ERR_BOUNDS with the
 id, and the access is skipped.  Runs in a child process: this one has the
 normal library loaded."""
@@ -46,6 +47,37 @@ CHILD = textwrap.dedent("""
         pts, feats, mlp, smp, rgb = frame(hp, sc, True, H.DECODE_FP32)
         hp.aggregate_render_backward(smp, pts, feats, sc.mlp_dims, mlp, torch.ones_like(rgb) * 1e-3)
         assert hp.status() == (0, 0), (sc.name, "backward", hp.status())
+        hp.close()
+
+    # the proposal paths: inference + restricted search + fallback (K 8: the
+    # warp kernel; K 16 with every hit ray falling back: the lane kernel, then
+    # the warp kernel), and the fused learned search
+    for K in (8, 16):
+        sc = scenes.objects_800(n_points=250_000, res=200)
+        sc.params.K = K
+        hp = H.HashPoint(sc.params, dev)
+        pts = torch.from_numpy(sc.points).to(dev)
+        feats = torch.from_numpy(sc.feats).to(dev)
+        mlp = torch.from_numpy(sc.mlp_params).to(dev)
+        R = sc.camera.width * sc.camera.height
+        st = H.ProposalState(dev, seed=3)
+        hp.build_table(pts, sc.camera, sc.params.r)
+        plain = hp.search_sample(None, K, sc.params.n_max)
+        packed = plain.packed(R)
+        ns, off, tt = packed["n_s"], packed["sample_offset"], packed["t"]
+        iv = torch.tensor([[sc.camera.t_near, sc.camera.t_far]]).repeat(R, 1)
+        hit = (ns > 0).nonzero().flatten()
+        iv[hit, 0] = (tt[off[hit]] + 1e-4).clamp(sc.camera.t_near, sc.camera.t_far)
+        iv = iv.to(dev).contiguous()
+        fb = torch.zeros(1, dtype=torch.int32, device=dev)
+        smp = hp.search_sample_proposal(None, K, sc.params.n_max, iv, fallback_count=fb)
+        hp.aggregate_render(smp, feats, sc.mlp_dims, mlp, decode=H.DECODE_BF16)
+        assert hp.status() == (0, 0), ("restricted", K, hp.status())
+        ivn = hp.proposal_infer(None, st.bf16)
+        smp = hp.search_sample_proposal(None, K, sc.params.n_max, ivn, fallback_count=fb)
+        smp = hp.search_sample_learned(None, K, sc.params.n_max, st.bf16)
+        hp.aggregate_render(smp, feats, sc.mlp_dims, mlp)
+        assert hp.status() == (0, 0), ("learned", K, hp.status())
         hp.close()
 
     # a neighbour id past the feature rows in the caller's packed lists
